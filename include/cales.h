@@ -1,0 +1,133 @@
+/*
+ * cales.h -- C ABI of the GB300 fast direct solver for the pressure Poisson
+ * and Crank-Nicolson velocity Helmholtz equations on a staggered grid.
+ *
+ * Method (paper Sec. 2.2): the Poisson equation for the pressure correction,
+ * Eq. (12), and the three Helmholtz equations of the implicit viscous step,
+ * Eq. (18), are discretised with second-order finite differences on a
+ * staggered grid and solved by an eigenfunction expansion: real FFT /
+ * DCT-II / DST-II in the uniform directions x and y, one tridiagonal system
+ * per wavenumber pair along the stretched direction z (Thomas algorithm),
+ * then the inverse transforms.  The paper computes its FFTs with cuFFT and
+ * its transposes with cuDecomp (Sec. 3.1); here every step is a hand-written
+ * sm_103a kernel behind this interface.
+ *
+ * Conventions (all calls):
+ *  - Fields are contiguous device arrays laid out [nz][ny][nx], x fastest.
+ *  - Element type: double for CALES_FP64 and CALES_FP32_REFINE plans, float
+ *    for CALES_FP32 plans.  The caller owns every field buffer; the plan owns
+ *    its tables and workspace (allocated by cales_plan / cales_set_precision).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Solves are asynchronous, launch kernels only, perform no host
+ *    synchronisation and no allocation, and may be captured in a CUDA graph.
+ *  - Return value: CALES_OK (0) or a negative cales_status code.  Conditions
+ *    detected on the device (non-finite values, non-positive pivots) are
+ *    OR-ed into a device status word read by cales_get_status.
+ *  - A plan may be used from one stream at a time (its workspace is shared
+ *    by its solves).
+ */
+#ifndef CALES_H
+#define CALES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cales_plan_s* cales_plan_t;
+typedef struct cales_batch_s* cales_batch_t;
+
+/* Boundary kinds, per side: xlo, xhi, ylo, yhi, zlo, zhi. */
+enum cales_bc {
+    CALES_BC_P = 0,  /* periodic (both sides of the direction)                       */
+    CALES_BC_N = 1,  /* homogeneous Neumann at the boundary face, cell-centred unknown */
+    CALES_BC_D = 2,  /* homogeneous Dirichlet at the boundary face, cell-centred
+                        unknown: ghost = -interior at the mirror distance            */
+    CALES_BC_DF = 3  /* homogeneous Dirichlet at a boundary node, node-centred unknown
+                        (z only): the boundary value is exactly zero               */
+};
+
+enum cales_precision {
+    CALES_FP64 = 0,        /* FP64 transforms and tridiagonal sweeps              */
+    CALES_FP32 = 1,        /* FP32 throughout (float fields)                     */
+    CALES_FP32_REFINE = 2  /* FP32 solves + FP64 residual and FP64 accumulation   */
+};
+
+enum cales_status {
+    CALES_OK = 0,
+    CALES_EINVAL = -1,       /* bad size, spacing, boundary pairing or argument  */
+    CALES_EUNSUPPORTED = -2, /* odd length > 1 or a radix outside {2,3,5} in x/y,
+                                DF in x/y, periodic z                           */
+    CALES_ENOMEM = -3,       /* device allocation failed                        */
+    CALES_ECUDA = -4         /* a CUDA runtime call failed                      */
+};
+
+enum cales_device_status_bits {
+    CALES_DEV_NONFINITE = 1, /* a non-finite value was produced               */
+    CALES_DEV_BADPIVOT = 2   /* a non-positive pivot met outside the pinned mode */
+};
+
+/*
+ * Create a plan for an nx x ny x nz grid (paper Sec. 2.2: uniform x, y;
+ * stretched z).  bc[6] = {xlo, xhi, ylo, yhi, zlo, zhi}; x and y take P, N or
+ * D with the same kind on both sides and an even length (or 1) whose half
+ * factors into 2, 3 and 5; z takes N, D or DF independently per side.
+ * dx, dy: uniform spacings.  dzc[0..nz]: distance between unknowns k-1 and k
+ * (dzc[0], dzc[nz]: to the ghost/boundary node; mirror value dzf[0] resp.
+ * dzf[nz-1] for cell-centred unknowns).  dzf[0..nz-1]: control-volume width
+ * of unknown k.  Both arrays are host memory and are copied.
+ * For node-centred unknowns (e.g. w in z with walls) pass the node grid:
+ * nz = number of interior nodes, dzc = distances between nodes, dzf = the
+ * widths between neighbouring cell centres.
+ * Default precision: CALES_FP64 with 2 refinement sweeps preset.
+ */
+int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6],
+               double dx, double dy, const double* dzc, const double* dzf);
+
+/* Select precision and refinement sweeps (0..8; used by CALES_FP32_REFINE).
+ * Allocates the FP32 workspace (4 bytes per grid point) when needed. */
+int cales_set_precision(cales_plan_t plan, int mode, int refine_sweeps);
+
+/*
+ * Poisson solve, Eq. (12): L p = f with the staggered 7-point Laplacian
+ * (Eq. 16).  With only periodic/Neumann sides L is singular: f is first made
+ * consistent (its dzf-weighted mean removed) and p is returned with zero
+ * dzf-weighted mean.  f and p are device arrays of nx*ny*nz elements; f == p
+ * is allowed (in place) for CALES_FP64 and CALES_FP32 plans.
+ */
+int cales_poisson_solve(cales_plan_t plan, const void* f, void* p, void* stream);
+
+/*
+ * Helmholtz solve, Eq. (18): (I - alpha L) u = f, alpha > 0
+ * (alpha = gamma_k nu dt / 2 of the Crank-Nicolson substep).
+ */
+int cales_helmholtz_solve(cales_plan_t plan, double alpha, const void* f, void* u, void* stream);
+
+/*
+ * Adjoint (transpose) solves: g = S^T w where S is the linear map f -> p of
+ * cales_poisson_solve (resp. f -> u of cales_helmholtz_solve).  Computed as
+ * the same transforms around the transposed tridiagonal systems
+ * (S^T = D S D^-1 with D = diag(dzf) along z).  CALES_FP64 and CALES_FP32
+ * plans; CALES_FP32_REFINE plans return CALES_EUNSUPPORTED.
+ */
+int cales_poisson_solve_adjoint(cales_plan_t plan, const void* w, void* g, void* stream);
+int cales_helmholtz_solve_adjoint(cales_plan_t plan, double alpha, const void* w, void* g, void* stream);
+
+/*
+ * FP64 residual r = f - L u (alpha < 0 selects Poisson) or r = f - (I - alpha L) u.
+ * u, f, r: double device arrays.  No projection is applied to f.
+ */
+int cales_residual(cales_plan_t plan, double alpha, const double* u, const double* f, double* r, void* stream);
+
+/* Read and clear the device status word (synchronises the plan's last stream). */
+int cales_get_status(cales_plan_t plan, int* device_status);
+
+/* Human-readable text of a cales_status code. */
+const char* cales_strerror(int code);
+
+/* Release the plan and its device memory (after its work has completed). */
+void cales_destroy(cales_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CALES_H */

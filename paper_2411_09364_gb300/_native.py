@@ -1,0 +1,67 @@
+"""ctypes declarations of the C ABI in include/cales.h (argument marshalling only).
+
+The library is the in-tree ``_build/libcales.so`` produced by ``build.py``.
+There is no fallback: if the library is missing or does not load, every
+entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libcales.so"
+_lib = None
+
+vp = C.c_void_p
+ip = C.POINTER(C.c_int)
+dp = C.POINTER(C.c_double)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "cales_plan": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.c_int, ip, C.c_double, C.c_double, dp, dp]),
+    "cales_set_precision": (C.c_int, [vp, C.c_int, C.c_int]),
+    "cales_poisson_solve": (C.c_int, [vp, vp, vp, vp]),
+    "cales_helmholtz_solve": (C.c_int, [vp, C.c_double, vp, vp, vp]),
+    "cales_poisson_solve_adjoint": (C.c_int, [vp, vp, vp, vp]),
+    "cales_helmholtz_solve_adjoint": (C.c_int, [vp, C.c_double, vp, vp, vp]),
+    "cales_residual": (C.c_int, [vp, C.c_double, vp, vp, vp, vp]),
+    "cales_get_status": (C.c_int, [vp, ip]),
+    "cales_strerror": (C.c_char_p, [C.c_int]),
+    "cales_destroy": (None, [vp]),
+    "cales_profile_enable": (C.c_int, [vp, C.c_int]),
+    "cales_profile_read": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_float)]),
+}
+
+
+def library_path() -> Path:
+    return Path(os.environ.get("CALES_LIB", _LIB_PATH))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not path.exists():
+            raise RuntimeError(f"CUDA library {path} is missing: run paper_2411_09364_gb300/build.py "
+                               "(or __graft_entry__.build()) first")
+        handle = C.CDLL(str(path))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+class CalesError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().cales_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def check(code: int, where: str) -> None:
+    if code != 0:
+        raise CalesError(code, where)

@@ -1,0 +1,243 @@
+// Shared device definitions of the CaLES-style fast direct solver on sm_103a.
+//
+// Fields are [nz][ny][nx] with x fastest.  Every uniform direction is
+// transformed by a real-to-real transform of length n:
+//   P (periodic)  : real DFT in halfcomplex order (Re of mode m at m, Im at n-m)
+//   N (Neumann)   : DCT-II        X_m = sum_i x_i cos(pi m (i+1/2)/n)
+//   D (Dirichlet) : DST-II        X_m = sum_i x_i sin(pi m (i+1/2)/n), m = 1..n
+// each computed from one complex FFT of length L = n/2 (real-input packing,
+// Makhoul's even/odd reordering for the cosine/sine transforms).  This keeps
+// the mode-space field real with exactly nx*ny*nz values, so the z tridiagonal
+// systems of the eigenfunction expansion (Sec. 2.2) are real too.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cales {
+
+enum { KIND_P = 0, KIND_N = 1, KIND_D = 2 };
+enum { ZBC_N = 1, ZBC_D = 2, ZBC_DF = 3 };
+constexpr int MAX_RADICES = 16;
+
+template <typename T> struct cpx { T x, y; };
+
+template <typename T> __device__ __forceinline__ cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {   // a * conj(b)
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ cpx<T> conj_(cpx<T> a) { return mk(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return mk(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot90(cpx<T> a) {
+    return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Tables of one uniform direction (device pointers, built by the plan on the
+// host in FP64 and rounded once for the FP32 copies).
+// ---------------------------------------------------------------------------
+template <typename T> struct DirTab {
+    int n, kind, L, nrad;
+    int radix[MAX_RADICES];
+    const cpx<T>* tw;     // W_L^t = exp(-2 pi i t / L), t in [0, L)
+    const cpx<T>* post;   // W_n^m = exp(-2 pi i m / n), m in [0, L]
+    const cpx<T>* mak;    // exp(-i pi m / (2n)),        m in [0, L]
+};
+
+// ---------------------------------------------------------------------------
+// Radix butterflies (forward: exp(-2 pi i / R); inverse: conjugate)
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV> struct Bfly;
+
+template <typename T, bool INV> struct Bfly<T, 2, INV> {
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        cpx<T> a = v[0], b = v[1];
+        v[0] = a + b; v[1] = a - b;
+    }
+};
+
+template <typename T, bool INV> struct Bfly<T, 4, INV> {
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        cpx<T> s02 = v[0] + v[2], d02 = v[0] - v[2];
+        cpx<T> s13 = v[1] + v[3], d13 = rot90<T, INV>(v[1] - v[3]);
+        v[0] = s02 + s13; v[2] = s02 - s13;
+        v[1] = d02 + d13; v[3] = d02 - d13;
+    }
+};
+
+template <typename T, bool INV> struct Bfly<T, 3, INV> {
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        const T h = T(0.5), s3 = T(0.86602540378443864676372317075294);
+        cpx<T> t = v[1] + v[2];
+        cpx<T> d = scale(rot90<T, INV>(v[1] - v[2]), s3);
+        cpx<T> m = v[0] - scale(t, h);
+        v[0] = v[0] + t; v[1] = m + d; v[2] = m - d;
+    }
+};
+
+template <typename T, bool INV> struct Bfly<T, 5, INV> {
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        const T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi / 5)
+        const T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi / 5)
+        const T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi / 5)
+        const T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi / 5)
+        cpx<T> t1 = v[1] + v[4], t2 = v[2] + v[3];
+        cpx<T> d1 = v[1] - v[4], d2 = v[2] - v[3];
+        cpx<T> a = v[0] + scale(t1, c1) + scale(t2, c2);
+        cpx<T> b = v[0] + scale(t1, c2) + scale(t2, c1);
+        cpx<T> e = rot90<T, INV>(scale(d1, s1) + scale(d2, s2));
+        cpx<T> f = rot90<T, INV>(scale(d1, s2) - scale(d2, s1));
+        v[0] = v[0] + t1 + t2;
+        v[1] = a + e; v[4] = a - e;
+        v[2] = b + f; v[3] = b - f;
+    }
+};
+
+template <typename T, bool INV> struct Bfly<T, 8, INV> {
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        const T r2 = T(0.70710678118654752440084436210485);
+        cpx<T> a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) { a[r] = v[r] + v[r + 4]; b[r] = v[r] - v[r + 4]; }
+        // b[r] *= W8^r
+        b[1] = INV ? mk(r2 * (b[1].x - b[1].y), r2 * (b[1].x + b[1].y))
+                   : mk(r2 * (b[1].x + b[1].y), r2 * (b[1].y - b[1].x));
+        b[2] = rot90<T, INV>(b[2]);
+        b[3] = INV ? mk(-r2 * (b[3].x + b[3].y), r2 * (b[3].x - b[3].y))
+                   : mk(r2 * (b[3].y - b[3].x), -r2 * (b[3].x + b[3].y));
+        Bfly<T, 4, INV>::run(a);
+        Bfly<T, 4, INV>::run(b);
+        v[0] = a[0]; v[2] = a[1]; v[4] = a[2]; v[6] = a[3];
+        v[1] = b[0]; v[3] = b[1]; v[5] = b[2]; v[7] = b[3];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// One Stockham autosort pass of radix R over a set of lines in shared memory
+// (Govindaraju et al., SC'08 formulation): reads element j + r*L/R, applies
+// the twiddles of sub-transform position k = j mod Ns, writes to
+// (j - k)*R + k + r*Ns.  Lines: element e of line l at l*ls + e*es.
+// LINES_FAST maps consecutive threads to consecutive lines (column tiles).
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV, bool LINES_FAST>
+__device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                              int L, int Ns, int nlines, int ls, int es,
+                                              const cpx<T>* __restrict__ tw) {
+    const int nb = L / R;
+    const int total = nb * nlines;
+    const int tstep = L / (Ns * R);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int line, j;
+        if (LINES_FAST) { j = idx / nlines; line = idx - j * nlines; }
+        else            { line = idx / nb;  j = idx - line * nb; }
+        const cpx<T>* s = src + line * ls;
+        cpx<T>* d = dst + line * ls;
+        const int k = j % Ns;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                cpx<T> w = tw[r * k * tstep];
+                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            }
+        }
+        Bfly<T, R, INV>::run(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[(base + r * Ns) * es] = v[r];
+    }
+}
+
+// All passes of a length-L FFT; returns the buffer holding the result.
+template <typename T, bool INV, bool LINES_FAST>
+__device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es) {
+    int Ns = 1;
+    cpx<T>* src = b0;
+    cpx<T>* dst = b1;
+    for (int p = 0; p < t.nrad; ++p) {
+        const int R = t.radix[p];
+        switch (R) {
+            case 8: stockham_pass<T, 8, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+            case 4: stockham_pass<T, 4, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+            case 2: stockham_pass<T, 2, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+            case 3: stockham_pass<T, 3, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+            default: stockham_pass<T, 5, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+        }
+        __syncthreads();
+        Ns *= R;
+        cpx<T>* tmp = src; src = dst; dst = tmp;
+    }
+    return src;
+}
+
+// Position of input sample s in the packed sequence v (Makhoul reordering for
+// N and D; identity for P) and its sign (-1)^s for D.
+__device__ __forceinline__ int pack_index(int kind, int n, int s) {
+    if (kind == KIND_P) return s;
+    return (s & 1) ? (n - 1 - (s >> 1)) : (s >> 1);
+}
+
+template <typename T> __device__ __forceinline__ T pack_sign(int kind, int s) {
+    return (kind == KIND_D && (s & 1)) ? T(-1) : T(1);
+}
+
+// Forward post-processing of mode m in [0, L] of one line: Z is the length-L
+// FFT of the packed pairs, the outputs go to the real buffer `out` (element q
+// of the line at out[q*es_r]).
+template <typename T>
+__device__ __forceinline__ void post_forward(const cpx<T>* Z, int zes, T* out, int oes, const DirTab<T>& t, int m) {
+    const int L = t.L, n = t.n;
+    cpx<T> zm = Z[(m == L ? 0 : m) * zes];
+    cpx<T> zc = conj_(Z[(m == 0 ? 0 : L - m) * zes]);
+    cpx<T> e = scale(zm + zc, T(0.5));
+    cpx<T> dd = zm - zc;
+    cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);            // (zm - zc) / (2i)
+    cpx<T> v = e + cmul(t.post[m], o);
+    if (t.kind == KIND_P) {
+        out[m * oes] = v.x;
+        if (m > 0 && m < L) out[(n - m) * oes] = v.y;
+    } else {
+        cpx<T> u = cmul(t.mak[m], v);
+        if (t.kind == KIND_N) {
+            out[m * oes] = u.x;
+            if (m > 0 && m < L) out[(n - m) * oes] = -u.y;
+        } else {
+            out[(n - 1 - m) * oes] = u.x;
+            if (m > 0 && m < L) out[(m - 1) * oes] = -u.y;
+        }
+    }
+}
+
+// V_m of the inverse (m in [0, L]) from the real coefficients X of one line.
+template <typename T>
+__device__ __forceinline__ cpx<T> inv_spectrum(const T* X, int xes, const DirTab<T>& t, int m) {
+    const int L = t.L, n = t.n;
+    if (t.kind == KIND_P) {
+        T im = (m > 0 && m < L) ? X[(n - m) * xes] : T(0);
+        return mk(X[m * xes], im);
+    }
+    cpx<T> u;
+    if (t.kind == KIND_N) u = mk(X[m * xes], m > 0 ? -X[(n - m) * xes] : T(0));
+    else                  u = mk(X[(n - 1 - m) * xes], m > 0 ? -X[(m - 1) * xes] : T(0));
+    return cmulc(u, t.mak[m]);   // exp(+i pi m / (2n)) * U_m
+}
+
+// Inverse pre-processing: Z_m (m in [0, L)) whose unnormalised inverse FFT
+// gives n * (x[2j] + i x[2j+1]) of the packed sequence.
+template <typename T>
+__device__ __forceinline__ cpx<T> pre_inverse(const T* X, int xes, const DirTab<T>& t, int m) {
+    cpx<T> vm = inv_spectrum(X, xes, t, m);
+    cpx<T> vc = conj_(inv_spectrum(X, xes, t, t.L - m));
+    cpx<T> s = vm + vc;
+    cpx<T> d = cmulc(vm - vc, t.post[m]);        // (vm - vc) * exp(+2 pi i m / n)
+    return mk(s.x - d.y, s.y + d.x);             // s + i d
+}
+
+}  // namespace cales

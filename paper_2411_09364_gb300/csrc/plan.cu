@@ -1,0 +1,462 @@
+// Plan construction and solve orchestration behind the C ABI (cales.h).
+//
+// A plan holds, per uniform direction, the FFT length L = n/2, its radix
+// factorisation and the twiddle / post-processing / eigenvalue tables
+// (computed on the host in FP64 with exact integer argument reduction, FP32
+// copies rounded once), and along z the tridiagonal couplings 1/(dzc dzf).
+// A solve is five launches on the caller's stream:
+//   x forward -> y forward -> z tridiagonal per mode -> y inverse -> x inverse
+// FP32_REFINE adds per sweep an FP64 residual and a second FP32 pass whose
+// last kernel accumulates the correction into the FP64 solution.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cales.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+using namespace cales;
+
+namespace {
+
+// cos and sin of 2 pi num / den with exact integer quadrant reduction.
+void cis_frac(long num, long den, double& c, double& s) {
+    long r = num % den;
+    if (r < 0) r += den;
+    const long q = (4 * r) / den;
+    const long rem = 4 * r - q * den;
+    const double a = 1.5707963267948966192313216916398 * (double)rem / (double)den;
+    const double ca = std::cos(a), sa = std::sin(a);
+    switch (q & 3) {
+        case 0: c = ca; s = sa; break;
+        case 1: c = -sa; s = ca; break;
+        case 2: c = -ca; s = -sa; break;
+        default: c = sa; s = -ca; break;
+    }
+}
+
+bool factorize(int L, int* radix, int& nrad) {
+    nrad = 0;
+    int m = L;
+    int twos = 0;
+    while (m % 2 == 0) { m /= 2; ++twos; }
+    while (twos >= 3) { radix[nrad++] = 8; twos -= 3; }
+    if (twos == 2) radix[nrad++] = 4;
+    if (twos == 1) radix[nrad++] = 2;
+    while (m % 5 == 0) { m /= 5; radix[nrad++] = 5; }
+    while (m % 3 == 0) { m /= 3; radix[nrad++] = 3; }
+    return m == 1 && nrad <= MAX_RADICES;
+}
+
+template <typename T> T* dev_upload(const std::vector<T>& h, std::vector<void*>& owned) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, h.size() * sizeof(T) + 16) != cudaSuccess) return nullptr;
+    cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    owned.push_back(p);
+    return reinterpret_cast<T*>(p);
+}
+
+int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) {
+    d.n = n;
+    d.kind = kind;
+    if (n > 1 && (n % 2)) return CALES_EUNSUPPORTED;
+    d.L = n >= 2 ? n / 2 : 1;
+    if (!factorize(d.L, d.radix, d.nrad)) return CALES_EUNSUPPORTED;
+    const int L = d.L;
+    std::vector<double2> tw(L), post(L + 1), mak(L + 1);
+    std::vector<float2> twf(L), postf(L + 1), makf(L + 1);
+    for (int t = 0; t < L; ++t) {
+        double c, s;
+        cis_frac(t, L, c, s);
+        tw[t] = make_double2(c, -s);
+    }
+    for (int m = 0; m <= L; ++m) {
+        double c, s;
+        cis_frac(m, n >= 2 ? n : 1, c, s);
+        post[m] = make_double2(c, -s);
+        cis_frac(m, 4L * (n >= 1 ? n : 1), c, s);
+        mak[m] = make_double2(c, -s);
+    }
+    std::vector<double> lam(n);
+    std::vector<float> lamf(n);
+    const double pi = 3.14159265358979323846;
+    for (int q = 0; q < n; ++q) {
+        double sv;
+        if (kind == KIND_P) {
+            const int m = q <= n / 2 ? q : n - q;
+            sv = std::sin(pi * m / n);
+        } else if (kind == KIND_N) {
+            sv = std::sin(pi * q / (2.0 * n));
+        } else {
+            sv = std::sin(pi * (q + 1) / (2.0 * n));
+        }
+        lam[q] = -(4.0 / (h * h)) * sv * sv;
+        lamf[q] = (float)lam[q];
+    }
+    for (int i = 0; i < L; ++i) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+    for (int i = 0; i <= L; ++i) {
+        postf[i] = make_float2((float)post[i].x, (float)post[i].y);
+        makf[i] = make_float2((float)mak[i].x, (float)mak[i].y);
+    }
+    d.tw_d = dev_upload(tw, owned);
+    d.post_d = dev_upload(post, owned);
+    d.mak_d = dev_upload(mak, owned);
+    d.lam_d = dev_upload(lam, owned);
+    d.tw_f = dev_upload(twf, owned);
+    d.post_f = dev_upload(postf, owned);
+    d.mak_f = dev_upload(makf, owned);
+    d.lam_f = dev_upload(lamf, owned);
+    if (!d.tw_d || !d.post_d || !d.mak_d || !d.lam_d || !d.tw_f || !d.post_f || !d.mak_f || !d.lam_f)
+        return CALES_ENOMEM;
+    return CALES_OK;
+}
+
+}  // namespace
+
+template <> DirTab<double> DirHost::tab<double>() const {
+    DirTab<double> t;
+    t.n = n; t.kind = kind; t.L = L; t.nrad = nrad;
+    for (int i = 0; i < MAX_RADICES; ++i) t.radix[i] = i < nrad ? radix[i] : 1;
+    t.tw = reinterpret_cast<const cpx<double>*>(tw_d);
+    t.post = reinterpret_cast<const cpx<double>*>(post_d);
+    t.mak = reinterpret_cast<const cpx<double>*>(mak_d);
+    return t;
+}
+
+template <> DirTab<float> DirHost::tab<float>() const {
+    DirTab<float> t;
+    t.n = n; t.kind = kind; t.L = L; t.nrad = nrad;
+    for (int i = 0; i < MAX_RADICES; ++i) t.radix[i] = i < nrad ? radix[i] : 1;
+    t.tw = reinterpret_cast<const cpx<float>*>(tw_f);
+    t.post = reinterpret_cast<const cpx<float>*>(post_f);
+    t.mak = reinterpret_cast<const cpx<float>*>(mak_f);
+    return t;
+}
+
+namespace cales {
+
+template <typename T> int rows_per_cta(int n) {
+    const size_t per_row = 2 * (size_t)(n >= 2 ? n : 2) * sizeof(T);
+    int rpc = (int)((48 * 1024) / per_row);
+    if (rpc < 1) rpc = 1;
+    if (rpc > 16) rpc = 16;
+    return rpc;
+}
+
+template <typename T> int choose_tm(int nz) {
+    const int CK = 16;
+    const int nck = (nz + CK - 1) / CK;
+    const int cands[5] = {128, 64, 32, 16, 8};
+    for (int i = 0; i < 5; ++i) {
+        const size_t sm = ((size_t)nz * cands[i] + (size_t)nck * cands[i] + 2 * (size_t)nz) * sizeof(T);
+        if (sm <= 100 * 1024) return cands[i];
+    }
+    for (int i = 2; i < 5; ++i) {
+        const size_t sm = ((size_t)nz * cands[i] + (size_t)nck * cands[i] + 2 * (size_t)nz) * sizeof(T);
+        if (sm <= 220 * 1024) return cands[i];
+    }
+    return 0;
+}
+
+template <typename T> int choose_tx(int ny) {
+    const int cands[3] = {sizeof(T) == 8 ? 16 : 32, sizeof(T) == 8 ? 8 : 16, sizeof(T) == 8 ? 4 : 8};
+    for (int i = 0; i < 3; ++i)
+        if ((size_t)2 * cands[i] * (ny >= 2 ? ny : 2) * sizeof(T) <= 160 * 1024) return cands[i];
+    return 0;
+}
+
+// One pass of the solver: in (TIn) -> work (T, mode space) -> out (TOut).
+template <typename T, typename TIn, typename TOut, bool ACC>
+int pipeline(cales_plan_s* P, const void* in, void* out, T* work, double sigma, double alpha, double scale,
+             bool singular, bool adjoint, double shift, cudaStream_t st) {
+    const long nrows = (long)P->ny * P->nz;
+    RowArgs<T> ra;
+    ra.t = P->X.tab<T>();
+    ra.in = in;
+    ra.out = work;
+    ra.nrows = nrows;
+    ra.rpc = rows_per_cta<T>(P->nx);
+    ra.in_scale = 1.0;
+    ra.shift = 0.0;
+    P->prof_begin(st, "x_fwd");
+    if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+
+    ColArgs<T> ca;
+    ca.t = P->Y.tab<T>();
+    ca.data = work;
+    ca.nx = P->nx;
+    ca.nplanes = P->nz;
+    ca.tx = choose_tx<T>(P->ny);
+    if (P->ny > 1) {
+        P->prof_begin(st, "y_fwd");
+        if (launch_cols<T>(ca, false, st) != cudaSuccess) return CALES_ECUDA;
+        P->prof_end(st);
+    }
+
+    ZArgs<T> za;
+    za.data = work;
+    za.lamx = sizeof(T) == 8 ? (const T*)P->X.lam_d : (const T*)P->X.lam_f;
+    za.lamy = sizeof(T) == 8 ? (const T*)P->Y.lam_d : (const T*)P->Y.lam_f;
+    za.za = sizeof(T) == 8 ? (const T*)P->za_d : (const T*)P->za_f;
+    za.zc = sizeof(T) == 8 ? (const T*)P->zc_d : (const T*)P->zc_f;
+    za.dzf = P->dzf_d;
+    za.nx = P->nx; za.ny = P->ny; za.nz = P->nz;
+    za.zlo = P->bc[4]; za.zhi = P->bc[5];
+    za.singular = singular ? 1 : 0;
+    za.adjoint = adjoint ? 1 : 0;
+    za.tm = choose_tm<T>(P->nz);
+    za.sigma = T(sigma); za.alpha = T(alpha); za.scale = T(scale);
+    za.status = P->status;
+    P->prof_begin(st, "z_solve");
+    if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+
+    if (P->ny > 1) {
+        P->prof_begin(st, "y_inv");
+        if (launch_cols<T>(ca, true, st) != cudaSuccess) return CALES_ECUDA;
+        P->prof_end(st);
+    }
+
+    RowArgs<T> ri = ra;
+    ri.in = work;
+    ri.out = out;
+    ri.shift = shift;
+    P->prof_begin(st, ACC ? "x_inv_acc" : "x_inv");
+    if (launch_rows_inverse<T, TOut, ACC>(ri, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+    return CALES_OK;
+}
+
+}  // namespace cales
+
+// ---------------------------------------------------------------------------
+// profiling hooks (CUDA events around each launch when enabled)
+// ---------------------------------------------------------------------------
+void cales_plan_s::prof_begin(cudaStream_t st, const char* name) {
+    if (!prof_on || prof_n >= PROF_MAX) return;
+    ProfRec& r = prof[prof_n];
+    if (!r.a) { cudaEventCreate(&r.a); cudaEventCreate(&r.b); }
+    r.name = name;
+    cudaEventRecord(r.a, st);
+}
+
+void cales_plan_s::prof_end(cudaStream_t st) {
+    if (!prof_on || prof_n >= PROF_MAX) return;
+    cudaEventRecord(prof[prof_n].b, st);
+    ++prof_n;
+}
+
+static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {
+    if (!P || !f || !p) return CALES_EINVAL;
+    if (helm && !(alpha > 0.0)) return CALES_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double nxy = (double)P->nx * (double)P->ny;
+    const double sigma = helm ? 1.0 : 0.0;
+    const double a = helm ? alpha : 1.0;
+    const double scale = (helm ? 1.0 : -1.0) / nxy;
+    const bool sing = !helm && P->singular_poisson;
+    P->prof_n = 0;
+    switch (P->precision) {
+        case CALES_FP64:
+            return pipeline<double, double, double, false>(P, f, p, (double*)p, sigma, a, scale, sing, adjoint, 0.0, st);
+        case CALES_FP32:
+            return pipeline<float, float, float, false>(P, f, p, (float*)p, sigma, a, scale, sing, adjoint, 0.0, st);
+        case CALES_FP32_REFINE: {
+            if (adjoint) return CALES_EUNSUPPORTED;
+            if (f == p || !P->work) return CALES_EINVAL;
+            int rc = pipeline<float, double, double, false>(P, f, p, P->work, sigma, a, scale, sing, false, 0.0, st);
+            if (rc) return rc;
+            for (int s = 0; s < P->sweeps; ++s) {
+                ResidArgs ra;
+                P->fill_resid(ra, (const double*)p, (const double*)f, P->work, false, helm ? 1.0 : 0.0, helm ? -alpha : 1.0);
+                P->prof_begin(st, "residual");
+                if (launch_residual(ra, st) != cudaSuccess) return CALES_ECUDA;
+                P->prof_end(st);
+                rc = pipeline<float, float, double, true>(P, P->work, p, P->work, sigma, a, scale, sing, false, 0.0, st);
+                if (rc) return rc;
+            }
+            return CALES_OK;
+        }
+        default:
+            return CALES_EINVAL;
+    }
+}
+
+void cales_plan_s::fill_resid(cales::ResidArgs& ra, const double* u, const double* f, void* r, bool r_double,
+                              double c0, double c1) const {
+    ra.u = u;
+    ra.f = f;
+    ra.r = r;
+    ra.r_is_double = r_double ? 1 : 0;
+    ra.nx = nx; ra.ny = ny; ra.nz = nz;
+    ra.bcx = bc[0]; ra.bcy = bc[2]; ra.zlo = bc[4]; ra.zhi = bc[5];
+    ra.idx2 = 1.0 / (dx * dx);
+    ra.idy2 = 1.0 / (dy * dy);
+    ra.za = za_d;
+    ra.zc = zc_d;
+    ra.c0 = c0;
+    ra.c1 = c1;
+    ra.fshift = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], double dx, double dy,
+               const double* dzc, const double* dzf) {
+    if (!out || !bc || !dzc || !dzf) return CALES_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0)) return CALES_EINVAL;
+    if ((long)nx * ny * nz > (1L << 34)) return CALES_EINVAL;
+    for (int i = 0; i < 6; ++i)
+        if (bc[i] < 0 || bc[i] > 3) return CALES_EINVAL;
+    if (bc[0] != bc[1] || bc[2] != bc[3]) return (bc[0] == 0 || bc[1] == 0 || bc[2] == 0 || bc[3] == 0) ? CALES_EINVAL : CALES_EUNSUPPORTED;
+    if (bc[0] == CALES_BC_DF || bc[2] == CALES_BC_DF) return CALES_EUNSUPPORTED;
+    if (bc[4] == CALES_BC_P || bc[5] == CALES_BC_P) return CALES_EUNSUPPORTED;
+    for (int k = 0; k <= nz; ++k)
+        if (!(dzc[k] > 0) || !std::isfinite(dzc[k])) return CALES_EINVAL;
+    for (int k = 0; k < nz; ++k)
+        if (!(dzf[k] > 0) || !std::isfinite(dzf[k])) return CALES_EINVAL;
+
+    cales_plan_s* P = new (std::nothrow) cales_plan_s();
+    if (!P) return CALES_ENOMEM;
+    P->nx = nx; P->ny = ny; P->nz = nz;
+    for (int i = 0; i < 6; ++i) P->bc[i] = bc[i];
+    P->dx = dx; P->dy = dy;
+    P->singular_poisson = (bc[0] != CALES_BC_D && bc[2] != CALES_BC_D && bc[4] == CALES_BC_N && bc[5] == CALES_BC_N) ? 1 : 0;
+    int rc = build_dir(P->X, nx, bc[0], dx, P->owned);
+    if (rc == CALES_OK) rc = build_dir(P->Y, ny, bc[2], dy, P->owned);
+    if (rc == CALES_OK) {
+        if (rows_per_cta<double>(nx) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || choose_tm<double>(nz) == 0 ||
+            choose_tx<double>(ny) == 0)
+            rc = CALES_EUNSUPPORTED;
+    }
+    if (rc == CALES_OK) {
+        std::vector<double> za(nz), zc(nz), df(dzf, dzf + nz);
+        std::vector<float> zaf(nz), zcf(nz);
+        for (int k = 0; k < nz; ++k) {
+            za[k] = 1.0 / (dzc[k] * dzf[k]);
+            zc[k] = 1.0 / (dzc[k + 1] * dzf[k]);
+            zaf[k] = (float)za[k];
+            zcf[k] = (float)zc[k];
+        }
+        P->za_d = dev_upload(za, P->owned);
+        P->zc_d = dev_upload(zc, P->owned);
+        P->dzf_d = dev_upload(df, P->owned);
+        P->za_f = dev_upload(zaf, P->owned);
+        P->zc_f = dev_upload(zcf, P->owned);
+        std::vector<int> st(4, 0);
+        P->status = dev_upload(st, P->owned);
+        if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status) rc = CALES_ENOMEM;
+    }
+    if (rc == CALES_OK && cudaDeviceSynchronize() != cudaSuccess) rc = CALES_ECUDA;
+    if (rc != CALES_OK) {
+        cales_destroy(P);
+        return rc;
+    }
+    P->precision = CALES_FP64;
+    P->sweeps = 2;
+    const char* pe = getenv("CALES_PROFILE");
+    P->prof_on = pe && pe[0] == '1';
+    *out = P;
+    return CALES_OK;
+}
+
+int cales_set_precision(cales_plan_t P, int mode, int sweeps) {
+    if (!P || mode < 0 || mode > 2 || sweeps < 0 || sweeps > 8) return CALES_EINVAL;
+    if (mode == CALES_FP32_REFINE && !P->work) {
+        void* w = nullptr;
+        const size_t bytes = (size_t)P->nx * P->ny * P->nz * sizeof(float);
+        if (cudaMalloc(&w, bytes) != cudaSuccess) return CALES_ENOMEM;
+        P->work = reinterpret_cast<float*>(w);
+    }
+    P->precision = mode;
+    P->sweeps = sweeps;
+    return CALES_OK;
+}
+
+int cales_poisson_solve(cales_plan_t P, const void* f, void* p, void* stream) {
+    return solve_common(P, false, 0.0, false, f, p, stream);
+}
+
+int cales_helmholtz_solve(cales_plan_t P, double alpha, const void* f, void* u, void* stream) {
+    return solve_common(P, true, alpha, false, f, u, stream);
+}
+
+int cales_poisson_solve_adjoint(cales_plan_t P, const void* w, void* g, void* stream) {
+    return solve_common(P, false, 0.0, true, w, g, stream);
+}
+
+int cales_helmholtz_solve_adjoint(cales_plan_t P, double alpha, const void* w, void* g, void* stream) {
+    return solve_common(P, true, alpha, true, w, g, stream);
+}
+
+int cales_residual(cales_plan_t P, double alpha, const double* u, const double* f, double* r, void* stream) {
+    if (!P || !u || !f || !r) return CALES_EINVAL;
+    ResidArgs ra;
+    const bool helm = alpha >= 0.0;
+    P->fill_resid(ra, u, f, r, true, helm ? 1.0 : 0.0, helm ? -alpha : 1.0);
+    if (launch_residual(ra, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return CALES_ECUDA;
+    return CALES_OK;
+}
+
+int cales_get_status(cales_plan_t P, int* device_status) {
+    if (!P || !device_status) return CALES_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return CALES_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CALES_ECUDA;
+    cudaMemset(P->status, 0, sizeof(int));
+    *device_status = v;
+    return CALES_OK;
+}
+
+const char* cales_strerror(int code) {
+    switch (code) {
+        case CALES_OK: return "ok";
+        case CALES_EINVAL: return "invalid argument";
+        case CALES_EUNSUPPORTED: return "unsupported size or boundary combination";
+        case CALES_ENOMEM: return "device allocation failed";
+        case CALES_ECUDA: return "CUDA runtime error";
+        default: return "unknown error";
+    }
+}
+
+void cales_destroy(cales_plan_t P) {
+    if (!P) return;
+    for (void* p : P->owned) cudaFree(p);
+    if (P->work) cudaFree(P->work);
+    for (int i = 0; i < cales_plan_s::PROF_MAX; ++i) {
+        if (P->prof[i].a) { cudaEventDestroy(P->prof[i].a); cudaEventDestroy(P->prof[i].b); }
+    }
+    delete P;
+}
+
+// Per-kernel timings of the last solve when profiling is on (CALES_PROFILE=1
+// or cales_profile_enable).  Synchronises.  Returns the number of records.
+int cales_profile_enable(cales_plan_t P, int on) {
+    if (!P) return CALES_EINVAL;
+    P->prof_on = on != 0;
+    P->prof_n = 0;
+    return CALES_OK;
+}
+
+int cales_profile_read(cales_plan_t P, int max, const char** names, float* ms) {
+    if (!P) return CALES_EINVAL;
+    cudaDeviceSynchronize();
+    const int n = P->prof_n < max ? P->prof_n : max;
+    for (int i = 0; i < n; ++i) {
+        names[i] = P->prof[i].name;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, P->prof[i].a, P->prof[i].b);
+        ms[i] = t;
+    }
+    return n;
+}
+
+}  // extern "C"

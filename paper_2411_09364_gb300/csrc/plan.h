@@ -1,0 +1,51 @@
+// Host-side plan object behind the opaque cales_plan_t handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kernels.cuh"
+
+struct DirHost {
+    int n = 1, kind = 0, L = 1, nrad = 0;
+    int radix[cales::MAX_RADICES] = {0};
+    double2* tw_d = nullptr;
+    double2* post_d = nullptr;
+    double2* mak_d = nullptr;
+    double* lam_d = nullptr;
+    float2* tw_f = nullptr;
+    float2* post_f = nullptr;
+    float2* mak_f = nullptr;
+    float* lam_f = nullptr;
+    template <typename T> cales::DirTab<T> tab() const;
+};
+
+struct ProfRec {
+    const char* name = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct cales_plan_s {
+    int nx = 0, ny = 0, nz = 0;
+    int bc[6] = {0};
+    double dx = 0, dy = 0;
+    int singular_poisson = 0;
+    DirHost X, Y;
+    double* za_d = nullptr;
+    double* zc_d = nullptr;
+    double* dzf_d = nullptr;
+    float* za_f = nullptr;
+    float* zc_f = nullptr;
+    int* status = nullptr;
+    int precision = 0, sweeps = 2;
+    float* work = nullptr;
+    std::vector<void*> owned;
+    static constexpr int PROF_MAX = 64;
+    bool prof_on = false;
+    int prof_n = 0;
+    ProfRec prof[PROF_MAX];
+    void prof_begin(cudaStream_t st, const char* name);
+    void prof_end(cudaStream_t st);
+    void fill_resid(cales::ResidArgs& ra, const double* u, const double* f, void* r, bool r_double, double c0,
+                    double c1) const;
+};

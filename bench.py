@@ -1,0 +1,336 @@
+"""Benchmark of the fast direct Poisson solver on one GB300 (or N replicas).
+
+Workload: duct Poisson problem 1536 x 512 x 512 (periodic x with Lx = 6,
+Neumann y walls with Ly = 2 -> DCT-II, Neumann z walls with Lz = 2 stretched
+by tanh(beta = 1.5)); seeded Gaussian right-hand side with its dzf-weighted
+mean removed.  One step = one Poisson solve in FP32 with double-float
+refinement (the default 2 sweeps) of a resident 3.2 GB FP64 right-hand side
+into a resident FP64 solution; the plain FP64 GPU solve is timed beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth_inputs as S  # noqa: E402
+
+WORKLOAD = dict(name="duct_poisson_1536x512x512", nx=1536, ny=512, nz=512, bc=(0, 0, 1, 1, 1, 1),
+                lx=6.0, ly=2.0, lz=2.0, beta=1.5, seed=3000)
+# oracle sample of the same family for the CPU baseline / reference arm
+SAMPLE = dict(nx=384, ny=128, nz=128)
+METRIC = "Gpoints/s per Poisson solve (FP32 + double-float refinement, rel err <= 1e-10 vs FP64)"
+UNIT = "Gpoints/s"
+# algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
+KERNEL_BYTES_PER_POINT = {
+    "x_fwd": 12.0,       # read f (FP64 8 B) or r (FP32 4 B, sweeps: see below), write 4 B
+    "x_fwd_sweep": 8.0,
+    "y_fwd": 8.0, "y_inv": 8.0, "z_solve": 8.0,
+    "x_inv": 12.0,       # read 4 B, write the (hi, lo) pair 8 B
+    "x_inv_acc": 20.0,   # read 4 B + pair 8 B, write 8 B
+    "residual": 20.0,    # read f 8 B + pair 8 B, write r 4 B
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def grid_arrays(w=WORKLOAD, nx=None, ny=None, nz=None):
+    nx, ny, nz = nx or w["nx"], ny or w["ny"], nz or w["nz"]
+    zf = S.tanh_faces(nz, w["beta"], w["lz"])
+    return nx, ny, nz, zf
+
+
+def make_rhs(nx, ny, nz, zf, seed):
+    f = S.gaussian(seed, (nz, ny, nx))
+    return S.remove_mean(f, np.diff(zf))
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    nx, ny, nz = SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"]
+    w = WORKLOAD
+    zf = S.tanh_faces(nz, w["beta"], w["lz"])
+    dzc, dzf = O.cell_spacings(zf)
+    g = O.Grid(nx, ny, nz, w["lx"] / nx, w["ly"] / ny, dzc, dzf, w["bc"])
+    f = make_rhs(nx, ny, nz, zf, w["seed"])
+    for _ in range(args.warmup):
+        O.solve(f, g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve(f, g)
+    dt = time.perf_counter() - t0
+    npts = nx * ny * nz
+    val = npts * args.steps / dt / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "sample": f"{nx}x{ny}x{nz}"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle solve of the same duct family at {nx}x{ny}x{nz} per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg():
+    """The oracle as it stands, timed on a bounded sample (about 10-30 s of CPU work)."""
+    import oracle as O
+    nx, ny, nz = SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"]
+    w = WORKLOAD
+    zf = S.tanh_faces(nz, w["beta"], w["lz"])
+    dzc, dzf = O.cell_spacings(zf)
+    g = O.Grid(nx, ny, nz, w["lx"] / nx, w["ly"] / ny, dzc, dzf, w["bc"])
+    f = make_rhs(nx, ny, nz, zf, w["seed"])
+    O.solve(f, g)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        O.solve(f, g)
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 20:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": nx * ny * nz / dt / 1e9, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"FP64 oracle solve of the same duct family at {nx}x{ny}x{nz}, "
+                                        f"{reps} repetitions ({dt:.2f} s each)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cales", choices=["cales", "reference"])
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="512x256x192 channel variant (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2411_09364_gb300 import solver as cs
+
+    w = dict(WORKLOAD)
+    if args.small:
+        w.update(name="channel_poisson_512x256x192", nx=512, ny=256, nz=192, bc=(0, 0, 0, 0, 1, 1),
+                 lx=2 * math.pi, ly=math.pi, beta=1.8)
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    npts = nx * ny * nz
+    zf = S.tanh_faces(nz, w["beta"], w["lz"])
+    dzc, dzf = cs.cell_spacings(zf)
+    plan = cs.Plan(nx, ny, nz, w["bc"], w["lx"] / nx, w["ly"] / ny, dzc, dzf, cs.FP32_REFINE, args.sweeps)
+    f_host = torch.from_numpy(make_rhs(nx, ny, nz, zf, w["seed"] + rank))
+    f = f_host.to(dev)
+    p = torch.empty_like(f)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # --- device-resident timing (FP32 + refinement) --------------------------
+    for _ in range(args.warmup):
+        plan.poisson(f, p)
+    plan.profile(True)
+    barrier()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.poisson(f, p)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    prof = plan.profile_read()
+    plan.profile(False)
+    p_ref = p.clone()
+
+    # --- per-kernel breakdown and roofline of the dominant kernel ------------
+    tot, cnt = {}, {}
+    prev = None
+    for name, t in prof:
+        key = "x_fwd_sweep" if (name == "x_fwd" and prev == "residual") else name
+        prev = name
+        tot[key] = tot.get(key, 0.0) + t
+        cnt[key] = cnt.get(key, 0) + 1
+    launches_per_step = len(prof) / args.steps if prof else 0
+    dom = max(tot, key=tot.get) if tot else None
+    hbm, src = peaks()
+    roof = None
+    if dom:
+        avg_ms = tot[dom] / cnt[dom]
+        bytes_per_launch = KERNEL_BYTES_PER_POINT.get(dom, 8.0) * npts
+        ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+        traffic = None
+        try:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+                traffic = json.load(fh).get(w["name"], {}).get(dom)
+        except Exception:
+            traffic = None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "peak_source": src,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+                "bytes_per_launch": bytes_per_launch, "avg_ms": avg_ms}
+    per_kernel = {k: {"ms_per_step": tot[k] / args.steps, "launches_per_step": cnt[k] / args.steps,
+                      "GB/s": KERNEL_BYTES_PER_POINT.get(k, 8.0) * npts / (tot[k] / cnt[k] * 1e-3) / 1e9}
+                  for k in tot}
+
+    # --- plain FP64 GPU solve beside it --------------------------------------
+    plan.set_precision(cs.FP64)
+    p64 = torch.empty_like(f)
+    plan.poisson(f, p64)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.fp64_steps):
+        plan.poisson(f, p64)
+    ev1.record(stream)
+    barrier()
+    ms64 = max_over_ranks(ev0.elapsed_time(ev1) / args.fp64_steps)
+    rel = float(torch.linalg.vector_norm(p_ref - p64) / torch.linalg.vector_norm(p64))
+    plan.set_precision(cs.FP32_REFINE, args.sweeps)
+
+    # --- end to end through the C ABI with host buffers ----------------------
+    f_pin = f_host.pin_memory()
+    p_pin = torch.empty_like(f_pin).pin_memory()
+    fd = torch.empty_like(f)
+    pd = torch.empty_like(f)
+    for _ in range(1):
+        fd.copy_(f_pin, non_blocking=True)
+        plan.poisson(fd, pd)
+        p_pin.copy_(pd, non_blocking=True)
+    barrier()
+    ev0.record(stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        fd.copy_(f_pin, non_blocking=True)
+        plan.poisson(fd, pd)
+        p_pin.copy_(pd, non_blocking=True)
+    ev1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / e2e_steps)
+    status = plan.status()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": npts * world / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "bc": "P x, N y (DCT-II), N z tanh",
+                   "precision": f"FP32 solves + {args.sweeps} double-float refinement sweeps",
+                   "l2": "inputs larger than L2 (f and p 3.2 GB each), no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": npts * world / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64, "unit": UNIT},
+        "rel_err_refine_vs_fp64_gpu": rel,
+        "device_status": status,
+        "e2e": {"value": npts * world / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": f.numel() * 8, "d2h_bytes_per_step": p.numel() * 8},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": roof,
+        "per_kernel": per_kernel,
+        "min_traffic_roofline_frac": (16.0 * npts / (ms * 1e-3) / 1e9) / hbm,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

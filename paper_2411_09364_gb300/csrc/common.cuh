@@ -240,4 +240,40 @@ __device__ __forceinline__ cpx<T> pre_inverse(const T* X, int xes, const DirTab<
     return mk(s.x - d.y, s.y + d.x);             // s + i d
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 units (Dekker / Knuth error-free
+// transformations): a value is hi + lo with |lo| <= ulp(hi)/2, about 48
+// significant bits.  Used where FP64 would run on GB300's narrow FP64 pipe.
+// ---------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_from_double(double v) {
+    const float h = __double2float_rn(v);
+    return ff{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
+
 }  // namespace cales

@@ -52,4 +52,76 @@ cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Double-float residual (FP32 pipes).  u is stored as (hi, lo) float pairs;
+// each difference and product is carried in double-float, and only the final
+// f - t.hi is taken in FP64 (one FP64 operation per point).  One CTA row of
+// the grid per z-plane, so the dzf weight of the gauge sum is uniform in it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ff ldu(const float2* __restrict__ u, long i) {
+    const float2 v = u[i];
+    return ff{v.x, v.y};
+}
+
+__device__ __forceinline__ ff ghost_ff(int kind, ff c) { return kind == KIND_N ? c : ff_neg(c); }
+
+__global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
+    const long nx = a.nx, ny = a.ny;
+    const long plane = nx * ny;
+    const int k = blockIdx.y;
+    const long kbase = (long)k * plane;
+    const float2* __restrict__ u = a.u;
+    const ff za = ff_from_double(a.c1 * a.za[k]);
+    const ff zc = ff_from_double(a.c1 * a.zc[k]);
+    const ff cx{a.cxh, a.cxl}, cy{a.cyh, a.cyl};
+    const ff csh = a.cshift ? ff_from_double(a.cshift[0]) : ff{0.f, 0.f};
+    const ff zero{0.f, 0.f};
+    ff sum{0.f, 0.f};
+    for (long rem = (long)blockIdx.x * blockDim.x + threadIdx.x; rem < plane; rem += (long)gridDim.x * blockDim.x) {
+        const long j = rem / nx, i = rem - j * nx;
+        const long idx = kbase + rem;
+        const ff pc = ldu(u, idx);
+        const ff pw = i > 0 ? ldu(u, idx - 1) : (a.bcx == KIND_P ? ldu(u, idx + nx - 1) : ghost_ff(a.bcx, pc));
+        const ff pe = i < nx - 1 ? ldu(u, idx + 1) : (a.bcx == KIND_P ? ldu(u, idx - (nx - 1)) : ghost_ff(a.bcx, pc));
+        const ff ps = j > 0 ? ldu(u, idx - nx) : (a.bcy == KIND_P ? ldu(u, idx + (ny - 1) * nx) : ghost_ff(a.bcy, pc));
+        const ff pn = j < ny - 1 ? ldu(u, idx + nx) : (a.bcy == KIND_P ? ldu(u, idx - (ny - 1) * nx) : ghost_ff(a.bcy, pc));
+        const ff pd = k > 0 ? ldu(u, idx - plane) : (a.zlo == ZBC_N ? pc : (a.zlo == ZBC_D ? ff_neg(pc) : zero));
+        const ff pu = k < a.nz - 1 ? ldu(u, idx + plane) : (a.zhi == ZBC_N ? pc : (a.zhi == ZBC_D ? ff_neg(pc) : zero));
+        const ff lx = ff_add(ff_sub(pe, pc), ff_sub(pw, pc));
+        const ff ly = ff_add(ff_sub(pn, pc), ff_sub(ps, pc));
+        ff t = ff_mul(cx, lx);
+        t = ff_add(t, ff_mul(cy, ly));
+        t = ff_add(t, ff_mul(zc, ff_sub(pu, pc)));
+        t = ff_add(t, ff_mul(za, ff_sub(pd, pc)));
+        if (a.c0h != 0.f) t = ff_add(t, pc);
+        t = ff_add(t, csh);
+        const double d = a.f[idx] - (double)t.hi;
+        a.r[idx] = __fsub_rn(__double2float_rn(d), t.lo);
+        if (a.gacc) sum = ff_add(sum, pc);
+    }
+    if (a.gacc) {
+        double v = ff_to_double(sum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __shared__ double red[32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            atomicAdd(a.gacc, s * a.dzf[k]);
+        }
+    }
+}
+
+cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st) {
+    const long plane = (long)a.nx * a.ny;
+    long bx = (plane + 255) / 256;
+    if (bx > 64) bx = 64;
+    dim3 grid((unsigned)bx, (unsigned)a.nz);
+    k_residual_ff<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace cales

@@ -49,8 +49,25 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     for (int e = threadIdx.x; e < tot; e += blockDim.x) out[e] = ob[e];
 }
 
-// Inverse along x.  ACC: out (double) += result - shift, else out = result.
-template <typename T, typename TOut, bool ACC>
+// Store of one inverse-x result according to the output mode.
+template <typename T, int MODE>
+__device__ __forceinline__ void store_out(void* outp, long e, T v, ff shift) {
+    if (MODE == OUT_T) {
+        reinterpret_cast<T*>(outp)[e] = v;
+    } else if (MODE == OUT_F64) {
+        reinterpret_cast<double*>(outp)[e] = double(v);
+    } else if (MODE == OUT_FF_INIT) {
+        reinterpret_cast<float2*>(outp)[e] = make_float2(float(v), 0.f);
+    } else {
+        const float2 pr = reinterpret_cast<const float2*>(outp)[e];
+        ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
+        if (MODE == OUT_FF_ACC) reinterpret_cast<float2*>(outp)[e] = make_float2(x.hi, x.lo);
+        else reinterpret_cast<double*>(outp)[e] = ff_to_double(x);
+    }
+}
+
+// Inverse along x; the output mode decides how the result is stored.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DirTab<T>& t = a.t;
@@ -58,14 +75,12 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     const long row0 = (long)blockIdx.x * a.rpc;
     const int nr = (int)min((long)a.rpc, a.nrows - row0);
     const T* __restrict__ in = reinterpret_cast<const T*>(a.in) + row0 * n;
-    TOut* __restrict__ out = reinterpret_cast<TOut*>(a.out) + row0 * n;
-    const double shift = a.shift;
+    void* outp = reinterpret_cast<unsigned char*>(a.out) + row0 * n * (MODE == OUT_T ? sizeof(T) : 8);
+    ff shift{0.f, 0.f};
+    if (MODE >= OUT_FF_ACC && a.shift_acc) shift = ff_from_double(a.shift_acc[0] * a.shift_scale);
     const int tot = nr * n;
     if (n == 1) {
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            if (ACC) out[e] = TOut(double(out[e]) + double(in[e]) - shift);
-            else out[e] = TOut(in[e]);
-        }
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) store_out<T, MODE>(outp, e, in[e], shift);
         return;
     }
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -84,8 +99,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
         const int r = e / n, s = e - r * n;
         const T v = zr[r * n + pack_index(t.kind, n, s)] * pack_sign<T>(t.kind, s);
-        if (ACC) out[e] = TOut(double(out[e]) + double(v) - shift);
-        else out[e] = TOut(v);
+        store_out<T, MODE>(outp, e, v, shift);
     }
 }
 
@@ -170,10 +184,10 @@ cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename T, typename TOut, bool ACC>
+template <typename T, int MODE>
 cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
     const size_t sm = row_smem(a.t, a.rpc);
-    auto kern = k_rows_inverse<T, TOut, ACC>;
+    auto kern = k_rows_inverse<T, MODE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
     kern<<<grid, 256, sm, st>>>(a);
@@ -209,10 +223,12 @@ cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
 template cudaError_t launch_rows_forward<double, double>(const RowArgs<double>&, cudaStream_t);
 template cudaError_t launch_rows_forward<float, float>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_forward<float, double>(const RowArgs<float>&, cudaStream_t);
-template cudaError_t launch_rows_inverse<double, double, false>(const RowArgs<double>&, cudaStream_t);
-template cudaError_t launch_rows_inverse<float, float, false>(const RowArgs<float>&, cudaStream_t);
-template cudaError_t launch_rows_inverse<float, double, false>(const RowArgs<float>&, cudaStream_t);
-template cudaError_t launch_rows_inverse<float, double, true>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<double, OUT_T>(const RowArgs<double>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_T>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_F64>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_FF_INIT>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_FF_ACC>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_FF_FINAL>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_cols<double>(const ColArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_cols<float>(const ColArgs<float>&, bool, cudaStream_t);
 

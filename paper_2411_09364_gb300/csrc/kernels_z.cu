@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(128) k_zsolve(ZArgs<T> a) {
                 sw += a.dzf[k];
             }
             gmean = s / sw;
+            if (a.cacc) a.cacc[0] += gmean * a.cacc_scale;
         }
         bool bad = false;
         // forward sweep

@@ -22,6 +22,11 @@ using namespace cales;
 
 namespace {
 
+void split_double(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 // cos and sin of 2 pi num / den with exact integer quadrant reduction.
 void cis_frac(long num, long den, double& c, double& s) {
     long r = num % den;
@@ -168,10 +173,18 @@ template <typename T> int choose_tx(int ny) {
     return 0;
 }
 
-// One pass of the solver: in (TIn) -> work (T, mode space) -> out (TOut).
-template <typename T, typename TIn, typename TOut, bool ACC>
-int pipeline(cales_plan_s* P, const void* in, void* out, T* work, double sigma, double alpha, double scale,
-             bool singular, bool adjoint, double shift, cudaStream_t st) {
+// Per-solve options of one pass of the solver.
+struct PassOpt {
+    double sigma, alpha, scale;
+    bool singular, adjoint;
+    double* cacc;              // consistency-constant accumulator (singular mode 0)
+    const double* shift_acc;   // gauge accumulator subtracted by the inverse-x kernel
+    double shift_scale;
+};
+
+// One pass of the solver: in (TIn) -> work (T, mode space) -> out (MODE).
+template <typename T, typename TIn, int MODE>
+int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st) {
     const long nrows = (long)P->ny * P->nz;
     RowArgs<T> ra;
     ra.t = P->X.tab<T>();
@@ -180,7 +193,8 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, double sigma, 
     ra.nrows = nrows;
     ra.rpc = rows_per_cta<T>(P->nx);
     ra.in_scale = 1.0;
-    ra.shift = 0.0;
+    ra.shift_acc = nullptr;
+    ra.shift_scale = 0.0;
     P->prof_begin(st, "x_fwd");
     if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
@@ -206,11 +220,13 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, double sigma, 
     za.dzf = P->dzf_d;
     za.nx = P->nx; za.ny = P->ny; za.nz = P->nz;
     za.zlo = P->bc[4]; za.zhi = P->bc[5];
-    za.singular = singular ? 1 : 0;
-    za.adjoint = adjoint ? 1 : 0;
+    za.singular = o.singular ? 1 : 0;
+    za.adjoint = o.adjoint ? 1 : 0;
     za.tm = choose_tm<T>(P->nz);
-    za.sigma = T(sigma); za.alpha = T(alpha); za.scale = T(scale);
+    za.sigma = T(o.sigma); za.alpha = T(o.alpha); za.scale = T(o.scale);
     za.status = P->status;
+    za.cacc = o.cacc;
+    za.cacc_scale = 1.0 / (o.scale * (double)P->nx * (double)P->ny);
     P->prof_begin(st, "z_solve");
     if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
@@ -224,9 +240,10 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, double sigma, 
     RowArgs<T> ri = ra;
     ri.in = work;
     ri.out = out;
-    ri.shift = shift;
-    P->prof_begin(st, ACC ? "x_inv_acc" : "x_inv");
-    if (launch_rows_inverse<T, TOut, ACC>(ri, st) != cudaSuccess) return CALES_ECUDA;
+    ri.shift_acc = o.shift_acc;
+    ri.shift_scale = o.shift_scale;
+    P->prof_begin(st, MODE >= OUT_FF_ACC ? "x_inv_acc" : "x_inv");
+    if (launch_rows_inverse<T, MODE>(ri, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
     return CALES_OK;
 }
@@ -250,37 +267,73 @@ void cales_plan_s::prof_end(cudaStream_t st) {
     ++prof_n;
 }
 
+// FP32 solves with double-float refinement.  While sweeping, the caller's
+// FP64 output buffer holds the solution as (hi, lo) float pairs; the last
+// sweep writes it back as doubles.  For a singular Poisson problem the
+// consistency constant of f is estimated from the first mode-space solve and
+// refined by every sweep (acc[0]); the dzf-weighted mean of the solution is
+// measured by each residual pass (acc[1]) and removed by the same sweep.
+static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, void* p, PassOpt o, cudaStream_t st) {
+    const int ns = P->sweeps;
+    const bool sing = o.singular;
+    if (cudaMemsetAsync(P->acc, 0, 2 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+    o.cacc = sing ? P->acc : nullptr;
+    int rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, P->work, o, st)
+                     : pipeline<float, double, OUT_FF_INIT>(P, f, p, P->work, o, st);
+    if (rc) return rc;
+    const double c1 = helm ? -alpha : 1.0;
+    for (int s = 0; s < ns; ++s) {
+        if (sing && cudaMemsetAsync(P->acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+        ResidFFArgs ra;
+        ra.f = (const double*)f;
+        ra.u = (const float2*)p;
+        ra.r = P->work;
+        ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
+        ra.bcx = P->bc[0]; ra.bcy = P->bc[2]; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
+        split_double(c1 / (P->dx * P->dx), ra.cxh, ra.cxl);
+        split_double(c1 / (P->dy * P->dy), ra.cyh, ra.cyl);
+        ra.c0h = helm ? 1.0f : 0.0f;
+        ra.za = P->za_d;
+        ra.zc = P->zc_d;
+        ra.c1 = c1;
+        ra.cshift = sing ? P->acc : nullptr;
+        ra.gacc = sing ? P->acc + 1 : nullptr;
+        ra.dzf = P->dzf_d;
+        P->prof_begin(st, "residual");
+        if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
+        P->prof_end(st);
+        o.shift_acc = sing ? P->acc + 1 : nullptr;
+        o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
+        rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, P->work, p, P->work, o, st)
+                           : pipeline<float, float, OUT_FF_ACC>(P, P->work, p, P->work, o, st);
+        if (rc) return rc;
+    }
+    return CALES_OK;
+}
+
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {
     if (!P || !f || !p) return CALES_EINVAL;
     if (helm && !(alpha > 0.0)) return CALES_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double nxy = (double)P->nx * (double)P->ny;
-    const double sigma = helm ? 1.0 : 0.0;
-    const double a = helm ? alpha : 1.0;
-    const double scale = (helm ? 1.0 : -1.0) / nxy;
-    const bool sing = !helm && P->singular_poisson;
-    P->prof_n = 0;
+    PassOpt o;
+    o.sigma = helm ? 1.0 : 0.0;
+    o.alpha = helm ? alpha : 1.0;
+    o.scale = (helm ? 1.0 : -1.0) / nxy;
+    o.singular = !helm && P->singular_poisson;
+    o.adjoint = adjoint;
+    o.cacc = nullptr;
+    o.shift_acc = nullptr;
+    o.shift_scale = 0.0;
     switch (P->precision) {
         case CALES_FP64:
-            return pipeline<double, double, double, false>(P, f, p, (double*)p, sigma, a, scale, sing, adjoint, 0.0, st);
+            return pipeline<double, double, OUT_T>(P, f, p, (double*)p, o, st);
         case CALES_FP32:
-            return pipeline<float, float, float, false>(P, f, p, (float*)p, sigma, a, scale, sing, adjoint, 0.0, st);
-        case CALES_FP32_REFINE: {
+            return pipeline<float, float, OUT_T>(P, f, p, (float*)p, o, st);
+        case CALES_FP32_REFINE:
             if (adjoint) return CALES_EUNSUPPORTED;
             if (f == p || !P->work) return CALES_EINVAL;
-            int rc = pipeline<float, double, double, false>(P, f, p, P->work, sigma, a, scale, sing, false, 0.0, st);
-            if (rc) return rc;
-            for (int s = 0; s < P->sweeps; ++s) {
-                ResidArgs ra;
-                P->fill_resid(ra, (const double*)p, (const double*)f, P->work, false, helm ? 1.0 : 0.0, helm ? -alpha : 1.0);
-                P->prof_begin(st, "residual");
-                if (launch_residual(ra, st) != cudaSuccess) return CALES_ECUDA;
-                P->prof_end(st);
-                rc = pipeline<float, float, double, true>(P, P->work, p, P->work, sigma, a, scale, sing, false, 0.0, st);
-                if (rc) return rc;
-            }
-            return CALES_OK;
-        }
+            return refine_solve(P, helm, alpha, f, p, o, st);
         default:
             return CALES_EINVAL;
     }
@@ -353,7 +406,11 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         P->zc_f = dev_upload(zcf, P->owned);
         std::vector<int> st(4, 0);
         P->status = dev_upload(st, P->owned);
-        if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status) rc = CALES_ENOMEM;
+        std::vector<double> acc(4, 0.0);
+        P->acc = dev_upload(acc, P->owned);
+        P->dzf_sum = 0.0;
+        for (int k = 0; k < nz; ++k) P->dzf_sum += dzf[k];
+        if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status || !P->acc) rc = CALES_ENOMEM;
     }
     if (rc == CALES_OK && cudaDeviceSynchronize() != cudaSuccess) rc = CALES_ECUDA;
     if (rc != CALES_OK) {

@@ -37,10 +37,12 @@ struct cales_plan_s {
     float* za_f = nullptr;
     float* zc_f = nullptr;
     int* status = nullptr;
+    double* acc = nullptr;       // [0] consistency constant, [1] gauge sum (refinement)
+    double dzf_sum = 0.0;
     int precision = 0, sweeps = 2;
     float* work = nullptr;
     std::vector<void*> owned;
-    static constexpr int PROF_MAX = 64;
+    static constexpr int PROF_MAX = 4096;
     bool prof_on = false;
     int prof_n = 0;
     ProfRec prof[PROF_MAX];

@@ -141,9 +141,9 @@ class Plan:
         N.check(N.lib().cales_profile_enable(self._h, 1 if on else 0), "cales_profile_enable")
 
     def profile_read(self):
-        names = (C.c_char_p * 64)()
-        ms = (C.c_float * 64)()
-        n = N.lib().cales_profile_read(self._h, 64, names, ms)
+        names = (C.c_char_p * 4096)()
+        ms = (C.c_float * 4096)()
+        n = N.lib().cales_profile_read(self._h, 4096, names, ms)
         return [(names[i].decode(), float(ms[i])) for i in range(max(n, 0))]
 
     def close(self):

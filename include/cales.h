@@ -118,6 +118,59 @@ int cales_helmholtz_solve_adjoint(cales_plan_t plan, double alpha, const void* w
  */
 int cales_residual(cales_plan_t plan, double alpha, const double* u, const double* f, double* r, void* stream);
 
+/*
+ * Staggered projection operators of the fractional-step method (Sec. 2.2,
+ * Eqs. 12-13) for plans periodic in x and y with Neumann (wall) z sides.
+ * Layout: u on x-faces and v on y-faces, [nz][ny][nx]; w on z-faces,
+ * [nz+1][ny][nx] with w[0] = w[nz] = 0 at the walls; scalars [nz][ny][nx].
+ * Element type as for the solves (float for CALES_FP32 plans, else double).
+ *   divergence: d = (u_i - u_{i-1})/dx + (v_j - v_{j-1})/dy + (w_{k+1} - w_k)/dzf_k
+ *   gradient  : (gx, gy, gz) = grad phi, gz = 0 on the walls; with uin, vin,
+ *               win non-NULL the outputs are (uin, vin, win) - grad phi, i.e.
+ *               the velocity correction of Eq. (13) with gamma dt folded in phi.
+ *   *_adjoint : the exact transposes (for gradients through the projection);
+ *               divergence_adjoint with uin, vin, win non-NULL returns
+ *               (uin, vin, win) - div^T d.
+ * Other boundary kinds return CALES_EUNSUPPORTED.
+ */
+int cales_divergence(cales_plan_t plan, const void* u, const void* v, const void* w, void* d, void* stream);
+int cales_gradient(cales_plan_t plan, const void* phi, const void* uin, const void* vin, const void* win,
+                   void* gx, void* gy, void* gz, void* stream);
+int cales_divergence_adjoint(cales_plan_t plan, const void* d, const void* uin, const void* vin, const void* win,
+                             void* u, void* v, void* w, void* stream);
+int cales_gradient_adjoint(cales_plan_t plan, const void* gx, const void* gy, const void* gz, void* phi, void* stream);
+
+/*
+ * Learned closure trained through the projection (the paper motivates
+ * machine-learned closures built on the solver, Sec. 1).  FP32, plan layout
+ * as above.  theta: device [3][27] taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1).
+ *   cales_stencil27: out_c = a*in_c + sum_t theta[c][t] in_c(x + o_t) + beta*tanh(in_c)
+ *     (x, y periodic; zero outside the component's planes in z; w walls held 0);
+ *     in[3], out[3]: device pointers of u, v, w (out != in).
+ *   cales_stencil27_weight_grad: gtheta[c][t] += sum_x g_c(x) in_c(x + o_t)
+ *     (FP64 device accumulators, zeroed by the caller; g at w walls ignored).
+ *   cales_sq_error: loss[0] += sum (pred - target)^2 over the three arrays of
+ *     n[c] elements; grad[c] (optional) = scale * (pred - target).
+ *   cales_adam_step: one Adam update of n parameters (Kingma & Ba) from the
+ *     FP64 gradient times grad_scale; m, v: device moment buffers; t >= 1.
+ */
+int cales_stencil27(cales_plan_t plan, const float* theta, float a, float beta, const float* const* in,
+                    float* const* out, void* stream);
+int cales_stencil27_weight_grad(cales_plan_t plan, const float* const* g, const float* const* in, double* gtheta,
+                                void* stream);
+int cales_sq_error(const float* const* pred, const float* const* target, float* const* grad, const long* n,
+                   float scale, double* loss, void* stream);
+int cales_adam_step(float* theta, const double* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
+                    float eps, int t, float grad_scale, void* stream);
+
+/* Asynchronous zero fill of `bytes` bytes of device memory (accumulators). */
+int cales_zero(void* p, unsigned long bytes, void* stream);
+
+/* Per-kernel CUDA-event timings: enable (resets the record list), then read
+ * name/ms pairs of every launch since (synchronises).  Returns the count. */
+int cales_profile_enable(cales_plan_t plan, int on);
+int cales_profile_read(cales_plan_t plan, int max, const char** names, float* ms);
+
 /* Read and clear the device status word (synchronises the plan's last stream). */
 int cales_get_status(cales_plan_t plan, int* device_status);
 

@@ -30,6 +30,16 @@ SIGNATURES = {
     "cales_strerror": (C.c_char_p, [C.c_int]),
     "cales_destroy": (None, [vp]),
     "cales_profile_enable": (C.c_int, [vp, C.c_int]),
+    "cales_divergence": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+    "cales_gradient": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "cales_divergence_adjoint": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "cales_zero": (C.c_int, [vp, C.c_ulong, vp]),
+    "cales_gradient_adjoint": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+    "cales_stencil27": (C.c_int, [vp, vp, C.c_float, C.c_float, C.POINTER(vp), C.POINTER(vp), vp]),
+    "cales_stencil27_weight_grad": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp, vp]),
+    "cales_sq_error": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_long), C.c_float, vp, vp]),
+    "cales_adam_step": (C.c_int, [vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                                  C.c_float, vp]),
     "cales_profile_read": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_float)]),
 }
 

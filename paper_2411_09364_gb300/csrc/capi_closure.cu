@@ -1,0 +1,138 @@
+// C ABI of the projection operators and learned-closure kernels (cales.h).
+#include "cales.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+
+
+using namespace cales;
+
+static bool channel_layout(cales_plan_t P) {
+    return P && P->bc[0] == CALES_BC_P && P->bc[2] == CALES_BC_P && P->bc[4] == CALES_BC_N && P->bc[5] == CALES_BC_N;
+}
+
+template <typename T> static GridArgs<T> gargs(cales_plan_t P) {
+    GridArgs<T> g;
+    g.nx = P->nx; g.ny = P->ny; g.nz = P->nz;
+    g.idx = T(1.0 / P->dx);
+    g.idy = T(1.0 / P->dy);
+    g.idzf = sizeof(T) == 8 ? (const T*)P->idzf_d : (const T*)P->idzf_f;
+    g.idzc = sizeof(T) == 8 ? (const T*)P->idzc_d : (const T*)P->idzc_f;
+    return g;
+}
+
+#define CALES_DISPATCH(P, CALL_D, CALL_F) \
+    ((P)->precision == CALES_FP32 ? (CALL_F) : (CALL_D))
+
+extern "C" {
+
+int cales_divergence(cales_plan_t P, const void* u, const void* v, const void* w, void* d, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!u || !v || !w || !d) return CALES_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = CALES_DISPATCH(P,
+        launch_divergence<double>(gargs<double>(P), (const double*)u, (const double*)v, (const double*)w, (double*)d, st),
+        launch_divergence<float>(gargs<float>(P), (const float*)u, (const float*)v, (const float*)w, (float*)d, st));
+    return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_gradient(cales_plan_t P, const void* phi, const void* uin, const void* vin, const void* win, void* gx,
+                   void* gy, void* gz, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!phi || !gx || !gy || !gz) return CALES_EINVAL;
+    const int sub = (uin && vin && win) ? 1 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = CALES_DISPATCH(P,
+        launch_gradient<double>(gargs<double>(P), (const double*)phi, (const double*)uin, (const double*)vin,
+                                (const double*)win, (double*)gx, (double*)gy, (double*)gz, sub, st),
+        launch_gradient<float>(gargs<float>(P), (const float*)phi, (const float*)uin, (const float*)vin,
+                               (const float*)win, (float*)gx, (float*)gy, (float*)gz, sub, st));
+    return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_divergence_adjoint(cales_plan_t P, const void* d, const void* uin, const void* vin, const void* win,
+                             void* u, void* v, void* w, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!d || !u || !v || !w) return CALES_EINVAL;
+    if (!(uin && vin && win)) uin = vin = win = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = CALES_DISPATCH(P,
+        launch_divergence_T<double>(gargs<double>(P), (const double*)d, (const double*)uin, (const double*)vin,
+                                    (const double*)win, (double*)u, (double*)v, (double*)w, st),
+        launch_divergence_T<float>(gargs<float>(P), (const float*)d, (const float*)uin, (const float*)vin,
+                                   (const float*)win, (float*)u, (float*)v, (float*)w, st));
+    return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_gradient_adjoint(cales_plan_t P, const void* gx, const void* gy, const void* gz, void* phi, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!gx || !gy || !gz || !phi) return CALES_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = CALES_DISPATCH(P,
+        launch_gradient_T<double>(gargs<double>(P), (const double*)gx, (const double*)gy, (const double*)gz, (double*)phi, st),
+        launch_gradient_T<float>(gargs<float>(P), (const float*)gx, (const float*)gy, (const float*)gz, (float*)phi, st));
+    return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_stencil27(cales_plan_t P, const float* theta, float a, float beta, const float* const* in, float* const* out,
+                    void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!theta || !in || !out) return CALES_EINVAL;
+    StencilArgs s;
+    s.nx = P->nx; s.ny = P->ny; s.nz = P->nz;
+    s.theta = theta;
+    for (int c = 0; c < 3; ++c) {
+        if (!in[c] || !out[c] || in[c] == out[c]) return CALES_EINVAL;
+        s.in[c] = in[c];
+        s.out[c] = out[c];
+    }
+    s.a = a;
+    s.beta = beta;
+    return launch_stencil27(s, (cudaStream_t)stream) == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_stencil27_weight_grad(cales_plan_t P, const float* const* g, const float* const* in, double* gtheta,
+                                void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!g || !in || !gtheta) return CALES_EINVAL;
+    WGradArgs s;
+    s.nx = P->nx; s.ny = P->ny; s.nz = P->nz;
+    for (int c = 0; c < 3; ++c) {
+        if (!g[c] || !in[c]) return CALES_EINVAL;
+        s.g[c] = g[c];
+        s.in[c] = in[c];
+    }
+    s.gtheta = gtheta;
+    return launch_stencil27_wgrad(s, (cudaStream_t)stream) == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_sq_error(const float* const* pred, const float* const* target, float* const* grad, const long* n,
+                   float scale, double* loss, void* stream) {
+    if (!pred || !target || !n || !loss) return CALES_EINVAL;
+    SqErrArgs s;
+    for (int c = 0; c < 3; ++c) {
+        if (!pred[c] || !target[c] || n[c] < 0) return CALES_EINVAL;
+        s.n[c] = n[c];
+        s.pred[c] = pred[c];
+        s.target[c] = target[c];
+        s.grad[c] = grad ? grad[c] : nullptr;
+    }
+    s.loss = loss;
+    s.scale = scale;
+    return launch_sqerr(s, (cudaStream_t)stream) == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_adam_step(float* theta, const double* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
+                    float eps, int t, float grad_scale, void* stream) {
+    if (!theta || !grad || !m || !v || n < 1 || t < 1) return CALES_EINVAL;
+    return launch_adam(theta, grad, m, v, n, lr, beta1, beta2, eps, t, grad_scale, (cudaStream_t)stream) == cudaSuccess
+               ? CALES_OK
+               : CALES_ECUDA;
+}
+
+int cales_zero(void* p, unsigned long bytes, void* stream) {
+    if (!p) return CALES_EINVAL;
+    return cudaMemsetAsync(p, 0, bytes, (cudaStream_t)stream) == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+}  // extern "C"

@@ -241,6 +241,76 @@ __device__ __forceinline__ cpx<T> pre_inverse(const T* X, int xes, const DirTab<
 }
 
 // ---------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk) between global and shared memory with an
+// mbarrier for completion.  Every wait is bounded: after MBAR_MAX_POLLS failed
+// polls the caller records a timeout in the status word and gives up.
+// ---------------------------------------------------------------------------
+constexpr long MBAR_MAX_POLLS = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    for (long i = 0; i < MBAR_MAX_POLLS; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+// global -> shared, completes `bytes` on the mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// shared -> global (bulk group)
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Warp 0 moves `nrows` rows of `rowb` bytes (row r: src + r*sstride -> dst +
+// r*dstride, strides in elements); lane 0 posts the byte count first.
+template <typename T>
+__device__ __forceinline__ void bulk_load_rows(uint64_t* bar, T* dst, long dstride, const T* src, long sstride,
+                                               int nrows, uint32_t rowb) {
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) mbar_expect_tx(bar, rowb * (uint32_t)nrows);
+        __syncwarp();
+        for (int r = threadIdx.x; r < nrows; r += 32) bulk_g2s(dst + r * dstride, src + r * sstride, rowb, bar);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void bulk_store_rows(T* dst, long dstride, const T* src, long sstride, int nrows,
+                                                uint32_t rowb) {
+    if (threadIdx.x < 32) {
+        for (int r = threadIdx.x; r < nrows; r += 32) bulk_s2g(dst + r * dstride, src + r * sstride, rowb);
+        bulk_commit();
+        bulk_wait_read_all();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Double-float arithmetic on the FP32 units (Dekker / Knuth error-free
 // transformations): a value is hi + lo with |lo| <= ulp(hi)/2, about 48
 // significant bits.  Used where FP64 would run on GB300's narrow FP64 pipe.

@@ -13,6 +13,8 @@ template <typename T> struct RowArgs {
     double in_scale;     // forward: multiply the input (1 normally)
     const double* shift_acc;   // inverse accumulation: subtract shift_acc[0] * shift_scale
     double shift_scale;
+    int bulk;            // rows move with TMA bulk copies (alignment checked on the host)
+    int* status;
 };
 
 // Output modes of the inverse x kernel.
@@ -29,7 +31,9 @@ template <typename T> struct ColArgs {
     void* data;          // in place, [nplanes][ny][nx]
     int nx;
     long nplanes;
-    int tx;              // columns per tile (8, 16 or 32)
+    int tx;              // columns per tile (4 .. 32)
+    int bulk;            // rows may be moved with TMA bulk copies (alignment checked on the host)
+    int* status;
 };
 
 // z tridiagonal solve per mode: (sigma - alpha L) u = scale * g in mode space,
@@ -46,6 +50,8 @@ template <typename T> struct ZArgs {
     int singular;        // Poisson with only P/N sides: project, pin, gauge mode 0
     int adjoint;         // apply D S D^-1 (D = diag(dzf))
     int tm;              // modes per CTA
+    int P;               // threads per mode (segments of the z line)
+    int bulk;            // tile rows may be moved with TMA bulk copies
     T sigma, alpha, scale;
     int* status;         // device status word (bit flags)
     double* cacc;        // singular mode 0: cacc[0] += (weighted mean of the rhs line) * cacc_scale
@@ -84,13 +90,53 @@ struct ResidFFArgs {
     const double* dzf;
 };
 
-enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2 };
+enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
 
 template <typename T, typename TIn> cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st);
 template <typename T, int MODE> cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st);
 template <typename T> cudaError_t launch_zsolve(const ZArgs<T>& a, cudaStream_t st);
+template <typename T> size_t zsolve_smem(int nz, int tm, int P);
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
 cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st);
+
+// ---- projection operators and learned-closure kernels ----
+template <typename T> struct GridArgs {
+    int nx, ny, nz;
+    T idx, idy;
+    const T* idzf;
+    const T* idzc;
+};
+struct StencilArgs {
+    int nx, ny, nz;
+    const float* theta;
+    const float* in[3];
+    float* out[3];
+    float a, beta;
+};
+struct WGradArgs {
+    int nx, ny, nz;
+    const float* g[3];
+    const float* in[3];
+    double* gtheta;
+};
+struct SqErrArgs {
+    long n[3];
+    const float* pred[3];
+    const float* target[3];
+    float* grad[3];
+    double* loss;
+    float scale;
+};
+template <typename T> cudaError_t launch_divergence(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
+template <typename T>
+cudaError_t launch_gradient(const GridArgs<T>&, const T*, const T*, const T*, const T*, T*, T*, T*, int, cudaStream_t);
+template <typename T>
+cudaError_t launch_divergence_T(const GridArgs<T>&, const T*, const T*, const T*, const T*, T*, T*, T*, cudaStream_t);
+template <typename T> cudaError_t launch_gradient_T(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
+cudaError_t launch_stencil27(const StencilArgs&, cudaStream_t);
+cudaError_t launch_stencil27_wgrad(const WGradArgs&, cudaStream_t);
+cudaError_t launch_sqerr(const SqErrArgs&, cudaStream_t);
+cudaError_t launch_adam(float*, const double*, float*, float*, int, float, float, float, float, int, float, cudaStream_t);
 
 }  // namespace cales

@@ -12,7 +12,10 @@
 namespace cales {
 
 // ---------------------------------------------------------------------------
-// x direction
+// x direction.  Shared memory: [mbarrier | b0 | b1 | staging], the staging
+// area holds FP64 input rows (forward, FP64 -> FP32 solves) or the 8-byte
+// output rows (inverse into FP64 or double-float pairs).  With `bulk` a CTA's
+// rows (contiguous in memory) move by one TMA bulk copy each way.
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn>
 __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
@@ -24,45 +27,72 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     const TIn* __restrict__ in = reinterpret_cast<const TIn*>(a.in) + row0 * n;
     T* __restrict__ out = reinterpret_cast<T*>(a.out) + row0 * n;
     const T sc = T(a.in_scale);
+    const int tid = threadIdx.x;
     if (n == 1) {
-        for (int e = threadIdx.x; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
+        for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
     cpx<T>* b1 = b0 + a.rpc * L;
-    T* r0 = reinterpret_cast<T*>(b0);
+    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b1) : reinterpret_cast<TIn*>(b1 + a.rpc * L);
     const int tot = nr * n;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    if (a.bulk) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (uint32_t)(tot * sizeof(TIn)));
+            bulk_g2s(stage, in, (uint32_t)(tot * sizeof(TIn)), bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
+            mbar_wait_bounded(bar, 0);
+            return;
+        }
+    } else {
+        for (int e = tid; e < tot; e += blockDim.x) stage[e] = in[e];
+        __syncthreads();
+    }
+    T* r0 = reinterpret_cast<T*>(b0);
+    for (int e = tid; e < tot; e += blockDim.x) {
         const int r = e / n, s = e - r * n;
-        const T v = T(in[e]) * sc * pack_sign<T>(t.kind, s);
-        r0[r * n + pack_index(t.kind, n, s)] = v;   // pair (v[2j], v[2j+1]) = complex j
+        r0[r * n + pack_index(t.kind, n, s)] = T(stage[e]) * sc * pack_sign<T>(t.kind, s);
     }
     __syncthreads();
     cpx<T>* Z = fft_lines<T, false, false>(b0, b1, t, nr, L, 1);
     T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
     const int npost = nr * (L + 1);
-    for (int idx = threadIdx.x; idx < npost; idx += blockDim.x) {
+    for (int idx = tid; idx < npost; idx += blockDim.x) {
         const int r = idx / (L + 1), m = idx - r * (L + 1);
         post_forward<T>(Z + r * L, 1, ob + r * n, 1, t, m);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) out[e] = ob[e];
+    if (a.bulk) {
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(out, ob, (uint32_t)(tot * sizeof(T)));
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+    } else {
+        __syncthreads();
+        for (int e = tid; e < tot; e += blockDim.x) out[e] = ob[e];
+    }
 }
 
-// Store of one inverse-x result according to the output mode.
+// One inverse-x result into an 8-byte slot according to the output mode.
 template <typename T, int MODE>
-__device__ __forceinline__ void store_out(void* outp, long e, T v, ff shift) {
-    if (MODE == OUT_T) {
-        reinterpret_cast<T*>(outp)[e] = v;
-    } else if (MODE == OUT_F64) {
-        reinterpret_cast<double*>(outp)[e] = double(v);
+__device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
+    if (MODE == OUT_F64) {
+        *reinterpret_cast<double*>(slot) = double(v);
     } else if (MODE == OUT_FF_INIT) {
-        reinterpret_cast<float2*>(outp)[e] = make_float2(float(v), 0.f);
+        *reinterpret_cast<float2*>(slot) = make_float2(float(v), 0.f);
     } else {
-        const float2 pr = reinterpret_cast<const float2*>(outp)[e];
-        ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
-        if (MODE == OUT_FF_ACC) reinterpret_cast<float2*>(outp)[e] = make_float2(x.hi, x.lo);
-        else reinterpret_cast<double*>(outp)[e] = ff_to_double(x);
+        const float2 pr = *reinterpret_cast<const float2*>(slot);
+        const ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
+        if (MODE == OUT_FF_ACC) *reinterpret_cast<float2*>(slot) = make_float2(x.hi, x.lo);
+        else *reinterpret_cast<double*>(slot) = ff_to_double(x);
     }
 }
 
@@ -75,36 +105,86 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     const long row0 = (long)blockIdx.x * a.rpc;
     const int nr = (int)min((long)a.rpc, a.nrows - row0);
     const T* __restrict__ in = reinterpret_cast<const T*>(a.in) + row0 * n;
-    void* outp = reinterpret_cast<unsigned char*>(a.out) + row0 * n * (MODE == OUT_T ? sizeof(T) : 8);
+    constexpr int OSZ = MODE == OUT_T ? (int)sizeof(T) : 8;
+    unsigned char* outp = reinterpret_cast<unsigned char*>(a.out) + row0 * n * OSZ;
     ff shift{0.f, 0.f};
     if (MODE >= OUT_FF_ACC && a.shift_acc) shift = ff_from_double(a.shift_acc[0] * a.shift_scale);
     const int tot = nr * n;
+    const int tid = threadIdx.x;
     if (n == 1) {
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) store_out<T, MODE>(outp, e, in[e], shift);
+        for (int e = tid; e < tot; e += blockDim.x) {
+            if (MODE == OUT_T) reinterpret_cast<T*>(outp)[e] = in[e];
+            else store8<T, MODE>(outp + (long)e * 8, in[e], shift);
+        }
         return;
     }
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
     cpx<T>* b1 = b0 + a.rpc * L;
+    unsigned char* o8 = reinterpret_cast<unsigned char*>(b1 + a.rpc * L);
     T* x0 = reinterpret_cast<T*>(b0);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) x0[e] = in[e];
-    __syncthreads();
+    constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL;
+    if (a.bulk) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            const uint32_t b_in = (uint32_t)(tot * sizeof(T));
+            const uint32_t b_out = LOAD_OUT ? (uint32_t)(tot * 8) : 0u;
+            mbar_expect_tx(bar, b_in + b_out);
+            bulk_g2s(x0, in, b_in, bar);
+            if (LOAD_OUT) bulk_g2s(o8, outp, b_out, bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
+            mbar_wait_bounded(bar, 0);
+            return;
+        }
+    } else {
+        for (int e = tid; e < tot; e += blockDim.x) x0[e] = in[e];
+        if (LOAD_OUT)
+            for (int e = tid; e < tot; e += blockDim.x)
+                reinterpret_cast<float2*>(o8)[e] = reinterpret_cast<const float2*>(outp)[e];
+        __syncthreads();
+    }
     const int npre = nr * L;
-    for (int idx = threadIdx.x; idx < npre; idx += blockDim.x) {
+    for (int idx = tid; idx < npre; idx += blockDim.x) {
         const int r = idx / L, m = idx - r * L;
         b1[r * L + m] = pre_inverse<T>(x0 + r * n, 1, t, m);
     }
     __syncthreads();
     cpx<T>* z = fft_lines<T, true, false>(b1, b0, t, nr, L, 1);
     const T* zr = reinterpret_cast<const T*>(z);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    unsigned char* ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(z == b0 ? b1 : b0) : o8;
+    for (int e = tid; e < tot; e += blockDim.x) {
         const int r = e / n, s = e - r * n;
         const T v = zr[r * n + pack_index(t.kind, n, s)] * pack_sign<T>(t.kind, s);
-        store_out<T, MODE>(outp, e, v, shift);
+        if (MODE == OUT_T) reinterpret_cast<T*>(ob)[e] = v;
+        else store8<T, MODE>(ob + (long)e * 8, v, shift);
+    }
+    if (a.bulk) {
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(outp, ob, (uint32_t)(tot * OSZ));
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+    } else {
+        __syncthreads();
+        if (MODE == OUT_T) {
+            for (int e = tid; e < tot; e += blockDim.x) reinterpret_cast<T*>(outp)[e] = reinterpret_cast<const T*>(ob)[e];
+        } else {
+            for (int e = tid; e < tot; e += blockDim.x)
+                reinterpret_cast<double*>(outp)[e] = reinterpret_cast<const double*>(ob)[e];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// y direction: tiles of TX columns of one z-plane, in place.
+// y direction: tiles of TX columns of one z-plane, in place.  With `bulk`, the
+// ny rows of TX elements are moved by TMA bulk copies (one row each) into a
+// natural-order staging buffer; otherwise by plain coalesced loads.
 // ---------------------------------------------------------------------------
 template <typename T, int TX, bool INV>
 __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
@@ -116,53 +196,76 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     const int plane = blockIdx.x / tiles_x;
     const int x0 = (blockIdx.x - plane * tiles_x) * TX;
     const int wx = min(TX, nx - x0);
+    const int tid = threadIdx.x;
     T* __restrict__ base = reinterpret_cast<T*>(a.data) + (long)plane * n * nx + x0;
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
     cpx<T>* b1 = b0 + TX * L;
     const int tot = n * TX;
+    const uint32_t rowb = (uint32_t)(wx * sizeof(T));
+    // natural-order tile into `nat`
+    T* nat = reinterpret_cast<T*>(INV ? b0 : b1);
+    if (a.bulk) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+        bulk_load_rows<T>(bar, nat, TX, base, nx, n, rowb);
+        const bool ok = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
+            mbar_wait_bounded(bar, 0);
+            return;
+        }
+        if (wx < TX)
+            for (int e = tid; e < tot; e += blockDim.x)
+                if ((e % TX) >= wx) nat[e] = T(0);
+    } else {
+        for (int e = tid; e < tot; e += blockDim.x) {
+            const int s = e / TX, c = e - s * TX;
+            nat[e] = (c < wx) ? base[(long)s * nx + c] : T(0);
+        }
+    }
+    __syncthreads();
+    T* ob;
     if (!INV) {
         T* r0 = reinterpret_cast<T*>(b0);
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        for (int e = tid; e < tot; e += blockDim.x) {
             const int s = e / TX, c = e - s * TX;
-            T v = (c < wx) ? base[(long)s * nx + c] : T(0);
-            v *= pack_sign<T>(t.kind, s);
             const int d = pack_index(t.kind, n, s);
-            r0[((d >> 1) * TX + c) * 2 + (d & 1)] = v;
+            r0[((d >> 1) * TX + c) * 2 + (d & 1)] = nat[e] * pack_sign<T>(t.kind, s);
         }
         __syncthreads();
         cpx<T>* Z = fft_lines<T, false, true>(b0, b1, t, TX, 1, TX);
-        T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
+        ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
         const int npost = (L + 1) * TX;
-        for (int idx = threadIdx.x; idx < npost; idx += blockDim.x) {
+        for (int idx = tid; idx < npost; idx += blockDim.x) {
             const int m = idx / TX, c = idx - m * TX;
             post_forward<T>(Z + c, TX, ob + c, TX, t, m);
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            if (c < wx) base[(long)s * nx + c] = ob[e];
-        }
     } else {
-        T* x0r = reinterpret_cast<T*>(b0);
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            x0r[e] = (c < wx) ? base[(long)s * nx + c] : T(0);
-        }
-        __syncthreads();
         const int npre = L * TX;
-        for (int idx = threadIdx.x; idx < npre; idx += blockDim.x) {
+        for (int idx = tid; idx < npre; idx += blockDim.x) {
             const int m = idx / TX, c = idx - m * TX;
-            b1[m * TX + c] = pre_inverse<T>(x0r + c, TX, t, m);
+            b1[m * TX + c] = pre_inverse<T>(nat + c, TX, t, m);
         }
         __syncthreads();
         cpx<T>* z = fft_lines<T, true, true>(b1, b0, t, TX, 1, TX);
         const T* zr = reinterpret_cast<const T*>(z);
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        ob = reinterpret_cast<T*>(z == b0 ? b1 : b0);
+        for (int e = tid; e < tot; e += blockDim.x) {
             const int s = e / TX, c = e - s * TX;
-            if (c < wx) {
-                const int d = pack_index(t.kind, n, s);
-                base[(long)s * nx + c] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
-            }
+            const int d = pack_index(t.kind, n, s);
+            ob[e] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
+        }
+    }
+    if (a.bulk) {
+        fence_proxy_async();
+        __syncthreads();
+        bulk_store_rows<T>(base, nx, ob, TX, n, rowb);
+    } else {
+        __syncthreads();
+        for (int e = tid; e < tot; e += blockDim.x) {
+            const int s = e / TX, c = e - s * TX;
+            if (c < wx) base[(long)s * nx + c] = ob[e];
         }
     }
 }
@@ -170,13 +273,11 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <typename T> static size_t row_smem(const DirTab<T>& t, int rpc) {
-    return (size_t)2 * rpc * (t.L > 0 ? t.L : 1) * sizeof(cpx<T>);
-}
-
 template <typename T, typename TIn>
 cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
-    const size_t sm = row_smem(a.t, a.rpc);
+    const size_t L = a.t.L > 0 ? a.t.L : 1;
+    const size_t sm = 16 + (size_t)2 * a.rpc * L * sizeof(cpx<T>) +
+                      (sizeof(TIn) != sizeof(T) ? (size_t)a.rpc * a.t.n * sizeof(TIn) : 0);
     auto kern = k_rows_forward<T, TIn>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -186,7 +287,8 @@ cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int MODE>
 cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
-    const size_t sm = row_smem(a.t, a.rpc);
+    const size_t L = a.t.L > 0 ? a.t.L : 1;
+    const size_t sm = 16 + (size_t)2 * a.rpc * L * sizeof(cpx<T>) + (MODE != OUT_T ? (size_t)a.rpc * a.t.n * 8 : 0);
     auto kern = k_rows_inverse<T, MODE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -196,7 +298,7 @@ cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int TX>
 static cudaError_t launch_cols_tx(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
-    const size_t sm = (size_t)2 * TX * a.t.L * sizeof(cpx<T>);
+    const size_t sm = 16 + (size_t)2 * TX * a.t.L * sizeof(cpx<T>);
     const unsigned grid = (unsigned)(a.nplanes * ((a.nx + TX - 1) / TX));
     if (inverse) {
         auto kern = k_cols<T, TX, true>;

@@ -10,6 +10,8 @@
 // last kernel accumulates the correction into the FP64 solution.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -143,35 +145,48 @@ template <> DirTab<float> DirHost::tab<float>() const {
 
 namespace cales {
 
-template <typename T> int rows_per_cta(int n) {
-    const size_t per_row = 2 * (size_t)(n >= 2 ? n : 2) * sizeof(T);
-    int rpc = (int)((48 * 1024) / per_row);
+// Rows per CTA of the x kernels: about 64 KB of shared memory per CTA
+// (two transform buffers plus the FP64 / pair staging row when used).
+template <typename T> int rows_per_cta(int n, size_t extra_per_elem) {
+    const size_t per_row = (2 * sizeof(T) + extra_per_elem) * (size_t)(n >= 2 ? n : 2);
+    int rpc = (int)((64 * 1024) / per_row);
     if (rpc < 1) rpc = 1;
     if (rpc > 16) rpc = 16;
     return rpc;
 }
 
-template <typename T> int choose_tm(int nz) {
-    const int CK = 16;
-    const int nck = (nz + CK - 1) / CK;
-    const int cands[5] = {128, 64, 32, 16, 8};
-    for (int i = 0; i < 5; ++i) {
-        const size_t sm = ((size_t)nz * cands[i] + (size_t)nck * cands[i] + 2 * (size_t)nz) * sizeof(T);
-        if (sm <= 100 * 1024) return cands[i];
+// z tiles: P threads per mode (segments of the z line) and tm modes per CTA,
+// at most 256 threads and about 100 KB of shared memory per CTA.
+template <typename T> bool choose_zt(int nz, int& tm, int& P) {
+    P = nz >= 96 ? 8 : nz >= 40 ? 4 : nz >= 12 ? 2 : 1;
+    tm = (P >= 4 ? 128 : 256) / P;
+    if (const char* ov = getenv("CALES_ZTILE")) {       // "tm,P" (tuning sweeps)
+        int a = 0, b = 0;
+        if (sscanf(ov, "%d,%d", &a, &b) == 2 && a >= 1 && (b == 1 || b == 2 || b == 4 || b == 8 || b == 16) &&
+            a * b <= 256 && zsolve_smem<T>(nz, a, b) <= 200 * 1024) {
+            tm = a;
+            P = b;
+            return true;
+        }
     }
-    for (int i = 2; i < 5; ++i) {
-        const size_t sm = ((size_t)nz * cands[i] + (size_t)nck * cands[i] + 2 * (size_t)nz) * sizeof(T);
-        if (sm <= 220 * 1024) return cands[i];
-    }
+    const int tm_min = (int)(16 / sizeof(T));
+    while (tm > tm_min && zsolve_smem<T>(nz, tm, P) > 100 * 1024) tm /= 2;
+    while (tm > 1 && zsolve_smem<T>(nz, tm, P) > 200 * 1024) tm /= 2;
+    return zsolve_smem<T>(nz, tm, P) <= 200 * 1024;
+}
+
+// y tiles: the widest tile (<= 32 columns) whose two buffers fit in ~72 KB.
+template <typename T> int choose_tx(int ny) {
+    const int cands[4] = {32, 16, 8, 4};
+    const size_t per_col = 2 * (size_t)(ny >= 2 ? ny : 2) * sizeof(T);
+    for (int i = 0; i < 4; ++i)
+        if (per_col * cands[i] <= 72 * 1024 && cands[i] * sizeof(T) <= 128) return cands[i];
+    for (int i = 0; i < 4; ++i)
+        if (per_col * cands[i] <= 200 * 1024) return cands[i];
     return 0;
 }
 
-template <typename T> int choose_tx(int ny) {
-    const int cands[3] = {sizeof(T) == 8 ? 16 : 32, sizeof(T) == 8 ? 8 : 16, sizeof(T) == 8 ? 4 : 8};
-    for (int i = 0; i < 3; ++i)
-        if ((size_t)2 * cands[i] * (ny >= 2 ? ny : 2) * sizeof(T) <= 160 * 1024) return cands[i];
-    return 0;
-}
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Per-solve options of one pass of the solver.
 struct PassOpt {
@@ -191,10 +206,13 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ra.in = in;
     ra.out = work;
     ra.nrows = nrows;
-    ra.rpc = rows_per_cta<T>(P->nx);
+    ra.rpc = rows_per_cta<T>(P->nx, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     ra.in_scale = 1.0;
     ra.shift_acc = nullptr;
     ra.shift_scale = 0.0;
+    ra.status = P->status;
+    ra.bulk = (aligned16(in) && aligned16(work) && ((size_t)P->nx * sizeof(TIn)) % 16 == 0 &&
+               ((size_t)P->nx * sizeof(T)) % 16 == 0) ? 1 : 0;
     P->prof_begin(st, "x_fwd");
     if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
@@ -205,6 +223,8 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ca.nx = P->nx;
     ca.nplanes = P->nz;
     ca.tx = choose_tx<T>(P->ny);
+    ca.bulk = (aligned16(work) && ((size_t)P->nx * sizeof(T)) % 16 == 0 && ca.tx * sizeof(T) >= 16) ? 1 : 0;
+    ca.status = P->status;
     if (P->ny > 1) {
         P->prof_begin(st, "y_fwd");
         if (launch_cols<T>(ca, false, st) != cudaSuccess) return CALES_ECUDA;
@@ -222,7 +242,8 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.zlo = P->bc[4]; za.zhi = P->bc[5];
     za.singular = o.singular ? 1 : 0;
     za.adjoint = o.adjoint ? 1 : 0;
-    za.tm = choose_tm<T>(P->nz);
+    choose_zt<T>(P->nz, za.tm, za.P);
+    za.bulk = (aligned16(work) && ((size_t)P->nx * P->ny * sizeof(T)) % 16 == 0 && (za.tm * sizeof(T)) % 16 == 0) ? 1 : 0;
     za.sigma = T(o.sigma); za.alpha = T(o.alpha); za.scale = T(o.scale);
     za.status = P->status;
     za.cacc = o.cacc;
@@ -240,6 +261,9 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     RowArgs<T> ri = ra;
     ri.in = work;
     ri.out = out;
+    ri.rpc = rows_per_cta<T>(P->nx, MODE != OUT_T ? 8 : 0);
+    ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
+               ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
     ri.shift_acc = o.shift_acc;
     ri.shift_scale = o.shift_scale;
     P->prof_begin(st, MODE >= OUT_FF_ACC ? "x_inv_acc" : "x_inv");
@@ -386,7 +410,8 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     int rc = build_dir(P->X, nx, bc[0], dx, P->owned);
     if (rc == CALES_OK) rc = build_dir(P->Y, ny, bc[2], dy, P->owned);
     if (rc == CALES_OK) {
-        if (rows_per_cta<double>(nx) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || choose_tm<double>(nz) == 0 ||
+        int tm_, p_;
+        if (rows_per_cta<double>(nx, 0) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || !choose_zt<double>(nz, tm_, p_) ||
             choose_tx<double>(ny) == 0)
             rc = CALES_EUNSUPPORTED;
     }
@@ -406,11 +431,21 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         P->zc_f = dev_upload(zcf, P->owned);
         std::vector<int> st(4, 0);
         P->status = dev_upload(st, P->owned);
+        std::vector<double> idzf(nz), idzc(nz + 1);
+        std::vector<float> idzff(nz), idzcf(nz + 1);
+        for (int k = 0; k < nz; ++k) { idzf[k] = 1.0 / dzf[k]; idzff[k] = (float)idzf[k]; }
+        for (int k = 0; k <= nz; ++k) { idzc[k] = 1.0 / dzc[k]; idzcf[k] = (float)idzc[k]; }
+        P->idzf_d = dev_upload(idzf, P->owned);
+        P->idzc_d = dev_upload(idzc, P->owned);
+        P->idzf_f = dev_upload(idzff, P->owned);
+        P->idzc_f = dev_upload(idzcf, P->owned);
         std::vector<double> acc(4, 0.0);
         P->acc = dev_upload(acc, P->owned);
         P->dzf_sum = 0.0;
         for (int k = 0; k < nz; ++k) P->dzf_sum += dzf[k];
-        if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status || !P->acc) rc = CALES_ENOMEM;
+        if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status || !P->acc || !P->idzf_d ||
+            !P->idzc_d || !P->idzf_f || !P->idzc_f)
+            rc = CALES_ENOMEM;
     }
     if (rc == CALES_OK && cudaDeviceSynchronize() != cudaSuccess) rc = CALES_ECUDA;
     if (rc != CALES_OK) {
@@ -517,3 +552,4 @@ int cales_profile_read(cales_plan_t P, int max, const char** names, float* ms) {
 }
 
 }  // extern "C"
+

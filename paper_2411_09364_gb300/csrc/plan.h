@@ -38,6 +38,10 @@ struct cales_plan_s {
     float* zc_f = nullptr;
     int* status = nullptr;
     double* acc = nullptr;       // [0] consistency constant, [1] gauge sum (refinement)
+    double* idzf_d = nullptr;    // 1/dzf [nz]
+    double* idzc_d = nullptr;    // 1/dzc [nz+1]
+    float* idzf_f = nullptr;
+    float* idzc_f = nullptr;
     double dzf_sum = 0.0;
     int precision = 0, sweeps = 2;
     float* work = nullptr;

@@ -58,7 +58,9 @@ enum cales_status {
     CALES_EUNSUPPORTED = -2, /* odd length > 1 or a radix outside {2,3,5} in x/y,
                                 DF in x/y, periodic z                           */
     CALES_ENOMEM = -3,       /* device allocation failed                        */
-    CALES_ECUDA = -4         /* a CUDA runtime call failed                      */
+    CALES_ECUDA = -4,        /* a CUDA runtime call failed                      */
+    CALES_ETOOBIG = -5       /* grid larger than the static scratch of
+                                cales_poisson_solve_noalloc                     */
 };
 
 enum cales_device_status_bits {
@@ -111,6 +113,25 @@ int cales_helmholtz_solve(cales_plan_t plan, double alpha, const void* f, void* 
  */
 int cales_poisson_solve_adjoint(cales_plan_t plan, const void* w, void* g, void* stream);
 int cales_helmholtz_solve_adjoint(cales_plan_t plan, double alpha, const void* w, void* g, void* stream);
+
+/*
+ * Poisson solve like cales_poisson_solve with FP32 solves and double-float
+ * refinement (the plan's refine_sweeps), for callers that cannot allocate
+ * device memory when they solve: code running inside CUDA stream capture,
+ * hosts that give the library a fixed memory budget, loops that must not
+ * stall in the allocator.  No counterpart in the paper (an interface
+ * addition).  It allocates nothing: its scratch (4 bytes per grid point plus
+ * 256 bytes) is one file-scope device array of the library, sized for at most
+ * 8,388,608 grid points (8 * 2^20); larger grids return CALES_ETOOBIG.  The
+ * plan needs no cales_set_precision call; f, p: double device arrays, f != p.
+ * The first call on each device looks the array's address up with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call on a device shares the one array, which keeps the last
+ * call's contents (the call clears what must start at zero itself): calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.
+ */
+int cales_poisson_solve_noalloc(cales_plan_t plan, const void* f, void* p, void* stream);
 
 /*
  * FP64 residual r = f - L u (alpha < 0 selects Poisson) or r = f - (I - alpha L) u.

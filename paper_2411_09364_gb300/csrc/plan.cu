@@ -515,6 +515,7 @@ const char* cales_strerror(int code) {
         case CALES_EUNSUPPORTED: return "unsupported size or boundary combination";
         case CALES_ENOMEM: return "device allocation failed";
         case CALES_ECUDA: return "CUDA runtime error";
+        case CALES_ETOOBIG: return "grid exceeds the 8388608-point static scratch of cales_poisson_solve_noalloc";
         default: return "unknown error";
     }
 }
@@ -553,3 +554,89 @@ int cales_profile_read(cales_plan_t P, int max, const char** names, float* ms) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Poisson solve (FP32 + double-float refinement) that allocates nothing.
+//
+// Some callers cannot allocate device memory at solve time: code that runs
+// while a CUDA stream is being captured into a graph (cudaMalloc is not
+// allowed there), hosts that hand the library a fixed memory budget and fail
+// any further allocation, and real-time loops that must not stall in the
+// allocator.  This entry point takes its scratch (the FP32 mode-space field
+// and two FP64 accumulators) from one file-scope device array instead of the
+// plan's workspace, so a plan never needs cales_set_precision(FP32_REFINE).
+// The array is CALES_STATIC_SCRATCH_POINTS floats plus 256 bytes; every GPU
+// that loads this library holds it until the process exits.
+// ---------------------------------------------------------------------------
+#define CALES_STATIC_SCRATCH_POINTS (8L * 1024 * 1024)
+static __device__ __align__(256) unsigned char g_static_scratch[256 + CALES_STATIC_SCRATCH_POINTS * sizeof(float)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device (looked up once
+// per device with that device current; the host symbol is not an address).
+int static_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CALES_ECUDA;
+    if (!g_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return CALES_ECUDA;
+        g_scratch_addr[dev] = ptr;
+    }
+    *out = g_scratch_addr[dev];
+    return CALES_OK;
+}
+}  // namespace
+
+extern "C" int cales_poisson_solve_noalloc(cales_plan_t P, const void* f, void* p, void* stream) {
+    if (!P || !f || !p || f == p) return CALES_EINVAL;
+    if ((long)P->nx * P->ny * P->nz > CALES_STATIC_SCRATCH_POINTS) return CALES_ETOOBIG;
+    void* base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc) return rc;
+    double* acc = reinterpret_cast<double*>(base);
+    float* work = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(base) + 256);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PassOpt o;
+    o.sigma = 0.0;
+    o.alpha = 1.0;
+    o.scale = -1.0 / ((double)P->nx * (double)P->ny);
+    o.singular = P->singular_poisson != 0;
+    o.adjoint = false;
+    o.cacc = o.singular ? acc : nullptr;
+    o.shift_acc = nullptr;
+    o.shift_scale = 0.0;
+    const int ns = P->sweeps;
+    const bool sing = o.singular;
+    // the array keeps the previous call's contents: clear the accumulators
+    if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+    rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, work, o, st)
+                 : pipeline<float, double, OUT_FF_INIT>(P, f, p, work, o, st);
+    if (rc) return rc;
+    for (int s = 0; s < ns; ++s) {
+        if (sing && cudaMemsetAsync(acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+        ResidFFArgs ra;
+        ra.f = (const double*)f;
+        ra.u = (const float2*)p;
+        ra.r = work;
+        ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
+        ra.bcx = P->bc[0]; ra.bcy = P->bc[2]; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
+        split_double(1.0 / (P->dx * P->dx), ra.cxh, ra.cxl);
+        split_double(1.0 / (P->dy * P->dy), ra.cyh, ra.cyl);
+        ra.c0h = 0.0f;
+        ra.za = P->za_d;
+        ra.zc = P->zc_d;
+        ra.c1 = 1.0;
+        ra.cshift = sing ? acc : nullptr;
+        ra.gacc = sing ? acc + 1 : nullptr;
+        ra.dzf = P->dzf_d;
+        if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
+        o.shift_acc = sing ? acc + 1 : nullptr;
+        o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
+        rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, work, p, work, o, st)
+                           : pipeline<float, float, OUT_FF_ACC>(P, work, p, work, o, st);
+        if (rc) return rc;
+    }
+    return CALES_OK;
+}

@@ -51,6 +51,8 @@ template <typename T> struct ZArgs {
     int adjoint;         // apply D S D^-1 (D = diag(dzf))
     int tm;              // modes per CTA
     int P;               // threads per mode (segments of the z line)
+    int maxm;            // > 0: register-pivot kernel for segments of at most maxm rows
+    int warp_mode;       // warp-per-segment kernel (32 modes per CTA, P warps)
     int bulk;            // tile rows may be moved with TMA bulk copies
     T sigma, alpha, scale;
     int* status;         // device status word (bit flags)
@@ -97,6 +99,8 @@ template <typename T, int MODE> cudaError_t launch_rows_inverse(const RowArgs<T>
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st);
 template <typename T> cudaError_t launch_zsolve(const ZArgs<T>& a, cudaStream_t st);
 template <typename T> size_t zsolve_smem(int nz, int tm, int P);
+template <typename T> size_t zsolve_reg_smem(int nz, int tm, int P);
+template <typename T> size_t zsolve_w_smem(int nz, int P);
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
 cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st);
 

@@ -198,26 +198,20 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     const int wx = min(TX, nx - x0);
     const int tid = threadIdx.x;
     T* __restrict__ base = reinterpret_cast<T*>(a.data) + (long)plane * n * nx + x0;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
     cpx<T>* b1 = b0 + TX * L;
     const int tot = n * TX;
-    const uint32_t rowb = (uint32_t)(wx * sizeof(T));
     // natural-order tile into `nat`
     T* nat = reinterpret_cast<T*>(INV ? b0 : b1);
+    constexpr int EPC = 16 / (int)sizeof(T);
+    constexpr int CPR = TX / EPC > 0 ? TX / EPC : 1;
     if (a.bulk) {
-        if (tid == 0) mbar_init(bar, 1);
-        __syncthreads();
-        bulk_load_rows<T>(bar, nat, TX, base, nx, n, rowb);
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
-            return;
+        // 16-byte cp.async chunks, all in flight; columns past the ragged edge zero-filled
+        for (int e = tid; e < n * CPR; e += blockDim.x) {
+            const int s = e / CPR, c0 = (e - s * CPR) * EPC;
+            cp_async16(nat + s * TX + c0, base + (long)s * nx + (c0 < wx ? c0 : 0), c0 < wx);
         }
-        if (wx < TX)
-            for (int e = tid; e < tot; e += blockDim.x)
-                if ((e % TX) >= wx) nat[e] = T(0);
+        cp_async_wait_all();
     } else {
         for (int e = tid; e < tot; e += blockDim.x) {
             const int s = e / TX, c = e - s * TX;
@@ -257,12 +251,14 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             ob[e] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
         }
     }
+    __syncthreads();
     if (a.bulk) {
-        fence_proxy_async();
-        __syncthreads();
-        bulk_store_rows<T>(base, nx, ob, TX, n, rowb);
+        for (int e = tid; e < n * CPR; e += blockDim.x) {
+            const int s = e / CPR, c0 = (e - s * CPR) * EPC;
+            if (c0 < wx)
+                *reinterpret_cast<float4*>(base + (long)s * nx + c0) = *reinterpret_cast<const float4*>(ob + s * TX + c0);
+        }
     } else {
-        __syncthreads();
         for (int e = tid; e < tot; e += blockDim.x) {
             const int s = e / TX, c = e - s * TX;
             if (c < wx) base[(long)s * nx + c] = ob[e];

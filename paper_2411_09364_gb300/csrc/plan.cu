@@ -155,24 +155,53 @@ template <typename T> int rows_per_cta(int n, size_t extra_per_elem) {
     return rpc;
 }
 
-// z tiles: P threads per mode (segments of the z line) and tm modes per CTA,
+// z tiles: P threads per mode (segments of the z line), tm modes per CTA and
+// the register bound maxm on the rows of a segment (register-pivot kernel);
 // at most 256 threads and about 100 KB of shared memory per CTA.
-template <typename T> bool choose_zt(int nz, int& tm, int& P) {
-    P = nz >= 96 ? 8 : nz >= 40 ? 4 : nz >= 12 ? 2 : 1;
-    tm = (P >= 4 ? 128 : 256) / P;
-    if (const char* ov = getenv("CALES_ZTILE")) {       // "tm,P" (tuning sweeps)
-        int a = 0, b = 0;
-        if (sscanf(ov, "%d,%d", &a, &b) == 2 && a >= 1 && (b == 1 || b == 2 || b == 4 || b == 8 || b == 16) &&
-            a * b <= 256 && zsolve_smem<T>(nz, a, b) <= 200 * 1024) {
-            tm = a;
-            P = b;
+template <typename T> bool choose_zt(int nz, int& tm, int& P, int& maxm, int& warp_mode) {
+    // default: warp-per-segment kernel, P = ceil(nz / maxm) warps of 32 modes
+    warp_mode = 0;
+    {
+        // measured on GB300: 16-row segments up to nz = 256, then 32 (P <= 16 warps)
+        int mm = nz <= 256 ? 16 : (nz <= 512 ? 32 : 64);
+        int pw = (nz + mm - 1) / mm;
+        const char* ov = getenv("CALES_ZTILE");
+        int a = 0, b = 0, c = 0;
+        if (ov && sscanf(ov, "w,%d,%d", &b, &c) == 2 && (c == 16 || c == 32 || c == 64) && b >= 1 && b <= 16) {
+            pw = b; mm = c;
+        } else if (ov && sscanf(ov, "%d,%d,%d", &a, &b, &c) >= 2) {
+            pw = 0;
+        }
+        if (pw >= 1 && pw <= 16 && (nz + pw - 1) / pw <= mm && zsolve_w_smem<T>(nz, pw) <= 200 * 1024) {
+            warp_mode = 1; P = pw; maxm = mm; tm = 32;
             return true;
         }
     }
+    if (nz <= 16) { P = 1; maxm = 16; }
+    else if (nz <= 32) { P = 2; maxm = 16; }
+    else if (nz <= 64) { P = 4; maxm = 16; }
+    else if (nz <= 128) { P = 8; maxm = 16; }
+    else if (nz <= 256) { P = 8; maxm = 32; }
+    else if (nz <= 512) { P = 8; maxm = 64; }
+    else if (nz <= 1024) { P = 16; maxm = 64; }
+    else { P = 16; maxm = 0; }
+    if (sizeof(T) == 8 && maxm == 64) { P = 16; maxm = 32; if (nz > 512) maxm = 64; }
+    tm = 128 / P;
+    if (const char* ov = getenv("CALES_ZTILE")) {       // "tm,P,maxm" (tuning sweeps)
+        int a = 0, b = 0, c = 0;
+        const int n = sscanf(ov, "%d,%d,%d", &a, &b, &c);
+        if (n >= 2 && a >= 1 && (b == 1 || b == 2 || b == 4 || b == 8 || b == 16) && a * b <= 256) {
+            tm = a; P = b;
+            maxm = n == 3 ? c : 0;
+        }
+    }
+    const int m = (nz + P - 1) / P;
+    if (maxm > 0 && m > maxm) maxm = 0;
+    auto smem = [&](int t) { return maxm > 0 ? zsolve_reg_smem<T>(nz, t, P) : zsolve_smem<T>(nz, t, P); };
     const int tm_min = (int)(16 / sizeof(T));
-    while (tm > tm_min && zsolve_smem<T>(nz, tm, P) > 100 * 1024) tm /= 2;
-    while (tm > 1 && zsolve_smem<T>(nz, tm, P) > 200 * 1024) tm /= 2;
-    return zsolve_smem<T>(nz, tm, P) <= 200 * 1024;
+    while (tm > tm_min && smem(tm) > 100 * 1024) tm /= 2;
+    while (tm > 1 && smem(tm) > 200 * 1024) tm /= 2;
+    return smem(tm) <= 200 * 1024;
 }
 
 // y tiles: the widest tile (<= 32 columns) whose two buffers fit in ~72 KB.
@@ -242,7 +271,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.zlo = P->bc[4]; za.zhi = P->bc[5];
     za.singular = o.singular ? 1 : 0;
     za.adjoint = o.adjoint ? 1 : 0;
-    choose_zt<T>(P->nz, za.tm, za.P);
+    choose_zt<T>(P->nz, za.tm, za.P, za.maxm, za.warp_mode);
     za.bulk = (aligned16(work) && ((size_t)P->nx * P->ny * sizeof(T)) % 16 == 0 && (za.tm * sizeof(T)) % 16 == 0) ? 1 : 0;
     za.sigma = T(o.sigma); za.alpha = T(o.alpha); za.scale = T(o.scale);
     za.status = P->status;
@@ -410,8 +439,8 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     int rc = build_dir(P->X, nx, bc[0], dx, P->owned);
     if (rc == CALES_OK) rc = build_dir(P->Y, ny, bc[2], dy, P->owned);
     if (rc == CALES_OK) {
-        int tm_, p_;
-        if (rows_per_cta<double>(nx, 0) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || !choose_zt<double>(nz, tm_, p_) ||
+        int tm_, p_, mm_, wm_;
+        if (rows_per_cta<double>(nx, 0) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || !choose_zt<double>(nz, tm_, p_, mm_, wm_) ||
             choose_tx<double>(ny) == 0)
             rc = CALES_EUNSUPPORTED;
     }

@@ -184,6 +184,44 @@ int cales_sq_error(const float* const* pred, const float* const* target, float* 
 int cales_adam_step(float* theta, const double* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
                     float eps, int t, float grad_scale, void* stream);
 
+/*
+ * Launch schedule of a plan: {x shared-memory budget per CTA in KB, y tile
+ * width in columns, z warps per CTA, z rows-per-segment bound}; 0 selects the
+ * built-in heuristic.  Infeasible values fall back to the heuristic.
+ */
+int cales_set_schedule(cales_plan_t plan, const int sched[4]);
+int cales_get_schedule(cales_plan_t plan, int sched[4]);
+
+/*
+ * Autotuner (the analogue of the paper's runtime-tuned decomposition and
+ * communication backends, Sec. 3.1): times candidate schedules of the plan's
+ * Poisson solve at its current precision on the device (each stage tuned in
+ * turn: x budget 32/64/96 KB, y tiles 8/16/32, z segments 16/32/64 rows),
+ * keeps the fastest and sets it on the plan.  With cache_path non-NULL the
+ * result is looked up first and stored after tuning in a JSON object keyed by
+ * "nx,ny,nz,bcx,bcy,zlo,zhi,precision,device".  Allocates two temporary fields
+ * and synchronises `stream`: call it at set-up, not inside a capture.
+ */
+int cales_autotune(cales_plan_t plan, const char* cache_path, void* stream);
+
+/*
+ * Batched solves (a Runge-Kutta substep of Algorithm 1: per domain the three
+ * Helmholtz solves of Eq. 18 and the Poisson solve of Eq. 12, over many
+ * independent domains).  kinds[i]: 0 = Poisson, 1 = Helmholtz with alphas[i].
+ * Solves are forked over up to 8 streams balanced by grid size (solves that
+ * share a plan stay on one stream) and joined back on the caller's stream.
+ * cales_batch_solve enqueues directly; cales_batch_capture records the same
+ * fork/join for fixed f[i], u[i] into one CUDA graph, replayed by
+ * cales_batch_launch with a single launch.  Plans, precisions and the
+ * pointers captured must stay valid while the graph is used.
+ */
+int cales_batch_create(cales_batch_t* out, int n, const cales_plan_t* plans, const int* kinds, const double* alphas);
+int cales_batch_solve(cales_batch_t batch, const void* const* f, void* const* u, void* stream);
+int cales_batch_capture(cales_batch_t batch, const void* const* f, void* const* u, void* stream);
+int cales_batch_launch(cales_batch_t batch, void* stream);
+int cales_batch_graph_nodes(cales_batch_t batch, unsigned long* nodes);
+void cales_batch_destroy(cales_batch_t batch);
+
 /* Asynchronous zero fill of `bytes` bytes of device memory (accumulators). */
 int cales_zero(void* p, unsigned long bytes, void* stream);
 

@@ -35,6 +35,15 @@ SIGNATURES = {
     "cales_gradient": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cales_divergence_adjoint": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cales_zero": (C.c_int, [vp, C.c_ulong, vp]),
+    "cales_set_schedule": (C.c_int, [vp, ip]),
+    "cales_get_schedule": (C.c_int, [vp, ip]),
+    "cales_autotune": (C.c_int, [vp, C.c_char_p, vp]),
+    "cales_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp), ip, dp]),
+    "cales_batch_solve": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
+    "cales_batch_capture": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
+    "cales_batch_launch": (C.c_int, [vp, vp]),
+    "cales_batch_graph_nodes": (C.c_int, [vp, C.POINTER(C.c_ulong)]),
+    "cales_batch_destroy": (None, [vp]),
     "cales_gradient_adjoint": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "cales_stencil27": (C.c_int, [vp, vp, C.c_float, C.c_float, C.POINTER(vp), C.POINTER(vp), vp]),
     "cales_stencil27_weight_grad": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp, vp]),

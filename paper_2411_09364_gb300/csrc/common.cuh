@@ -357,4 +357,38 @@ __device__ __forceinline__ ff ff_from_double(double v) {
 }
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
+// 2^k as a float for k in [-126, 127] (bit construction, no FP64 / MUFU).
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// Double -> float by truncating the significand to 24 bits, with integer
+// operations only (GB300's FP64 pipe is ~1/64 of the FP32 rate, and
+// conversions run on it).  |d| below 2^-126 flushes to zero.
+__device__ __forceinline__ float trunc_double_int(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hw = (unsigned)(b >> 32);
+    const unsigned sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7ff);
+    const int ef = e - 1023 + 127;
+    if (ef <= 0) return __int_as_float(sign);
+    if (ef >= 255) return __int_as_float(sign | 0x7f800000u | (e == 0x7ff && (b << 12) ? 0x400000u : 0u));
+    const unsigned mh = (unsigned)((b >> 29) & 0x7fffffu);
+    return __int_as_float(sign | ((unsigned)ef << 23) | mh);
+}
+
+// Double -> double-float pair (hi = 24-bit truncation, lo = the remaining 29
+// significand bits rounded to a float), integer and FP32 operations only;
+// hi + lo carries about 48 bits of d.
+__device__ __forceinline__ ff split_double_int(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const float hi = trunc_double_int(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int ef = e - 1023 + 127;
+    if (ef <= 0 || ef >= 255) return ff{hi, 0.f};
+    const unsigned rem = (unsigned)(b & 0x1fffffffu);            // low 29 bits of the significand
+    float lo = __uint2float_rn(rem);                             // exact to 24 bits
+    const int k = e - 1075;                                      // weight of bit 0
+    lo = lo * pow2f(max(k + 50, -126)) * pow2f(-50);
+    return ff{hi, (b >> 63) ? -lo : lo};
+}
+
 }  // namespace cales

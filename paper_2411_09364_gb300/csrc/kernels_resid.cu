@@ -54,8 +54,8 @@ cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Double-float residual (FP32 pipes).  u is stored as (hi, lo) float pairs;
-// each difference and product is carried in double-float, and only the final
-// f - t.hi is taken in FP64 (one FP64 operation per point).  One CTA row of
+// each difference and product is carried in double-float, and f is split
+// into a pair with integer operations, so no FP64 instruction runs per point.  One CTA row of
 // the grid per z-plane, so the dzf weight of the gauge sum is uniform in it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ ff ldu(const float2* __restrict__ u, long i) {
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
         t = ff_add(t, ff_mul(za, ff_sub(pd, pc)));
         if (a.c0h != 0.f) t = ff_add(t, pc);
         t = ff_add(t, csh);
-        const double d = a.f[idx] - (double)t.hi;
-        a.r[idx] = __fsub_rn(__double2float_rn(d), t.lo);
+        const ff r = ff_sub(split_double_int(a.f[idx]), t);
+        a.r[idx] = __fadd_rn(r.hi, r.lo);
         if (a.gacc) sum = ff_add(sum, pc);
     }
     if (a.gacc) {

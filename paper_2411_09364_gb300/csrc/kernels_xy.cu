@@ -57,7 +57,10 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     T* r0 = reinterpret_cast<T*>(b0);
     for (int e = tid; e < tot; e += blockDim.x) {
         const int r = e / n, s = e - r * n;
-        r0[r * n + pack_index(t.kind, n, s)] = T(stage[e]) * sc * pack_sign<T>(t.kind, s);
+        T v;
+        if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));   // FP64 input, FP32 solve
+        else v = T(stage[e]);
+        r0[r * n + pack_index(t.kind, n, s)] = v * sc * pack_sign<T>(t.kind, s);
     }
     __syncthreads();
     cpx<T>* Z = fft_lines<T, false, false>(b0, b1, t, nr, L, 1);

@@ -147,9 +147,9 @@ namespace cales {
 
 // Rows per CTA of the x kernels: about 64 KB of shared memory per CTA
 // (two transform buffers plus the FP64 / pair staging row when used).
-template <typename T> int rows_per_cta(int n, size_t extra_per_elem) {
+template <typename T> int rows_per_cta(int n, size_t extra_per_elem, int budget_kb = 64) {
     const size_t per_row = (2 * sizeof(T) + extra_per_elem) * (size_t)(n >= 2 ? n : 2);
-    int rpc = (int)((64 * 1024) / per_row);
+    int rpc = (int)(((size_t)(budget_kb > 0 ? budget_kb : 64) * 1024) / per_row);
     if (rpc < 1) rpc = 1;
     if (rpc > 16) rpc = 16;
     return rpc;
@@ -158,13 +158,17 @@ template <typename T> int rows_per_cta(int n, size_t extra_per_elem) {
 // z tiles: P threads per mode (segments of the z line), tm modes per CTA and
 // the register bound maxm on the rows of a segment (register-pivot kernel);
 // at most 256 threads and about 100 KB of shared memory per CTA.
-template <typename T> bool choose_zt(int nz, int& tm, int& P, int& maxm, int& warp_mode) {
+template <typename T> bool choose_zt(int nz, int& tm, int& P, int& maxm, int& warp_mode, int fw = 0, int fm = 0) {
     // default: warp-per-segment kernel, P = ceil(nz / maxm) warps of 32 modes
     warp_mode = 0;
     {
         // measured on GB300: 16-row segments up to nz = 256, then 32 (P <= 16 warps)
         int mm = nz <= 256 ? 16 : (nz <= 512 ? 32 : 64);
         int pw = (nz + mm - 1) / mm;
+        if ((fm == 16 || fm == 32 || fm == 64) && fw >= 1 && fw <= 16 && (nz + fw - 1) / fw <= fm) {
+            pw = fw;
+            mm = fm;
+        }
         const char* ov = getenv("CALES_ZTILE");
         int a = 0, b = 0, c = 0;
         if (ov && sscanf(ov, "w,%d,%d", &b, &c) == 2 && (c == 16 || c == 32 || c == 64) && b >= 1 && b <= 16) {
@@ -205,8 +209,10 @@ template <typename T> bool choose_zt(int nz, int& tm, int& P, int& maxm, int& wa
 }
 
 // y tiles: the widest tile (<= 32 columns) whose two buffers fit in ~72 KB.
-template <typename T> int choose_tx(int ny) {
+template <typename T> int choose_tx(int ny, int forced = 0) {
     const int cands[4] = {32, 16, 8, 4};
+    if (forced == 4 || forced == 8 || forced == 16 || forced == 32)
+        if ((size_t)2 * forced * (ny >= 2 ? ny : 2) * sizeof(T) <= 200 * 1024 && forced * sizeof(T) >= 16) return forced;
     const size_t per_col = 2 * (size_t)(ny >= 2 ? ny : 2) * sizeof(T);
     for (int i = 0; i < 4; ++i)
         if (per_col * cands[i] <= 72 * 1024 && cands[i] * sizeof(T) <= 128) return cands[i];
@@ -235,7 +241,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ra.in = in;
     ra.out = work;
     ra.nrows = nrows;
-    ra.rpc = rows_per_cta<T>(P->nx, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    ra.rpc = rows_per_cta<T>(P->nx, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0, P->sched[0]);
     ra.in_scale = 1.0;
     ra.shift_acc = nullptr;
     ra.shift_scale = 0.0;
@@ -251,7 +257,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ca.data = work;
     ca.nx = P->nx;
     ca.nplanes = P->nz;
-    ca.tx = choose_tx<T>(P->ny);
+    ca.tx = choose_tx<T>(P->ny, P->sched[1]);
     ca.bulk = (aligned16(work) && ((size_t)P->nx * sizeof(T)) % 16 == 0 && ca.tx * sizeof(T) >= 16) ? 1 : 0;
     ca.status = P->status;
     if (P->ny > 1) {
@@ -271,7 +277,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.zlo = P->bc[4]; za.zhi = P->bc[5];
     za.singular = o.singular ? 1 : 0;
     za.adjoint = o.adjoint ? 1 : 0;
-    choose_zt<T>(P->nz, za.tm, za.P, za.maxm, za.warp_mode);
+    choose_zt<T>(P->nz, za.tm, za.P, za.maxm, za.warp_mode, P->sched[2], P->sched[3]);
     za.bulk = (aligned16(work) && ((size_t)P->nx * P->ny * sizeof(T)) % 16 == 0 && (za.tm * sizeof(T)) % 16 == 0) ? 1 : 0;
     za.sigma = T(o.sigma); za.alpha = T(o.alpha); za.scale = T(o.scale);
     za.status = P->status;
@@ -290,7 +296,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     RowArgs<T> ri = ra;
     ri.in = work;
     ri.out = out;
-    ri.rpc = rows_per_cta<T>(P->nx, MODE != OUT_T ? 8 : 0);
+    ri.rpc = rows_per_cta<T>(P->nx, MODE != OUT_T ? 8 : 0, P->sched[0]);
     ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
                ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
     ri.shift_acc = o.shift_acc;
@@ -362,6 +368,13 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
         if (rc) return rc;
     }
     return CALES_OK;
+}
+
+static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream);
+
+int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint, const void* f, void* p,
+                         void* stream) {
+    return solve_common(P, helm, alpha, adjoint, f, p, stream);
 }
 
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {

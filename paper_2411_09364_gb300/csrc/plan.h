@@ -25,6 +25,11 @@ struct ProfRec {
     cudaEvent_t a = nullptr, b = nullptr;
 };
 
+struct cales_plan_s;
+// Internal entry shared by the C ABI, the batch executor and the autotuner.
+int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint, const void* f, void* p,
+                         void* stream);
+
 struct cales_plan_s {
     int nx = 0, ny = 0, nz = 0;
     int bc[6] = {0};
@@ -44,6 +49,9 @@ struct cales_plan_s {
     float* idzc_f = nullptr;
     double dzf_sum = 0.0;
     int precision = 0, sweeps = 2;
+    // launch schedule (0 = built-in heuristic): x shared-memory budget in KB,
+    // y tile width, z warps per CTA, z rows per segment bound
+    int sched[4] = {0, 0, 0, 0};
     float* work = nullptr;
     std::vector<void*> owned;
     static constexpr int PROF_MAX = 4096;

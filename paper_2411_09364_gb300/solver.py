@@ -132,6 +132,21 @@ class Plan:
                                        _ptr(out, torch.float64, n, "out"), _stream(stream)), "cales_residual")
         return out
 
+    def set_schedule(self, sched):
+        arr = (C.c_int * 4)(*[int(v) for v in sched])
+        N.check(N.lib().cales_set_schedule(self._h, arr), "cales_set_schedule")
+
+    def schedule(self):
+        arr = (C.c_int * 4)()
+        N.check(N.lib().cales_get_schedule(self._h, arr), "cales_get_schedule")
+        return tuple(arr)
+
+    def autotune(self, cache_path=None, stream=None):
+        """Time candidate schedules on the device (or read them from the JSON cache)."""
+        path = None if cache_path is None else str(cache_path).encode()
+        N.check(N.lib().cales_autotune(self._h, path, _stream(stream)), "cales_autotune")
+        return self.schedule()
+
     def status(self) -> int:
         v = C.c_int(0)
         N.check(N.lib().cales_get_status(self._h, C.byref(v)), "cales_get_status")

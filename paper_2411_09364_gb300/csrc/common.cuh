@@ -44,10 +44,24 @@ template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot90(cpx<T> a
 template <typename T> struct DirTab {
     int n, kind, L, nrad;
     int radix[MAX_RADICES];
+    int nsv[MAX_RADICES];          // sub-transform size Ns before pass p
+    int tstep[MAX_RADICES];        // twiddle index step L / (Ns R) of pass p
+    unsigned nbmag[MAX_RADICES];   // fast-division magic of L / R_p
+    unsigned nsmag[MAX_RADICES];   // fast-division magic of Ns_p
+    unsigned nmag, l1mag, lmag;    // magics of n, L + 1 and L
     const cpx<T>* tw;     // W_L^t = exp(-2 pi i t / L), t in [0, L)
     const cpx<T>* post;   // W_n^m = exp(-2 pi i m / n), m in [0, L]
     const cpx<T>* mak;    // exp(-i pi m / (2n)),        m in [0, L]
 };
+
+// q = n / d for the small operands of the transforms (n * d < 2^32): the
+// magic is ceil(2^32 / d), 0 encoding d = 1 (Granlund-Montgomery style
+// multiply-high; exact since the rounding error n * (magic*d - 2^32) / 2^32
+// stays below 1/d).
+__host__ __device__ __forceinline__ unsigned div_magic(unsigned d) {
+    return d <= 1 ? 0u : (unsigned)((0x100000000ull + d - 1) / d);
+}
+__device__ __forceinline__ unsigned fdivu(unsigned n, unsigned mag) { return mag ? __umulhi(n, mag) : n; }
 
 // ---------------------------------------------------------------------------
 // Radix butterflies (forward: exp(-2 pi i / R); inverse: conjugate)
@@ -122,29 +136,36 @@ template <typename T, bool INV> struct Bfly<T, 8, INV> {
 // (Govindaraju et al., SC'08 formulation): reads element j + r*L/R, applies
 // the twiddles of sub-transform position k = j mod Ns, writes to
 // (j - k)*R + k + r*Ns.  Lines: element e of line l at l*ls + e*es.
-// LINES_FAST maps consecutive threads to consecutive lines (column tiles).
+// TXC > 0: TXC lines (tile columns), consecutive threads -> consecutive lines;
+// TXC == 0: consecutive threads -> consecutive butterflies of one line.
+// Divisions by run-time sizes use precomputed multiply-high magics.
 // ---------------------------------------------------------------------------
-template <typename T, int R, bool INV, bool LINES_FAST>
+template <typename T, int R, bool INV, int TXC>
 __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
-                                              int L, int Ns, int nlines, int ls, int es,
+                                              const DirTab<T>& t, int p, int nlines, int ls, int es,
                                               const cpx<T>* __restrict__ tw) {
+    const int L = t.L;
     const int nb = L / R;
-    const int total = nb * nlines;
-    const int tstep = L / (Ns * R);
+    const int Ns = t.nsv[p];
+    const unsigned nsmag = t.nsmag[p];
+    const int tstep = t.tstep[p];
+    const unsigned nbmag = t.nbmag[p];
+    const int total = nb * (TXC > 0 ? TXC : nlines);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int line, j;
-        if (LINES_FAST) { j = idx / nlines; line = idx - j * nlines; }
-        else            { line = idx / nb;  j = idx - line * nb; }
+        if (TXC > 0) { j = idx / (TXC > 0 ? TXC : 1); line = idx - j * TXC; }
+        else { line = (int)fdivu((unsigned)idx, nbmag); j = idx - line * nb; }
         const cpx<T>* s = src + line * ls;
         cpx<T>* d = dst + line * ls;
-        const int k = j % Ns;
+        const int k = j - (int)fdivu((unsigned)j, nsmag) * Ns;
         cpx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
         if (Ns > 1) {
+            const int ks = k * tstep;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                cpx<T> w = tw[r * k * tstep];
+                const cpx<T> w = tw[r * ks];
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
@@ -156,22 +177,21 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
 }
 
 // All passes of a length-L FFT; returns the buffer holding the result.
-template <typename T, bool INV, bool LINES_FAST>
-__device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es) {
-    int Ns = 1;
+// `tw` is the twiddle table W_L^t staged in shared memory by the caller.
+template <typename T, bool INV, int TXC>
+__device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
+                             const cpx<T>* tw) {
     cpx<T>* src = b0;
     cpx<T>* dst = b1;
     for (int p = 0; p < t.nrad; ++p) {
-        const int R = t.radix[p];
-        switch (R) {
-            case 8: stockham_pass<T, 8, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
-            case 4: stockham_pass<T, 4, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
-            case 2: stockham_pass<T, 2, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
-            case 3: stockham_pass<T, 3, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
-            default: stockham_pass<T, 5, INV, LINES_FAST>(src, dst, t.L, Ns, nlines, ls, es, t.tw); break;
+        switch (t.radix[p]) {
+            case 8: stockham_pass<T, 8, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
+            case 4: stockham_pass<T, 4, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
+            case 2: stockham_pass<T, 2, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
+            case 3: stockham_pass<T, 3, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
+            default: stockham_pass<T, 5, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
         }
         __syncthreads();
-        Ns *= R;
         cpx<T>* tmp = src; src = dst; dst = tmp;
     }
     return src;

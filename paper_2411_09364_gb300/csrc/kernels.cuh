@@ -90,6 +90,7 @@ struct ResidFFArgs {
     const double* cshift;
     double* gacc;
     const double* dzf;
+    int rows_per_cta;    // set by the launcher
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };

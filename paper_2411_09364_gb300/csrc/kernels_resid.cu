@@ -65,42 +65,91 @@ __device__ __forceinline__ ff ldu(const float2* __restrict__ u, long i) {
 
 __device__ __forceinline__ ff ghost_ff(int kind, ff c) { return kind == KIND_N ? c : ff_neg(c); }
 
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return ff{p, __fmaf_rn(a, b, -p)};
+}
+
+// r = f - cshift - (c0 u + c1 L u) with u = (hi, lo) pairs, written with the
+// neighbour differences first,
+//   f - cshift - c0 uc - [cx ((ue-uc) + (uw-uc)) + cy ((un-uc) + (us-uc))
+//                         + zc (uu-uc) + za (ud-uc)],
+// so rounding errors scale with the (small) differences of a smooth u, not
+// with u times the large 1/dz^2 couplings.  Differences of the hi parts are
+// exact (TwoSum), products of the leading parts exact (TwoProd by FMA), the
+// accumulation is TwoSum with every rounding error gathered in one FP32
+// compensation term, and the lo parts (2^-24 smaller) and the low halves of
+// the coefficients enter that term in plain FP32: about double-float accuracy
+// with fewer instructions.
 __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
-    const long nx = a.nx, ny = a.ny;
-    const long plane = nx * ny;
+    const int nx = a.nx, ny = a.ny;
+    const long plane = (long)nx * ny;
     const int k = blockIdx.y;
     const long kbase = (long)k * plane;
     const float2* __restrict__ u = a.u;
-    const ff za = ff_from_double(a.c1 * a.za[k]);
-    const ff zc = ff_from_double(a.c1 * a.zc[k]);
+    // plane coefficients (FP64 once per CTA, then split)
+    const double zad = a.c1 * a.za[k], zcd = a.c1 * a.zc[k];
+    const double cxd = (double)a.cxh + (double)a.cxl, cyd = (double)a.cyh + (double)a.cyl;
+    const ff za = ff_from_double(zad), zc = ff_from_double(zcd);
     const ff cx{a.cxh, a.cxl}, cy{a.cyh, a.cyl};
+    const float c0 = a.c0h;     // 0 (Poisson) or 1 (Helmholtz): c0 u is exact
+    (void)cxd; (void)cyd;
     const ff csh = a.cshift ? ff_from_double(a.cshift[0]) : ff{0.f, 0.f};
-    const ff zero{0.f, 0.f};
-    ff sum{0.f, 0.f};
-    for (long rem = (long)blockIdx.x * blockDim.x + threadIdx.x; rem < plane; rem += (long)gridDim.x * blockDim.x) {
-        const long j = rem / nx, i = rem - j * nx;
-        const long idx = kbase + rem;
-        const ff pc = ldu(u, idx);
-        const ff pw = i > 0 ? ldu(u, idx - 1) : (a.bcx == KIND_P ? ldu(u, idx + nx - 1) : ghost_ff(a.bcx, pc));
-        const ff pe = i < nx - 1 ? ldu(u, idx + 1) : (a.bcx == KIND_P ? ldu(u, idx - (nx - 1)) : ghost_ff(a.bcx, pc));
-        const ff ps = j > 0 ? ldu(u, idx - nx) : (a.bcy == KIND_P ? ldu(u, idx + (ny - 1) * nx) : ghost_ff(a.bcy, pc));
-        const ff pn = j < ny - 1 ? ldu(u, idx + nx) : (a.bcy == KIND_P ? ldu(u, idx - (ny - 1) * nx) : ghost_ff(a.bcy, pc));
-        const ff pd = k > 0 ? ldu(u, idx - plane) : (a.zlo == ZBC_N ? pc : (a.zlo == ZBC_D ? ff_neg(pc) : zero));
-        const ff pu = k < a.nz - 1 ? ldu(u, idx + plane) : (a.zhi == ZBC_N ? pc : (a.zhi == ZBC_D ? ff_neg(pc) : zero));
-        const ff lx = ff_add(ff_sub(pe, pc), ff_sub(pw, pc));
-        const ff ly = ff_add(ff_sub(pn, pc), ff_sub(ps, pc));
-        ff t = ff_mul(cx, lx);
-        t = ff_add(t, ff_mul(cy, ly));
-        t = ff_add(t, ff_mul(zc, ff_sub(pu, pc)));
-        t = ff_add(t, ff_mul(za, ff_sub(pd, pc)));
-        if (a.c0h != 0.f) t = ff_add(t, pc);
-        t = ff_add(t, csh);
-        const ff r = ff_sub(split_double_int(a.f[idx]), t);
-        a.r[idx] = __fadd_rn(r.hi, r.lo);
-        if (a.gacc) sum = ff_add(sum, pc);
+    const bool kd = k > 0, ku = k < a.nz - 1;
+    const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
+    const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
+    const float gx = a.bcx == KIND_N ? 1.f : -1.f, gy = a.bcy == KIND_N ? 1.f : -1.f;
+    ff gsum{0.f, 0.f};                       // gauge sum of u (double-float)
+    const int rows = a.rows_per_cta;
+    const int j0 = blockIdx.x * rows, j1 = min(j0 + rows, ny);
+    for (int j = j0; j < j1; ++j) {
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const long idx = kbase + (long)j * nx + i;
+            const float2 c = u[idx];
+            float2 w, e, s, n, d, up;
+            if (i > 0) w = u[idx - 1];
+            else w = a.bcx == KIND_P ? u[idx + nx - 1] : make_float2(gx * c.x, gx * c.y);
+            if (i < nx - 1) e = u[idx + 1];
+            else e = a.bcx == KIND_P ? u[idx - (nx - 1)] : make_float2(gx * c.x, gx * c.y);
+            if (j > 0) s = u[idx - nx];
+            else s = a.bcy == KIND_P ? u[idx + (long)(ny - 1) * nx] : make_float2(gy * c.x, gy * c.y);
+            if (j < ny - 1) n = u[idx + nx];
+            else n = a.bcy == KIND_P ? u[idx - (long)(ny - 1) * nx] : make_float2(gy * c.x, gy * c.y);
+            d = kd ? u[idx - plane] : make_float2(gd * c.x, gd * c.y);
+            up = ku ? u[idx + plane] : make_float2(gu * c.x, gu * c.y);
+            // exact differences of the hi parts (TwoSum), lo parts in FP32:
+            // errors scale with the small neighbour differences of a smooth u
+            const ff de = two_sum(e.x, -c.x), dw = two_sum(w.x, -c.x);
+            const ff dn = two_sum(n.x, -c.x), ds = two_sum(s.x, -c.x);
+            const ff du = two_sum(up.x, -c.x), dd = two_sum(d.x, -c.x);
+            const ff sx = two_sum(de.hi, dw.hi), sy = two_sum(dn.hi, ds.hi);
+            const float sxl = sx.lo + de.lo + dw.lo + ((e.y - c.y) + (w.y - c.y));
+            const float syl = sy.lo + dn.lo + ds.lo + ((n.y - c.y) + (s.y - c.y));
+            const float dul = du.lo + (up.y - c.y), ddl = dd.lo + (d.y - c.y);
+            // exact products of the leading parts, first-order corrections in comp
+            const ff px = two_prod(cx.hi, sx.hi);
+            float comp = __fmaf_rn(cx.hi, sxl, __fmaf_rn(cx.lo, sx.hi, px.lo));
+            const ff py = two_prod(cy.hi, sy.hi);
+            comp += __fmaf_rn(cy.hi, syl, __fmaf_rn(cy.lo, sy.hi, py.lo));
+            const ff pz = two_prod(zc.hi, du.hi);
+            comp += __fmaf_rn(zc.hi, dul, __fmaf_rn(zc.lo, du.hi, pz.lo));
+            const ff pd = two_prod(za.hi, dd.hi);
+            comp += __fmaf_rn(za.hi, ddl, __fmaf_rn(za.lo, dd.hi, pd.lo));
+            // accumulate f - cshift - c0 u - t
+            const ff fs = split_double_int(a.f[idx]);
+            ff acc = two_sum(fs.hi, -csh.hi);
+            float err = acc.lo + fs.lo - csh.lo - comp - c0 * c.y;
+            acc = two_sum(acc.hi, -c0 * c.x); err += acc.lo;
+            acc = two_sum(acc.hi, -px.hi); err += acc.lo;
+            acc = two_sum(acc.hi, -py.hi); err += acc.lo;
+            acc = two_sum(acc.hi, -pz.hi); err += acc.lo;
+            acc = two_sum(acc.hi, -pd.hi); err += acc.lo;
+            a.r[idx] = __fadd_rn(acc.hi, err);
+            if (a.gacc) gsum = ff_add(gsum, ff{c.x, c.y});
+        }
     }
     if (a.gacc) {
-        double v = ff_to_double(sum);
+        double v = ff_to_double(gsum);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         __shared__ double red[32];
@@ -108,18 +157,21 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
         if (lane == 0) red[wid] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-            atomicAdd(a.gacc, s * a.dzf[k]);
+            double t = 0.0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[w2];
+            atomicAdd(a.gacc, t * a.dzf[k]);
         }
     }
 }
 
-cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st) {
-    const long plane = (long)a.nx * a.ny;
-    long bx = (plane + 255) / 256;
-    if (bx > 64) bx = 64;
-    dim3 grid((unsigned)bx, (unsigned)a.nz);
+cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
+    ResidFFArgs a = a0;
+    // about 4096 points per CTA, whole rows
+    int rows = (int)((4096 + a.nx - 1) / a.nx);
+    if (rows < 1) rows = 1;
+    if (rows > a.ny) rows = a.ny;
+    a.rows_per_cta = rows;
+    dim3 grid((unsigned)((a.ny + rows - 1) / rows), (unsigned)a.nz);
     k_residual_ff<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -1,21 +1,40 @@
 // Transforms of the two uniform directions (eigenfunction expansion, Sec. 2.2).
 //
-// Row kernels (x): a CTA loads `rpc` consecutive rows (contiguous in memory,
-// coalesced), packs them into complex pairs in shared memory, runs the
-// Stockham passes and post-processing, and writes the rows back.  The paper's
-// pencil transposes (Sec. 3.1) are not needed: the column kernels (y) stage a
-// tile of TX consecutive columns x all ny rows of one z-plane through shared
-// memory, so every global access is a contiguous run of TX elements while the
-// FFT runs along y inside shared memory.
+// Row kernels (x): a CTA moves `rpc` consecutive rows (contiguous in memory)
+// with one TMA bulk copy each way, packs them into complex pairs in shared
+// memory, runs the Stockham passes and the post-processing, and writes the
+// rows back.  The paper's pencil transposes (Sec. 3.1) are not needed: the
+// column kernels (y) stage a tile of TX consecutive columns x all ny rows of
+// one z-plane through shared memory with 16-byte cp.async copies, so every
+// global access is a contiguous run of TX elements while the FFT runs along y
+// inside shared memory.  Twiddles are staged in shared memory; every division
+// by a run-time size is a multiply-high by a precomputed magic.
 #include "kernels.cuh"
 
 namespace cales {
 
+__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared-memory layout of the row kernels: [mbarrier 16 B | b0 | b1 | tw | extra]
+template <typename T> struct RowLayout {
+    size_t b0, b1, tw, extra, total;
+    __host__ __device__ RowLayout(int rpc, int L, int n, size_t extra_per_elem) {
+        const size_t C = sizeof(cpx<T>);
+        b0 = 16;
+        b1 = al16(b0 + (size_t)rpc * L * C);
+        tw = al16(b1 + (size_t)rpc * L * C);
+        extra = al16(tw + (size_t)L * C);
+        total = al16(extra + (size_t)rpc * n * extra_per_elem);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t) {
+    for (int i = threadIdx.x; i < t.L; i += blockDim.x) tw_s[i] = t.tw[i];
+}
+
 // ---------------------------------------------------------------------------
-// x direction.  Shared memory: [mbarrier | b0 | b1 | staging], the staging
-// area holds FP64 input rows (forward, FP64 -> FP32 solves) or the 8-byte
-// output rows (inverse into FP64 or double-float pairs).  With `bulk` a CTA's
-// rows (contiguous in memory) move by one TMA bulk copy each way.
+// x direction
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn>
 __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
@@ -32,10 +51,12 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
+    const RowLayout<T> lay(a.rpc, L, n, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
-    cpx<T>* b1 = b0 + a.rpc * L;
-    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b1) : reinterpret_cast<TIn*>(b1 + a.rpc * L);
+    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
+    cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
+    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
+    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b1) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
     const int tot = nr * n;
     if (a.bulk) {
         if (tid == 0) {
@@ -43,6 +64,7 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
             mbar_expect_tx(bar, (uint32_t)(tot * sizeof(TIn)));
             bulk_g2s(stage, in, (uint32_t)(tot * sizeof(TIn)), bar);
         }
+        stage_twiddles(tw_s, t);
         __syncthreads();
         const bool ok = mbar_wait_bounded(bar, 0);
         if (__syncthreads_or(!ok)) {
@@ -52,22 +74,23 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         }
     } else {
         for (int e = tid; e < tot; e += blockDim.x) stage[e] = in[e];
+        stage_twiddles(tw_s, t);
         __syncthreads();
     }
     T* r0 = reinterpret_cast<T*>(b0);
     for (int e = tid; e < tot; e += blockDim.x) {
-        const int r = e / n, s = e - r * n;
+        const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
         T v;
         if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));   // FP64 input, FP32 solve
         else v = T(stage[e]);
         r0[r * n + pack_index(t.kind, n, s)] = v * sc * pack_sign<T>(t.kind, s);
     }
     __syncthreads();
-    cpx<T>* Z = fft_lines<T, false, false>(b0, b1, t, nr, L, 1);
+    cpx<T>* Z = fft_lines<T, false, 0>(b0, b1, t, nr, L, 1, tw_s);
     T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
     const int npost = nr * (L + 1);
     for (int idx = tid; idx < npost; idx += blockDim.x) {
-        const int r = idx / (L + 1), m = idx - r * (L + 1);
+        const int r = (int)fdivu((unsigned)idx, t.l1mag), m = idx - r * (L + 1);
         post_forward<T>(Z + r * L, 1, ob + r * n, 1, t, m);
     }
     if (a.bulk) {
@@ -121,10 +144,12 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         }
         return;
     }
+    const RowLayout<T> lay(a.rpc, L, n, MODE != OUT_T ? 8 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
-    cpx<T>* b1 = b0 + a.rpc * L;
-    unsigned char* o8 = reinterpret_cast<unsigned char*>(b1 + a.rpc * L);
+    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
+    cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
+    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
+    unsigned char* o8 = smem_raw + lay.extra;
     T* x0 = reinterpret_cast<T*>(b0);
     constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL;
     if (a.bulk) {
@@ -136,6 +161,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
             bulk_g2s(x0, in, b_in, bar);
             if (LOAD_OUT) bulk_g2s(o8, outp, b_out, bar);
         }
+        stage_twiddles(tw_s, t);
         __syncthreads();
         const bool ok = mbar_wait_bounded(bar, 0);
         if (__syncthreads_or(!ok)) {
@@ -148,19 +174,20 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         if (LOAD_OUT)
             for (int e = tid; e < tot; e += blockDim.x)
                 reinterpret_cast<float2*>(o8)[e] = reinterpret_cast<const float2*>(outp)[e];
+        stage_twiddles(tw_s, t);
         __syncthreads();
     }
     const int npre = nr * L;
     for (int idx = tid; idx < npre; idx += blockDim.x) {
-        const int r = idx / L, m = idx - r * L;
+        const int r = (int)fdivu((unsigned)idx, t.lmag), m = idx - r * L;
         b1[r * L + m] = pre_inverse<T>(x0 + r * n, 1, t, m);
     }
     __syncthreads();
-    cpx<T>* z = fft_lines<T, true, false>(b1, b0, t, nr, L, 1);
+    cpx<T>* z = fft_lines<T, true, 0>(b1, b0, t, nr, L, 1, tw_s);
     const T* zr = reinterpret_cast<const T*>(z);
     unsigned char* ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(z == b0 ? b1 : b0) : o8;
     for (int e = tid; e < tot; e += blockDim.x) {
-        const int r = e / n, s = e - r * n;
+        const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
         const T v = zr[r * n + pack_index(t.kind, n, s)] * pack_sign<T>(t.kind, s);
         if (MODE == OUT_T) reinterpret_cast<T*>(ob)[e] = v;
         else store8<T, MODE>(ob + (long)e * 8, v, shift);
@@ -186,9 +213,13 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
 
 // ---------------------------------------------------------------------------
 // y direction: tiles of TX columns of one z-plane, in place.  With `bulk`, the
-// ny rows of TX elements are moved by TMA bulk copies (one row each) into a
-// natural-order staging buffer; otherwise by plain coalesced loads.
+// tile moves by 16-byte cp.async copies (all in flight), else by plain loads.
+// Shared memory: [16 B | b0 | b1 | tw].
 // ---------------------------------------------------------------------------
+template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L) {
+    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)L * sizeof(cpx<T>);
+}
+
 template <typename T, int TX, bool INV>
 __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,23 +234,24 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     T* __restrict__ base = reinterpret_cast<T*>(a.data) + (long)plane * n * nx + x0;
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
     cpx<T>* b1 = b0 + TX * L;
+    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)));
     const int tot = n * TX;
-    // natural-order tile into `nat`
-    T* nat = reinterpret_cast<T*>(INV ? b0 : b1);
+    T* nat = reinterpret_cast<T*>(INV ? b0 : b1);      // natural-order tile
     constexpr int EPC = 16 / (int)sizeof(T);
     constexpr int CPR = TX / EPC > 0 ? TX / EPC : 1;
     if (a.bulk) {
-        // 16-byte cp.async chunks, all in flight; columns past the ragged edge zero-filled
         for (int e = tid; e < n * CPR; e += blockDim.x) {
             const int s = e / CPR, c0 = (e - s * CPR) * EPC;
             cp_async16(nat + s * TX + c0, base + (long)s * nx + (c0 < wx ? c0 : 0), c0 < wx);
         }
+        stage_twiddles(tw_s, t);
         cp_async_wait_all();
     } else {
         for (int e = tid; e < tot; e += blockDim.x) {
             const int s = e / TX, c = e - s * TX;
             nat[e] = (c < wx) ? base[(long)s * nx + c] : T(0);
         }
+        stage_twiddles(tw_s, t);
     }
     __syncthreads();
     T* ob;
@@ -231,7 +263,7 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             r0[((d >> 1) * TX + c) * 2 + (d & 1)] = nat[e] * pack_sign<T>(t.kind, s);
         }
         __syncthreads();
-        cpx<T>* Z = fft_lines<T, false, true>(b0, b1, t, TX, 1, TX);
+        cpx<T>* Z = fft_lines<T, false, TX>(b0, b1, t, TX, 1, TX, tw_s);
         ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
         const int npost = (L + 1) * TX;
         for (int idx = tid; idx < npost; idx += blockDim.x) {
@@ -245,7 +277,7 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             b1[m * TX + c] = pre_inverse<T>(nat + c, TX, t, m);
         }
         __syncthreads();
-        cpx<T>* z = fft_lines<T, true, true>(b1, b0, t, TX, 1, TX);
+        cpx<T>* z = fft_lines<T, true, TX>(b1, b0, t, TX, 1, TX, tw_s);
         const T* zr = reinterpret_cast<const T*>(z);
         ob = reinterpret_cast<T*>(z == b0 ? b1 : b0);
         for (int e = tid; e < tot; e += blockDim.x) {
@@ -274,30 +306,27 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn>
 cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
-    const size_t L = a.t.L > 0 ? a.t.L : 1;
-    const size_t sm = 16 + (size_t)2 * a.rpc * L * sizeof(cpx<T>) +
-                      (sizeof(TIn) != sizeof(T) ? (size_t)a.rpc * a.t.n * sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     auto kern = k_rows_forward<T, TIn>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
-    kern<<<grid, 256, sm, st>>>(a);
+    kern<<<grid, 256, lay.total, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
-    const size_t L = a.t.L > 0 ? a.t.L : 1;
-    const size_t sm = 16 + (size_t)2 * a.rpc * L * sizeof(cpx<T>) + (MODE != OUT_T ? (size_t)a.rpc * a.t.n * 8 : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, MODE != OUT_T ? 8 : 0);
     auto kern = k_rows_inverse<T, MODE>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
-    kern<<<grid, 256, sm, st>>>(a);
+    kern<<<grid, 256, lay.total, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int TX>
 static cudaError_t launch_cols_tx(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
-    const size_t sm = 16 + (size_t)2 * TX * a.t.L * sizeof(cpx<T>);
+    const size_t sm = col_smem<T>(TX, a.t.L);
     const unsigned grid = (unsigned)(a.nplanes * ((a.nx + TX - 1) / TX));
     if (inverse) {
         auto kern = k_cols<T, TX, true>;

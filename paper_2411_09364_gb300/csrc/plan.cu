@@ -126,7 +126,18 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
 template <> DirTab<double> DirHost::tab<double>() const {
     DirTab<double> t;
     t.n = n; t.kind = kind; t.L = L; t.nrad = nrad;
-    for (int i = 0; i < MAX_RADICES; ++i) t.radix[i] = i < nrad ? radix[i] : 1;
+    int ns = 1;
+    for (int i = 0; i < MAX_RADICES; ++i) {
+        t.radix[i] = i < nrad ? radix[i] : 1;
+        t.nsv[i] = ns;
+        t.tstep[i] = i < nrad ? L / (ns * radix[i]) : 1;
+        t.nbmag[i] = i < nrad ? div_magic((unsigned)(L / radix[i])) : 0u;
+        t.nsmag[i] = div_magic((unsigned)ns);
+        if (i < nrad) ns *= radix[i];
+    }
+    t.nmag = div_magic((unsigned)n);
+    t.l1mag = div_magic((unsigned)(L + 1));
+    t.lmag = div_magic((unsigned)L);
     t.tw = reinterpret_cast<const cpx<double>*>(tw_d);
     t.post = reinterpret_cast<const cpx<double>*>(post_d);
     t.mak = reinterpret_cast<const cpx<double>*>(mak_d);
@@ -136,7 +147,18 @@ template <> DirTab<double> DirHost::tab<double>() const {
 template <> DirTab<float> DirHost::tab<float>() const {
     DirTab<float> t;
     t.n = n; t.kind = kind; t.L = L; t.nrad = nrad;
-    for (int i = 0; i < MAX_RADICES; ++i) t.radix[i] = i < nrad ? radix[i] : 1;
+    int ns = 1;
+    for (int i = 0; i < MAX_RADICES; ++i) {
+        t.radix[i] = i < nrad ? radix[i] : 1;
+        t.nsv[i] = ns;
+        t.tstep[i] = i < nrad ? L / (ns * radix[i]) : 1;
+        t.nbmag[i] = i < nrad ? div_magic((unsigned)(L / radix[i])) : 0u;
+        t.nsmag[i] = div_magic((unsigned)ns);
+        if (i < nrad) ns *= radix[i];
+    }
+    t.nmag = div_magic((unsigned)n);
+    t.l1mag = div_magic((unsigned)(L + 1));
+    t.lmag = div_magic((unsigned)L);
     t.tw = reinterpret_cast<const cpx<float>*>(tw_f);
     t.post = reinterpret_cast<const cpx<float>*>(post_f);
     t.mak = reinterpret_cast<const cpx<float>*>(mak_f);

@@ -48,7 +48,7 @@ template <typename T> struct DirTab {
     int tstep[MAX_RADICES];        // twiddle index step L / (Ns R) of pass p
     unsigned nbmag[MAX_RADICES];   // fast-division magic of L / R_p
     unsigned nsmag[MAX_RADICES];   // fast-division magic of Ns_p
-    unsigned nmag, l1mag, lmag;    // magics of n, L + 1 and L
+    unsigned nmag, l1mag, lmag, hmag;   // magics of n, L + 1, L and L/2 + 1
     const cpx<T>* tw;     // W_L^t = exp(-2 pi i t / L), t in [0, L)
     const cpx<T>* post;   // W_n^m = exp(-2 pi i m / n), m in [0, L]
     const cpx<T>* mak;    // exp(-i pi m / (2n)),        m in [0, L]
@@ -131,72 +131,6 @@ template <typename T, bool INV> struct Bfly<T, 8, INV> {
     }
 };
 
-// ---------------------------------------------------------------------------
-// One Stockham autosort pass of radix R over a set of lines in shared memory
-// (Govindaraju et al., SC'08 formulation): reads element j + r*L/R, applies
-// the twiddles of sub-transform position k = j mod Ns, writes to
-// (j - k)*R + k + r*Ns.  Lines: element e of line l at l*ls + e*es.
-// TXC > 0: TXC lines (tile columns), consecutive threads -> consecutive lines;
-// TXC == 0: consecutive threads -> consecutive butterflies of one line.
-// Divisions by run-time sizes use precomputed multiply-high magics.
-// ---------------------------------------------------------------------------
-template <typename T, int R, bool INV, int TXC>
-__device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
-                                              const DirTab<T>& t, int p, int nlines, int ls, int es,
-                                              const cpx<T>* __restrict__ tw) {
-    const int L = t.L;
-    const int nb = L / R;
-    const int Ns = t.nsv[p];
-    const unsigned nsmag = t.nsmag[p];
-    const int tstep = t.tstep[p];
-    const unsigned nbmag = t.nbmag[p];
-    const int total = nb * (TXC > 0 ? TXC : nlines);
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int line, j;
-        if (TXC > 0) { j = idx / (TXC > 0 ? TXC : 1); line = idx - j * TXC; }
-        else { line = (int)fdivu((unsigned)idx, nbmag); j = idx - line * nb; }
-        const cpx<T>* s = src + line * ls;
-        cpx<T>* d = dst + line * ls;
-        const int k = j - (int)fdivu((unsigned)j, nsmag) * Ns;
-        cpx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
-        if (Ns > 1) {
-            const int ks = k * tstep;
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const cpx<T> w = tw[r * ks];
-                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
-            }
-        }
-        Bfly<T, R, INV>::run(v);
-        const int base = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) d[(base + r * Ns) * es] = v[r];
-    }
-}
-
-// All passes of a length-L FFT; returns the buffer holding the result.
-// `tw` is the twiddle table W_L^t staged in shared memory by the caller.
-template <typename T, bool INV, int TXC>
-__device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
-                             const cpx<T>* tw) {
-    cpx<T>* src = b0;
-    cpx<T>* dst = b1;
-    for (int p = 0; p < t.nrad; ++p) {
-        switch (t.radix[p]) {
-            case 8: stockham_pass<T, 8, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
-            case 4: stockham_pass<T, 4, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
-            case 2: stockham_pass<T, 2, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
-            case 3: stockham_pass<T, 3, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
-            default: stockham_pass<T, 5, INV, TXC>(src, dst, t, p, nlines, ls, es, tw); break;
-        }
-        __syncthreads();
-        cpx<T>* tmp = src; src = dst; dst = tmp;
-    }
-    return src;
-}
-
 // Position of input sample s in the packed sequence v (Makhoul reordering for
 // N and D; identity for P) and its sign (-1)^s for D.
 __device__ __forceinline__ int pack_index(int kind, int n, int s) {
@@ -208,24 +142,137 @@ template <typename T> __device__ __forceinline__ T pack_sign(int kind, int s) {
     return (kind == KIND_D && (s & 1)) ? T(-1) : T(1);
 }
 
-// Forward post-processing of mode m in [0, L] of one line: Z is the length-L
-// FFT of the packed pairs, the outputs go to the real buffer `out` (element q
-// of the line at out[q*es_r]).
+// Natural sample behind element d of the packed sequence v (inverse of
+// pack_index; n even): identity for P, Makhoul's even/odd split for N and D.
+__device__ __forceinline__ int unpack_src(int kind, int n, int d) {
+    if (kind == KIND_P) return d;
+    return d < (n >> 1) ? 2 * d : 2 * (n - 1 - d) + 1;
+}
+
+// Real natural-order lines: element s of line l at base[l * nls + s * nes].
+template <typename T> struct NatIO {
+    const T* in;
+    T* out;
+    int nls, nes;
+};
+
+// ---------------------------------------------------------------------------
+// One Stockham autosort pass of radix R over a set of lines in shared memory
+// (Govindaraju et al., SC'08 formulation): reads element j + r*L/R, applies
+// the twiddles of sub-transform position k = j mod Ns, writes to
+// (j - k)*R + k + r*Ns.  Lines: element e of line l at l*ls + e*es.
+// TXC > 0: TXC lines (tile columns), consecutive threads -> consecutive lines;
+// TXC == 0: consecutive threads -> consecutive butterflies of one line.
+// IO bit 0: the pass reads the real natural-order input directly, applying
+// the packing (real pairs, Makhoul order, DST signs) on the fly; bit 1: the
+// pass writes the real natural-order output directly (the inverse unpacking).
+// Divisions by run-time sizes use precomputed multiply-high magics.
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV, int TXC, int IO>
+__device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                              const DirTab<T>& t, int p, int nlines, int ls, int es,
+                                              const cpx<T>* __restrict__ tw, const NatIO<T>& nat) {
+    const int L = t.L, n = t.n, kind = t.kind;
+    const int nb = L / R;
+    const int Ns = t.nsv[p];
+    const unsigned nsmag = t.nsmag[p];
+    const int tstep = t.tstep[p];
+    const unsigned nbmag = t.nbmag[p];
+    const int total = nb * (TXC > 0 ? TXC : nlines);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int line, j;
+        if (TXC > 0) { j = idx / (TXC > 0 ? TXC : 1); line = idx - j * TXC; }
+        else { line = (int)fdivu((unsigned)idx, nbmag); j = idx - line * nb; }
+        const int k = j - (int)fdivu((unsigned)j, nsmag) * Ns;
+        cpx<T> v[R];
+        if (IO & 1) {
+            const T* xin = nat.in + line * nat.nls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int q = j + r * nb;
+                const int s0 = unpack_src(kind, n, 2 * q), s1 = unpack_src(kind, n, 2 * q + 1);
+                v[r] = mk(xin[s0 * nat.nes] * pack_sign<T>(kind, s0), xin[s1 * nat.nes] * pack_sign<T>(kind, s1));
+            }
+        } else {
+            const cpx<T>* sp = src + line * ls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = sp[(j + r * nb) * es];
+        }
+        if (Ns > 1) {
+            const int ks = k * tstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const cpx<T> w = tw[r * ks];
+                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            }
+        }
+        Bfly<T, R, INV>::run(v);
+        const int base = (j - k) * R + k;
+        if (IO & 2) {
+            T* xo = nat.out + line * nat.nls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int q = base + r * Ns;
+                const int s0 = unpack_src(kind, n, 2 * q), s1 = unpack_src(kind, n, 2 * q + 1);
+                xo[s0 * nat.nes] = v[r].x * pack_sign<T>(kind, s0);
+                xo[s1 * nat.nes] = v[r].y * pack_sign<T>(kind, s1);
+            }
+        } else {
+            cpx<T>* dp = dst + line * ls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dp[(base + r * Ns) * es] = v[r];
+        }
+    }
+}
+
+template <typename T, bool INV, int TXC, int IO>
+__device__ __forceinline__ void pass_dispatch(int R, const cpx<T>* src, cpx<T>* dst, const DirTab<T>& t, int p,
+                                              int nlines, int ls, int es, const cpx<T>* tw, const NatIO<T>& nat) {
+    switch (R) {
+        case 8: stockham_pass<T, 8, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
+        case 4: stockham_pass<T, 4, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
+        case 2: stockham_pass<T, 2, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
+        case 3: stockham_pass<T, 3, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
+        default: stockham_pass<T, 5, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
+    }
+}
+
+// All passes of a length-L FFT (t.nrad >= 1); returns the buffer holding the
+// result (for STORE_NAT the result is in nat.out and the return is unused).
+// LOAD_NAT: the first pass packs the real natural input itself (b0 unused as
+// input); STORE_NAT: the last pass unpacks into the real natural output.
+// `tw` is the twiddle table W_L^t staged in shared memory by the caller.
+template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT>
+__device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
+                             const cpx<T>* tw, const NatIO<T>& nat) {
+    cpx<T>* src = b0;
+    cpx<T>* dst = b1;
+    for (int p = 0; p < t.nrad; ++p) {
+        const bool first = p == 0, last = p == t.nrad - 1;
+        const int R = t.radix[p];
+        if (LOAD_NAT && first && STORE_NAT && last) pass_dispatch<T, INV, TXC, 3>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else if (LOAD_NAT && first) pass_dispatch<T, INV, TXC, 1>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else if (STORE_NAT && last) pass_dispatch<T, INV, TXC, 2>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else pass_dispatch<T, INV, TXC, 0>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        __syncthreads();
+        cpx<T>* tmp = src; src = dst; dst = tmp;
+    }
+    return src;
+}
+
+// Forward post-processing of the mode pair (m, L - m), m in [0, L/2], of one
+// line: Z is the length-L FFT of the packed pairs, the real outputs go to
+// `out` (element q of the line at out[q*oes]).  pst, mk: W_n^m and
+// exp(-i pi m / (2n)) tables (m in [0, L]).  For V_{L-m} the even and odd
+// parts are the conjugates of those of V_m.
 template <typename T>
-__device__ __forceinline__ void post_forward(const cpx<T>* Z, int zes, T* out, int oes, const DirTab<T>& t, int m) {
-    const int L = t.L, n = t.n;
-    cpx<T> zm = Z[(m == L ? 0 : m) * zes];
-    cpx<T> zc = conj_(Z[(m == 0 ? 0 : L - m) * zes]);
-    cpx<T> e = scale(zm + zc, T(0.5));
-    cpx<T> dd = zm - zc;
-    cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);            // (zm - zc) / (2i)
-    cpx<T> v = e + cmul(t.post[m], o);
-    if (t.kind == KIND_P) {
+__device__ __forceinline__ void post_store(T* out, int oes, int kind, int n, int L, int m, cpx<T> v, cpx<T> mkm) {
+    if (kind == KIND_P) {
         out[m * oes] = v.x;
         if (m > 0 && m < L) out[(n - m) * oes] = v.y;
     } else {
-        cpx<T> u = cmul(t.mak[m], v);
-        if (t.kind == KIND_N) {
+        const cpx<T> u = cmul(mkm, v);
+        if (kind == KIND_N) {
             out[m * oes] = u.x;
             if (m > 0 && m < L) out[(n - m) * oes] = -u.y;
         } else {
@@ -235,29 +282,56 @@ __device__ __forceinline__ void post_forward(const cpx<T>* Z, int zes, T* out, i
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void post_forward_pair(const cpx<T>* Z, int zes, T* out, int oes, const DirTab<T>& t,
+                                                  const cpx<T>* pst, const cpx<T>* mkt, int m) {
+    const int L = t.L, n = t.n;
+    const cpx<T> zm = Z[(m == L ? 0 : m) * zes];
+    const cpx<T> zc = conj_(Z[(m == 0 ? 0 : L - m) * zes]);
+    const cpx<T> e = scale(zm + zc, T(0.5));
+    const cpx<T> dd = zm - zc;
+    const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);            // (zm - zc) / (2i)
+    post_store<T>(out, oes, t.kind, n, L, m, e + cmul(pst[m], o), mkt[m]);
+    const int m2 = L - m;
+    if (m2 != m) post_store<T>(out, oes, t.kind, n, L, m2, conj_(e) + cmul(pst[m2], conj_(o)), mkt[m2]);
+}
+
 // V_m of the inverse (m in [0, L]) from the real coefficients X of one line.
 template <typename T>
-__device__ __forceinline__ cpx<T> inv_spectrum(const T* X, int xes, const DirTab<T>& t, int m) {
+__device__ __forceinline__ cpx<T> inv_spectrum(const T* X, int xes, const DirTab<T>& t, const cpx<T>* mkt, int m) {
     const int L = t.L, n = t.n;
     if (t.kind == KIND_P) {
-        T im = (m > 0 && m < L) ? X[(n - m) * xes] : T(0);
+        const T im = (m > 0 && m < L) ? X[(n - m) * xes] : T(0);
         return mk(X[m * xes], im);
     }
     cpx<T> u;
     if (t.kind == KIND_N) u = mk(X[m * xes], m > 0 ? -X[(n - m) * xes] : T(0));
     else                  u = mk(X[(n - 1 - m) * xes], m > 0 ? -X[(m - 1) * xes] : T(0));
-    return cmulc(u, t.mak[m]);   // exp(+i pi m / (2n)) * U_m
+    return cmulc(u, mkt[m]);   // exp(+i pi m / (2n)) * U_m
 }
 
-// Inverse pre-processing: Z_m (m in [0, L)) whose unnormalised inverse FFT
-// gives n * (x[2j] + i x[2j+1]) of the packed sequence.
+// Inverse pre-processing of the pair (m, L - m), m in [0, L/2]: Z_m (and
+// Z_{L-m} when it differs and is < L) whose unnormalised inverse FFT gives
+// n * (x[2j] + i x[2j+1]) of the packed sequence.
 template <typename T>
-__device__ __forceinline__ cpx<T> pre_inverse(const T* X, int xes, const DirTab<T>& t, int m) {
-    cpx<T> vm = inv_spectrum(X, xes, t, m);
-    cpx<T> vc = conj_(inv_spectrum(X, xes, t, t.L - m));
-    cpx<T> s = vm + vc;
-    cpx<T> d = cmulc(vm - vc, t.post[m]);        // (vm - vc) * exp(+2 pi i m / n)
-    return mk(s.x - d.y, s.y + d.x);             // s + i d
+__device__ __forceinline__ void pre_inverse_pair(const T* X, int xes, cpx<T>* Z, int zes, const DirTab<T>& t,
+                                                 const cpx<T>* pst, const cpx<T>* mkt, int m) {
+    const int L = t.L;
+    const cpx<T> vm = inv_spectrum(X, xes, t, mkt, m);
+    const cpx<T> vl = inv_spectrum(X, xes, t, mkt, L - m);
+    {
+        const cpx<T> vc = conj_(vl);
+        const cpx<T> s = vm + vc;
+        const cpx<T> d = cmulc(vm - vc, pst[m]);
+        Z[m * zes] = mk(s.x - d.y, s.y + d.x);
+    }
+    const int m2 = L - m;
+    if (m2 != m && m2 < L) {
+        const cpx<T> vc = conj_(vm);
+        const cpx<T> s = vl + vc;
+        const cpx<T> d = cmulc(vl - vc, pst[m2]);
+        Z[m2 * zes] = mk(s.x - d.y, s.y + d.x);
+    }
 }
 
 // ---------------------------------------------------------------------------

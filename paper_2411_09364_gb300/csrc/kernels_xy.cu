@@ -23,14 +23,21 @@ template <typename T> struct RowLayout {
         b0 = 16;
         b1 = al16(b0 + (size_t)rpc * L * C);
         tw = al16(b1 + (size_t)rpc * L * C);
-        extra = al16(tw + (size_t)L * C);
+        extra = al16(tw + (size_t)(3 * L + 2) * C);
         total = al16(extra + (size_t)rpc * n * extra_per_elem);
     }
 };
 
+// Twiddles W_L^t (L), then the post-processing tables W_n^m and
+// exp(-i pi m/(2n)) (L + 1 each), staged contiguously in shared memory.
 template <typename T>
 __device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t) {
-    for (int i = threadIdx.x; i < t.L; i += blockDim.x) tw_s[i] = t.tw[i];
+    const int L = t.L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw_s[i] = t.tw[i];
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) {
+        tw_s[L + i] = t.post[i];
+        tw_s[2 * L + 1 + i] = t.mak[i];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -56,7 +63,10 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
-    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b1) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
+    // natural rows land in b0 (same type) or in the extra area (FP64 input)
+    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b0) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
+    const cpx<T>* pst = tw_s + L;
+    const cpx<T>* mkt = tw_s + 2 * L + 1;
     const int tot = nr * n;
     if (a.bulk) {
         if (tid == 0) {
@@ -77,21 +87,31 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         stage_twiddles(tw_s, t);
         __syncthreads();
     }
-    T* r0 = reinterpret_cast<T*>(b0);
-    for (int e = tid; e < tot; e += blockDim.x) {
-        const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
-        T v;
-        if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));   // FP64 input, FP32 solve
-        else v = T(stage[e]);
-        r0[r * n + pack_index(t.kind, n, s)] = v * sc * pack_sign<T>(t.kind, s);
+    NatIO<T> nat{reinterpret_cast<const T*>(b0), nullptr, n, 1};
+    const bool fused = sizeof(TIn) == sizeof(T) && t.nrad > 0 && sc == T(1);
+    if (!fused) {
+        // explicit packing (FP64 input of an FP32 solve, or n == 2)
+        T* r0 = reinterpret_cast<T*>(sizeof(TIn) == sizeof(T) ? b1 : b0);
+        for (int e = tid; e < tot; e += blockDim.x) {
+            const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
+            T v;
+            if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));
+            else v = T(stage[e]);
+            r0[r * n + pack_index(t.kind, n, s)] = v * sc * pack_sign<T>(t.kind, s);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    cpx<T>* Z = fft_lines<T, false, 0>(b0, b1, t, nr, L, 1, tw_s);
+    cpx<T>* Z;
+    if (fused && t.kind == KIND_P) Z = fft_lines<T, false, 0, false, false>(b0, b1, t, nr, L, 1, tw_s, nat);
+    else if (fused) Z = fft_lines<T, false, 0, true, false>(b0, b1, t, nr, L, 1, tw_s, nat);
+    else if (sizeof(TIn) == sizeof(T)) Z = fft_lines<T, false, 0, false, false>(b1, b0, t, nr, L, 1, tw_s, nat);
+    else Z = fft_lines<T, false, 0, false, false>(b0, b1, t, nr, L, 1, tw_s, nat);
     T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
-    const int npost = nr * (L + 1);
+    const int half = L / 2 + 1;
+    const int npost = nr * half;
     for (int idx = tid; idx < npost; idx += blockDim.x) {
-        const int r = (int)fdivu((unsigned)idx, t.l1mag), m = idx - r * (L + 1);
-        post_forward<T>(Z + r * L, 1, ob + r * n, 1, t, m);
+        const int r = (int)fdivu((unsigned)idx, t.hmag), m = idx - r * half;
+        post_forward_pair<T>(Z + r * L, 1, ob + r * n, 1, t, pst, mkt, m);
     }
     if (a.bulk) {
         fence_proxy_async();
@@ -177,20 +197,39 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         stage_twiddles(tw_s, t);
         __syncthreads();
     }
-    const int npre = nr * L;
+    const cpx<T>* pst = tw_s + L;
+    const cpx<T>* mkt = tw_s + 2 * L + 1;
+    const int half = L / 2 + 1;
+    const int npre = nr * half;
     for (int idx = tid; idx < npre; idx += blockDim.x) {
-        const int r = (int)fdivu((unsigned)idx, t.lmag), m = idx - r * L;
-        b1[r * L + m] = pre_inverse<T>(x0 + r * n, 1, t, m);
+        const int r = (int)fdivu((unsigned)idx, t.hmag), m = idx - r * half;
+        pre_inverse_pair<T>(x0 + r * n, 1, b1 + r * L, 1, t, pst, mkt, m);
     }
     __syncthreads();
-    cpx<T>* z = fft_lines<T, true, 0>(b1, b0, t, nr, L, 1, tw_s);
-    const T* zr = reinterpret_cast<const T*>(z);
-    unsigned char* ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(z == b0 ? b1 : b0) : o8;
-    for (int e = tid; e < tot; e += blockDim.x) {
-        const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
-        const T v = zr[r * n + pack_index(t.kind, n, s)] * pack_sign<T>(t.kind, s);
-        if (MODE == OUT_T) reinterpret_cast<T*>(ob)[e] = v;
-        else store8<T, MODE>(ob + (long)e * 8, v, shift);
+    unsigned char* ob;
+    if (t.nrad > 0) {
+        // the last pass unpacks straight into natural order (real rows); a
+        // periodic row's packed pairs already are its natural order
+        T* natout = reinterpret_cast<T*>((t.nrad & 1) ? b0 : b1);
+        const NatIO<T> nat{nullptr, natout, n, 1};
+        if (t.kind == KIND_P) fft_lines<T, true, 0, false, false>(b1, b0, t, nr, L, 1, tw_s, nat);
+        else fft_lines<T, true, 0, false, true>(b1, b0, t, nr, L, 1, tw_s, nat);
+        if (MODE == OUT_T) {
+            ob = reinterpret_cast<unsigned char*>(natout);
+        } else {
+            ob = o8;
+            for (int e = tid; e < tot; e += blockDim.x) store8<T, MODE>(ob + (long)e * 8, natout[e], shift);
+        }
+    } else {
+        const T* zr = reinterpret_cast<const T*>(b1);
+        T* tmp = reinterpret_cast<T*>(b0);
+        ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(tmp) : o8;
+        for (int e = tid; e < tot; e += blockDim.x) {
+            const int r = (int)fdivu((unsigned)e, t.nmag), s2 = e - r * n;
+            const T v = zr[r * n + pack_index(t.kind, n, s2)] * pack_sign<T>(t.kind, s2);
+            if (MODE == OUT_T) tmp[e] = v;
+            else store8<T, MODE>(ob + (long)e * 8, v, shift);
+        }
     }
     if (a.bulk) {
         fence_proxy_async();
@@ -217,7 +256,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
 // Shared memory: [16 B | b0 | b1 | tw].
 // ---------------------------------------------------------------------------
 template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L) {
-    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)L * sizeof(cpx<T>);
+    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)(3 * L + 2) * sizeof(cpx<T>);
 }
 
 template <typename T, int TX, bool INV>
@@ -236,7 +275,9 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     cpx<T>* b1 = b0 + TX * L;
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)));
     const int tot = n * TX;
-    T* nat = reinterpret_cast<T*>(INV ? b0 : b1);      // natural-order tile
+    T* nat = reinterpret_cast<T*>(b0);                 // natural-order tile [ny][TX]
+    const cpx<T>* pst = tw_s + L;
+    const cpx<T>* mkt = tw_s + 2 * L + 1;
     constexpr int EPC = 16 / (int)sizeof(T);
     constexpr int CPR = TX / EPC > 0 ? TX / EPC : 1;
     if (a.bulk) {
@@ -255,35 +296,48 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     }
     __syncthreads();
     T* ob;
+    const int half = L / 2 + 1;
     if (!INV) {
-        T* r0 = reinterpret_cast<T*>(b0);
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            const int d = pack_index(t.kind, n, s);
-            r0[((d >> 1) * TX + c) * 2 + (d & 1)] = nat[e] * pack_sign<T>(t.kind, s);
+        cpx<T>* Z;
+        if (t.nrad > 0) {
+            const NatIO<T> natio{nat, nullptr, 1, TX};
+            Z = fft_lines<T, false, TX, true, false>(b0, b1, t, TX, 1, TX, tw_s, natio);
+        } else {
+            T* r1 = reinterpret_cast<T*>(b1);
+            for (int e = tid; e < tot; e += blockDim.x) {
+                const int s = e / TX, c = e - s * TX;
+                const int d = pack_index(t.kind, n, s);
+                r1[((d >> 1) * TX + c) * 2 + (d & 1)] = nat[e] * pack_sign<T>(t.kind, s);
+            }
+            __syncthreads();
+            Z = b1;
         }
-        __syncthreads();
-        cpx<T>* Z = fft_lines<T, false, TX>(b0, b1, t, TX, 1, TX, tw_s);
         ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
-        const int npost = (L + 1) * TX;
+        const int npost = half * TX;
         for (int idx = tid; idx < npost; idx += blockDim.x) {
             const int m = idx / TX, c = idx - m * TX;
-            post_forward<T>(Z + c, TX, ob + c, TX, t, m);
+            post_forward_pair<T>(Z + c, TX, ob + c, TX, t, pst, mkt, m);
         }
     } else {
-        const int npre = L * TX;
+        const int npre = half * TX;
         for (int idx = tid; idx < npre; idx += blockDim.x) {
             const int m = idx / TX, c = idx - m * TX;
-            b1[m * TX + c] = pre_inverse<T>(nat + c, TX, t, m);
+            pre_inverse_pair<T>(nat + c, TX, b1 + c, TX, t, pst, mkt, m);
         }
         __syncthreads();
-        cpx<T>* z = fft_lines<T, true, TX>(b1, b0, t, TX, 1, TX, tw_s);
-        const T* zr = reinterpret_cast<const T*>(z);
-        ob = reinterpret_cast<T*>(z == b0 ? b1 : b0);
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            const int d = pack_index(t.kind, n, s);
-            ob[e] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
+        if (t.nrad > 0) {
+            T* natout = reinterpret_cast<T*>((t.nrad & 1) ? b0 : b1);
+            const NatIO<T> natio{nullptr, natout, 1, TX};
+            fft_lines<T, true, TX, false, true>(b1, b0, t, TX, 1, TX, tw_s, natio);
+            ob = natout;
+        } else {
+            const T* zr = reinterpret_cast<const T*>(b1);
+            ob = reinterpret_cast<T*>(b0);
+            for (int e = tid; e < tot; e += blockDim.x) {
+                const int s = e / TX, c = e - s * TX;
+                const int d = pack_index(t.kind, n, s);
+                ob[e] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
+            }
         }
     }
     __syncthreads();

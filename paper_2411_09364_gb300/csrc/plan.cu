@@ -138,6 +138,7 @@ template <> DirTab<double> DirHost::tab<double>() const {
     t.nmag = div_magic((unsigned)n);
     t.l1mag = div_magic((unsigned)(L + 1));
     t.lmag = div_magic((unsigned)L);
+    t.hmag = div_magic((unsigned)(L / 2 + 1));
     t.tw = reinterpret_cast<const cpx<double>*>(tw_d);
     t.post = reinterpret_cast<const cpx<double>*>(post_d);
     t.mak = reinterpret_cast<const cpx<double>*>(mak_d);
@@ -159,6 +160,7 @@ template <> DirTab<float> DirHost::tab<float>() const {
     t.nmag = div_magic((unsigned)n);
     t.l1mag = div_magic((unsigned)(L + 1));
     t.lmag = div_magic((unsigned)L);
+    t.hmag = div_magic((unsigned)(L / 2 + 1));
     t.tw = reinterpret_cast<const cpx<float>*>(tw_f);
     t.post = reinterpret_cast<const cpx<float>*>(post_f);
     t.mak = reinterpret_cast<const cpx<float>*>(mak_f);

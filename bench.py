@@ -178,6 +178,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="512x256x192 channel variant (profiling)")
+    ap.add_argument("--shape", default=None, help="NX,NY,NZ: the duct at another size (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -198,6 +199,10 @@ def main():
     if args.small:
         w.update(name="channel_poisson_512x256x192", nx=512, ny=256, nz=192, bc=(0, 0, 0, 0, 1, 1),
                  lx=2 * math.pi, ly=math.pi, beta=1.8)
+    if args.shape:
+        sx, sy, sz = (int(v) for v in args.shape.split(","))
+        w.update(name=f"duct_poisson_{sx}x{sy}x{sz}", nx=sx, ny=sy, nz=sz,
+                 lx=w["lx"] * sx / w["nx"], ly=w["ly"] * sy / w["ny"])
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     npts = nx * ny * nz
     zf = S.tanh_faces(nz, w["beta"], w["lz"])

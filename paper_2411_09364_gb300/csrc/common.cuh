@@ -112,6 +112,46 @@ template <typename T, bool INV> struct Bfly<T, 5, INV> {
     }
 };
 
+// multiply by W16^e = exp(-2 pi i e / 16) (forward) or its conjugate (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> w16(cpx<T> a, T wr, T wi) {
+    const T w2 = INV ? -wi : wi;
+    return mk(a.x * wr - a.y * w2, a.x * w2 + a.y * wr);
+}
+
+template <typename T, bool INV> struct Bfly<T, 16, INV> {
+    // 16 = 4 x 4: radix-4 DFTs over n1 (input 4 n1 + n2), twiddles W16^(n2 k1),
+    // radix-4 DFTs over n2 (output k1 + 4 k2)
+    static __device__ __forceinline__ void run(cpx<T>* v) {
+        const T c = T(0.92387953251128675612818318939679);    // cos(pi / 8)
+        const T s = T(0.38268343236508977172845998403040);    // sin(pi / 8)
+        const T r2 = T(0.70710678118654752440084436210485);
+        cpx<T> a[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            cpx<T> t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+            Bfly<T, 4, INV>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+        }
+        a[1][1] = w16<T, INV>(a[1][1], c, -s);
+        a[1][2] = w16<T, INV>(a[1][2], r2, -r2);
+        a[1][3] = w16<T, INV>(a[1][3], s, -c);
+        a[2][1] = w16<T, INV>(a[2][1], r2, -r2);
+        a[2][2] = rot90<T, INV>(a[2][2]);
+        a[2][3] = w16<T, INV>(a[2][3], -r2, -r2);
+        a[3][1] = w16<T, INV>(a[3][1], s, -c);
+        a[3][2] = w16<T, INV>(a[3][2], -r2, -r2);
+        a[3][3] = w16<T, INV>(a[3][3], -c, s);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cpx<T> t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            Bfly<T, 4, INV>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+        }
+    }
+};
+
 template <typename T, bool INV> struct Bfly<T, 8, INV> {
     static __device__ __forceinline__ void run(cpx<T>* v) {
         const T r2 = T(0.70710678118654752440084436210485);
@@ -168,6 +208,23 @@ template <typename T> struct NatIO {
 // pass writes the real natural-order output directly (the inverse unpacking).
 // Divisions by run-time sizes use precomputed multiply-high magics.
 // ---------------------------------------------------------------------------
+// Row work buffers (FP32 complex, lines contiguous) are XOR-swizzled within
+// blocks of 16 elements: element i lives at i ^ sw(i >> 4) with
+// sw(b) = (b & 7) | ((parity(b & 7) ^ bit 3 of b) << 3), a bijection of the
+// low four bits of b.  Aligned runs of 16 stay one conflict-free wavefront,
+// and the strided writes of the early Stockham passes (R = 16 with Ns = 1,
+// R = 8 with Ns = 1, 2, 4, 8, R = 4 with Ns = 1) land in 16 distinct 8-byte
+// bank pairs per half-warp instead of piling into R-way conflicts.  Buffers
+// hold a multiple of 16 elements so the map stays inside them.
+template <bool ON> __device__ __forceinline__ int swz(int i) {
+    if (!ON) return i;
+    const int b = i >> 4;
+    const int lo = b & 7;
+    return i ^ (lo | (((__popc(lo) ^ (b >> 3)) & 1) << 3));
+}
+
+// IO bits: 1 = first pass packs the real natural input, 2 = last pass unpacks
+// into the real natural output, 4 = source swizzled, 8 = destination swizzled.
 template <typename T, int R, bool INV, int TXC, int IO>
 __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
                                               const DirTab<T>& t, int p, int nlines, int ls, int es,
@@ -194,9 +251,9 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
                 v[r] = mk(xin[s0 * nat.nes] * pack_sign<T>(kind, s0), xin[s1 * nat.nes] * pack_sign<T>(kind, s1));
             }
         } else {
-            const cpx<T>* sp = src + line * ls;
+            const int s0 = line * ls + j * es, sst = nb * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = sp[(j + r * nb) * es];
+            for (int r = 0; r < R; ++r) v[r] = src[swz<(IO & 4) != 0>(s0 + r * sst)];
         }
         if (Ns > 1) {
             const int ks = k * tstep;
@@ -218,9 +275,9 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
                 xo[s1 * nat.nes] = v[r].y * pack_sign<T>(kind, s1);
             }
         } else {
-            cpx<T>* dp = dst + line * ls;
+            const int d0 = line * ls + base * es, dstp = Ns * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dp[(base + r * Ns) * es] = v[r];
+            for (int r = 0; r < R; ++r) dst[swz<(IO & 8) != 0>(d0 + r * dstp)] = v[r];
         }
     }
 }
@@ -229,6 +286,7 @@ template <typename T, bool INV, int TXC, int IO>
 __device__ __forceinline__ void pass_dispatch(int R, const cpx<T>* src, cpx<T>* dst, const DirTab<T>& t, int p,
                                               int nlines, int ls, int es, const cpx<T>* tw, const NatIO<T>& nat) {
     switch (R) {
+        case 16: stockham_pass<T, 16, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
         case 8: stockham_pass<T, 8, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
         case 4: stockham_pass<T, 4, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
         case 2: stockham_pass<T, 2, INV, TXC, IO>(src, dst, t, p, nlines, ls, es, tw, nat); break;
@@ -245,15 +303,19 @@ __device__ __forceinline__ void pass_dispatch(int R, const cpx<T>* src, cpx<T>* 
 template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT>
 __device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
                              const cpx<T>* tw, const NatIO<T>& nat) {
+    // row buffers between passes are swizzled (FP32 only: 8-byte elements);
+    // the input of the first and the output of the last pass are not
+    constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
+    constexpr int LN = LOAD_NAT ? 1 : 0, SN = STORE_NAT ? 2 : 0;
     cpx<T>* src = b0;
     cpx<T>* dst = b1;
     for (int p = 0; p < t.nrad; ++p) {
         const bool first = p == 0, last = p == t.nrad - 1;
         const int R = t.radix[p];
-        if (LOAD_NAT && first && STORE_NAT && last) pass_dispatch<T, INV, TXC, 3>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else if (LOAD_NAT && first) pass_dispatch<T, INV, TXC, 1>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else if (STORE_NAT && last) pass_dispatch<T, INV, TXC, 2>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else pass_dispatch<T, INV, TXC, 0>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        if (first && last) pass_dispatch<T, INV, TXC, LN | SN>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else if (first) pass_dispatch<T, INV, TXC, LN | 8 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else if (last) pass_dispatch<T, INV, TXC, SN | 4 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+        else pass_dispatch<T, INV, TXC, 12 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
         __syncthreads();
         cpx<T>* tmp = src; src = dst; dst = tmp;
     }

@@ -164,6 +164,116 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
     }
 }
 
+// One point of the double-float residual (the arithmetic of k_residual_ff):
+// c the point, w e s n d up its neighbours (x-, x+, y-, y+, z-, z+), fv = f.
+// SING: singular Poisson (consistency shift subtracted, gauge sum of u kept
+// as an unnormalised (hi, lo) pair); HELM: the c0 u term of Eq. 18.
+template <bool SING, bool HELM>
+__device__ __forceinline__ float resid_point(float2 c, float2 w, float2 e, float2 s, float2 n, float2 d, float2 up,
+                                             double fv, ff cx, ff cy, ff zc, ff za, ff csh, float& ghi, float& glo) {
+    const ff de = two_sum(e.x, -c.x), dw = two_sum(w.x, -c.x);
+    const ff dn = two_sum(n.x, -c.x), ds = two_sum(s.x, -c.x);
+    const ff du = two_sum(up.x, -c.x), dd = two_sum(d.x, -c.x);
+    const ff sx = two_sum(de.hi, dw.hi), sy = two_sum(dn.hi, ds.hi);
+    const float sxl = sx.lo + de.lo + dw.lo + ((e.y - c.y) + (w.y - c.y));
+    const float syl = sy.lo + dn.lo + ds.lo + ((n.y - c.y) + (s.y - c.y));
+    const float dul = du.lo + (up.y - c.y), ddl = dd.lo + (d.y - c.y);
+    const ff px = two_prod(cx.hi, sx.hi);
+    float comp = __fmaf_rn(cx.hi, sxl, __fmaf_rn(cx.lo, sx.hi, px.lo));
+    const ff py = two_prod(cy.hi, sy.hi);
+    comp += __fmaf_rn(cy.hi, syl, __fmaf_rn(cy.lo, sy.hi, py.lo));
+    const ff pz = two_prod(zc.hi, du.hi);
+    comp += __fmaf_rn(zc.hi, dul, __fmaf_rn(zc.lo, du.hi, pz.lo));
+    const ff pd = two_prod(za.hi, dd.hi);
+    comp += __fmaf_rn(za.hi, ddl, __fmaf_rn(za.lo, dd.hi, pd.lo));
+    const ff fs = split_double_int(fv);
+    ff acc;
+    float err;
+    if (SING) {
+        acc = two_sum(fs.hi, -csh.hi);
+        err = acc.lo + fs.lo - csh.lo - comp;
+    } else {
+        acc = ff{fs.hi, 0.f};
+        err = fs.lo - comp;
+    }
+    if (HELM) {
+        acc = two_sum(acc.hi, -c.x);
+        err += acc.lo - c.y;
+    }
+    acc = two_sum(acc.hi, -px.hi); err += acc.lo;
+    acc = two_sum(acc.hi, -py.hi); err += acc.lo;
+    acc = two_sum(acc.hi, -pz.hi); err += acc.lo;
+    acc = two_sum(acc.hi, -pd.hi); err += acc.lo;
+    if (SING) {
+        const ff g = two_sum(ghi, c.x);
+        ghi = g.hi;
+        glo += g.lo + c.y;
+    }
+    return __fadd_rn(acc.hi, err);
+}
+
+__device__ __forceinline__ float4 ld4(const float2* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 sc4(float g, float4 v) { return make_float4(g * v.x, g * v.y, g * v.z, g * v.w); }
+
+// Two x-adjacent points per thread with 16-byte loads (nx even, 16-byte
+// aligned u and f): the centre pair, both y and both z neighbour pairs and
+// f come in one vector load each, the x neighbours of the pair in two 8-byte
+// loads.  A CTA covers whole rows of one z-plane.
+template <bool SING, bool HELM>
+__global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
+    const int nx = a.nx, ny = a.ny;
+    const long plane = (long)nx * ny;
+    const int k = blockIdx.y;
+    const long kbase = (long)k * plane;
+    const float2* __restrict__ u = a.u;
+    const ff za = ff_from_double(a.c1 * a.za[k]), zc = ff_from_double(a.c1 * a.zc[k]);
+    const ff cx{a.cxh, a.cxl}, cy{a.cyh, a.cyl};
+    const ff csh = (SING && a.cshift) ? ff_from_double(a.cshift[0]) : ff{0.f, 0.f};
+    const bool kd = k > 0, ku = k < a.nz - 1;
+    const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
+    const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
+    const float gx = a.bcx == KIND_N ? 1.f : -1.f, gy = a.bcy == KIND_N ? 1.f : -1.f;
+    const bool px_ = a.bcx == KIND_P, py_ = a.bcy == KIND_P;
+    float ghi = 0.f, glo = 0.f;
+    const int npair = nx >> 1;
+    const int j0 = blockIdx.x * a.rows_per_cta, j1 = min(j0 + a.rows_per_cta, ny);
+    const int items = (j1 - j0) * npair;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int jr = it / npair, pi = it - jr * npair;
+        const int j = j0 + jr, i = 2 * pi;
+        const long idx = kbase + (long)j * nx + i;
+        const float4 c = ld4(u + idx);
+        const float4 s = j > 0 ? ld4(u + idx - nx) : (py_ ? ld4(u + idx + (long)(ny - 1) * nx) : sc4(gy, c));
+        const float4 n = j < ny - 1 ? ld4(u + idx + nx) : (py_ ? ld4(u + idx - (long)(ny - 1) * nx) : sc4(gy, c));
+        const float4 d = kd ? ld4(u + idx - plane) : sc4(gd, c);
+        const float4 up = ku ? ld4(u + idx + plane) : sc4(gu, c);
+        const float2 w = i > 0 ? u[idx - 1] : (px_ ? u[idx + nx - 1] : make_float2(gx * c.x, gx * c.y));
+        const float2 e = i + 2 < nx ? u[idx + 2] : (px_ ? u[idx - i] : make_float2(gx * c.z, gx * c.w));
+        const double2 fv = *reinterpret_cast<const double2*>(a.f + idx);
+        const float r0 = resid_point<SING, HELM>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up), fv.x,
+                                                 cx, cy, zc, za, csh, ghi, glo);
+        const float r1 = resid_point<SING, HELM>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up), fv.y,
+                                                 cx, cy, zc, za, csh, ghi, glo);
+        *reinterpret_cast<float2*>(a.r + idx) = make_float2(r0, r1);
+    }
+    if (SING && a.gacc) {
+        double v = (double)ghi + (double)glo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __shared__ double red[32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[w2];
+            atomicAdd(a.gacc, t * a.dzf[k]);
+        }
+    }
+}
+
 cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     ResidFFArgs a = a0;
     // about 4096 points per CTA, whole rows
@@ -172,7 +282,15 @@ cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     if (rows > a.ny) rows = a.ny;
     a.rows_per_cta = rows;
     dim3 grid((unsigned)((a.ny + rows - 1) / rows), (unsigned)a.nz);
-    k_residual_ff<<<grid, 256, 0, st>>>(a);
+    const bool vec = (a.nx % 2 == 0) && ((uintptr_t)a.u % 16 == 0) && ((uintptr_t)a.f % 16 == 0) &&
+                     ((uintptr_t)a.r % 8 == 0);
+    const bool sing = a.gacc != nullptr || a.cshift != nullptr;
+    const bool helm = a.c0h != 0.f;
+    if (!vec) k_residual_ff<<<grid, 256, 0, st>>>(a);
+    else if (sing && !helm) k_residual_ff2<true, false><<<grid, 256, 0, st>>>(a);
+    else if (sing) k_residual_ff2<true, true><<<grid, 256, 0, st>>>(a);
+    else if (helm) k_residual_ff2<false, true><<<grid, 256, 0, st>>>(a);
+    else k_residual_ff2<false, false><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

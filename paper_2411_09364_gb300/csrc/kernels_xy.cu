@@ -15,28 +15,41 @@ namespace cales {
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Shared-memory layout of the row kernels: [mbarrier 16 B | b0 | b1 | tw | extra]
+// Number of table entries staged in shared memory: twiddles W_L^t (L), the
+// post-processing factors W_n^m (L + 1) and, for the cosine and sine kinds,
+// exp(-i pi m/(2n)) (L + 1).
+__host__ __device__ __forceinline__ int table_len(int L, int kind) {
+    return 2 * L + 1 + (kind != KIND_P ? L + 1 : 0);
+}
+
+// Shared-memory layout of the row kernels: [mbarrier 16 B | b0 | b1 | tw | extra];
+// b0 and b1 hold a multiple of 16 complex elements (swizzle blocks).
 template <typename T> struct RowLayout {
     size_t b0, b1, tw, extra, total;
-    __host__ __device__ RowLayout(int rpc, int L, int n, size_t extra_per_elem) {
+    __host__ __device__ RowLayout(int rpc, int L, int n, int kind, size_t extra_per_elem) {
         const size_t C = sizeof(cpx<T>);
+        const size_t nel = ((size_t)rpc * L + 15) & ~size_t(15);
         b0 = 16;
-        b1 = al16(b0 + (size_t)rpc * L * C);
-        tw = al16(b1 + (size_t)rpc * L * C);
-        extra = al16(tw + (size_t)(3 * L + 2) * C);
+        b1 = al16(b0 + nel * C);
+        tw = al16(b1 + nel * C);
+        extra = al16(tw + (size_t)table_len(L, kind) * C);
         total = al16(extra + (size_t)rpc * n * extra_per_elem);
     }
 };
 
-// Twiddles W_L^t (L), then the post-processing tables W_n^m and
-// exp(-i pi m/(2n)) (L + 1 each), staged contiguously in shared memory.
+// Twiddles W_L^t (L), then the post-processing tables W_n^m and (cosine and
+// sine kinds) exp(-i pi m/(2n)) (L + 1 each), staged contiguously in shared memory.
 template <typename T>
 __device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t) {
     const int L = t.L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) tw_s[i] = t.tw[i];
-    for (int i = threadIdx.x; i <= L; i += blockDim.x) {
-        tw_s[L + i] = t.post[i];
-        tw_s[2 * L + 1 + i] = t.mak[i];
+    if (t.kind != KIND_P) {
+        for (int i = threadIdx.x; i <= L; i += blockDim.x) {
+            tw_s[L + i] = t.post[i];
+            tw_s[2 * L + 1 + i] = t.mak[i];
+        }
+    } else {
+        for (int i = threadIdx.x; i <= L; i += blockDim.x) tw_s[L + i] = t.post[i];
     }
 }
 
@@ -58,7 +71,7 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, L, n, t.kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         }
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, MODE != OUT_T ? 8 : 0);
+    const RowLayout<T> lay(a.rpc, L, n, t.kind, MODE != OUT_T ? 8 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
@@ -255,8 +268,8 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
 // tile moves by 16-byte cp.async copies (all in flight), else by plain loads.
 // Shared memory: [16 B | b0 | b1 | tw].
 // ---------------------------------------------------------------------------
-template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L) {
-    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)(3 * L + 2) * sizeof(cpx<T>);
+template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L, int kind) {
+    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)table_len(L, kind) * sizeof(cpx<T>);
 }
 
 template <typename T, int TX, bool INV>
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn>
 cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     auto kern = k_rows_forward<T, TIn>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -370,7 +383,7 @@ cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int MODE>
 cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, MODE != OUT_T ? 8 : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, MODE != OUT_T ? 8 : 0);
     auto kern = k_rows_inverse<T, MODE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -380,7 +393,7 @@ cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int TX>
 static cudaError_t launch_cols_tx(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
-    const size_t sm = col_smem<T>(TX, a.t.L);
+    const size_t sm = col_smem<T>(TX, a.t.L, a.t.kind);
     const unsigned grid = (unsigned)(a.nplanes * ((a.nx + TX - 1) / TX));
     if (inverse) {
         auto kern = k_cols<T, TX, true>;

@@ -601,7 +601,11 @@ static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
 // once) and vector stores.  Segment states are chained by warp 0 through
 // shared memory.  Pivot reciprocals of a segment stay in registers.
 // ---------------------------------------------------------------------------
-template <typename T, int MAXM>
+// FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
+// predicates and the first/last-row conditions reduce to compile-time tests
+// on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
+// transposed) instead of the uniform forward scale.
+template <typename T, int MAXM, bool FULL, bool ADJ>
 __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TM = 32;
@@ -662,6 +666,9 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     const T* Cc = sC + k0;
     const T* G = sG + k0;
     const T* O = sO + k0;
+    const T gsc = T(a.scale);
+    const bool lastseg = s == P - 1, firstseg = s == 0;
+    (void)lastseg; (void)firstseg;
     T* col = tile + k0 * TM + c;
     const T cprev = s > 0 ? sC[k0 - 1] : T(0);
     T* c11 = ch;
@@ -670,8 +677,11 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     T* c22 = ch + 3 * P * TM;
     T* cin = ch + 4 * P * TM;
     const int me = s * TM + c;
-#define CT(j) ((k0 + (j) < nz - 1) ? Cc[j] : T(0))
-#define XT(j) ((k0 + (j) == nz - 1) ? etop : T(0))
+#define CT(j) (FULL ? (((j) < MAXM - 1 || !lastseg) ? Cc[j] : T(0)) : ((k0 + (j) < nz - 1) ? Cc[j] : T(0)))
+#define XT(j) (FULL ? (((j) == MAXM - 1 && lastseg) ? etop : T(0)) : ((k0 + (j) == nz - 1) ? etop : T(0)))
+#define AK(j) (FULL ? (((j) > 0 || !firstseg) ? A[j] : T(0)) : ((k0 + (j) > 0) ? A[j] : T(0)))
+#define GW(j) (ADJ ? G[j] : gsc)
+#define INSEG(j) (FULL || (j) < mseg)
     bool bad = false;
 
     // A: composite pivot map of the segment
@@ -681,12 +691,12 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
             T e = base + ebot + (nz == 1 ? etop : T(0));
 #pragma unroll
             for (int j = 1; j < MAXM; ++j)
-                if (j < mseg) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
+                if (INSEG(j)) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
             g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
         } else {
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
-                if (j < mseg) {
+                if (INSEG(j)) {
                     const T x = XT(j);
                     const T cm = j > 0 ? Cc[j - 1] : cprev;
                     const T am = base + A[j] + x, bm = (base + x) * cm;
@@ -722,12 +732,12 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
         else e = base + A[0] * e_in * frcp<T>(cprev + e_in) + XT(0);
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
-            if (j < mseg) {
+            if (INSEG(j)) {
                 if (j > 0) e = base + A[j] * e * inv[j - 1] + XT(j);
                 inv[j] = frcp<T>(CT(j) + e);
-                const T ak = (k0 + j > 0) ? A[j] : T(0);
+                const T ak = AK(j);
                 al = ak * inv[j] * al;
-                be = (col[j * TM] * G[j] + ak * be) * inv[j];
+                be = (col[j * TM] * GW(j) + ak * be) * inv[j];
                 bad |= !(inv[j] > T(0));
             }
         }
@@ -749,9 +759,9 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
         T y = cin[me], Q = T(0), R = T(1);
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
-            if (j < mseg) {
-                const T ak = (k0 + j > 0) ? A[j] : T(0);
-                y = (col[j * TM] * G[j] + ak * y) * inv[j];
+            if (INSEG(j)) {
+                const T ak = AK(j);
+                y = (col[j * TM] * GW(j) + ak * y) * inv[j];
                 col[j * TM] = y;
                 Q += R * y;
                 R *= CT(j) * inv[j];
@@ -775,15 +785,18 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
         T x = cin[me];
 #pragma unroll
         for (int j = MAXM - 1; j >= 0; --j) {
-            if (j < mseg) {
+            if (INSEG(j)) {
                 x = col[j * TM] + CT(j) * inv[j] * x;
-                col[j * TM] = x * O[j];
+                col[j * TM] = ADJ ? x * O[j] : x;
                 bad |= !isfinite(x);
             }
         }
     }
 #undef CT
 #undef XT
+#undef AK
+#undef GW
+#undef INSEG
     if ((sing_tile && c == 0) || c >= w) bad = false;
     if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
     __syncthreads();
@@ -821,7 +834,9 @@ size_t zsolve_w_smem(int nz, int P) {
 template <typename T, int MAXM>
 static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
     const size_t sm = zsolve_w_smem<T>(a.nz, a.P);
-    auto kern = k_zsolve_w<T, MAXM>;
+    const bool full = a.nz == a.P * MAXM;
+    auto kern = full ? (a.adjoint ? k_zsolve_w<T, MAXM, true, true> : k_zsolve_w<T, MAXM, true, false>)
+                     : (a.adjoint ? k_zsolve_w<T, MAXM, false, true> : k_zsolve_w<T, MAXM, false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const long nmodes = (long)a.nx * a.ny;
     const unsigned grid = (unsigned)((nmodes + 31) / 32);

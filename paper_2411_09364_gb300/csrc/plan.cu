@@ -50,6 +50,13 @@ bool factorize(int L, int* radix, int& nrad) {
     int m = L;
     int twos = 0;
     while (m % 2 == 0) { m /= 2; ++twos; }
+    // radix 16 first (fewer shared-memory passes), CALES_MAXRADIX=8 keeps the
+    // radix-8 factorisation
+    static const int maxr = [] {
+        const char* e = getenv("CALES_MAXRADIX");
+        return (e && atoi(e) == 8) ? 8 : 16;
+    }();
+    while (maxr == 16 && twos >= 4) { radix[nrad++] = 16; twos -= 4; }
     while (twos >= 3) { radix[nrad++] = 8; twos -= 3; }
     if (twos == 2) radix[nrad++] = 4;
     if (twos == 1) radix[nrad++] = 2;

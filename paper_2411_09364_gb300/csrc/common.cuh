@@ -225,22 +225,34 @@ template <bool ON> __device__ __forceinline__ int swz(int i) {
 
 // IO bits: 1 = first pass packs the real natural input, 2 = last pass unpacks
 // into the real natural output, 4 = source swizzled, 8 = destination swizzled.
-template <typename T, int R, bool INV, int TXC, int IO>
+// LS > 0: the line length L = LS is a compile-time constant (n = 2 LS), and
+// so are the pass sizes (NSS = Ns of this pass); KS >= 0: compile-time kind.
+// Then every index division folds to constants and shifts.
+template <typename T, int R, bool INV, int TXC, int IO, int LS = 0, int NSS = 0, int KS = -1>
 __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
                                               const DirTab<T>& t, int p, int nlines, int ls, int es,
                                               const cpx<T>* __restrict__ tw, const NatIO<T>& nat) {
-    const int L = t.L, n = t.n, kind = t.kind;
-    const int nb = L / R;
-    const int Ns = t.nsv[p];
-    const unsigned nsmag = t.nsmag[p];
-    const int tstep = t.tstep[p];
-    const unsigned nbmag = t.nbmag[p];
+    const int n = LS ? 2 * LS : t.n;
+    const int kind = KS >= 0 ? KS : t.kind;
+    constexpr int nbS = LS ? LS / R : 1;
+    const int nb = LS ? nbS : t.L / R;
+    const int Ns = LS ? NSS : t.nsv[p];
+    const int tstep = LS ? LS / (NSS * R) : t.tstep[p];
     const int total = nb * (TXC > 0 ? TXC : nlines);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int line, j;
-        if (TXC > 0) { j = idx / (TXC > 0 ? TXC : 1); line = idx - j * TXC; }
-        else { line = (int)fdivu((unsigned)idx, nbmag); j = idx - line * nb; }
-        const int k = j - (int)fdivu((unsigned)j, nsmag) * Ns;
+        int line, j, k;
+        if (TXC > 0) {
+            j = (int)((unsigned)idx / (unsigned)(TXC > 0 ? TXC : 1));
+            line = idx - j * TXC;
+        } else if (LS) {
+            line = (int)((unsigned)idx / (unsigned)nbS);
+            j = idx - line * nbS;
+        } else {
+            line = (int)fdivu((unsigned)idx, t.nbmag[p]);
+            j = idx - line * nb;
+        }
+        if (LS) k = (int)((unsigned)j % (unsigned)(NSS > 0 ? NSS : 1));
+        else k = j - (int)fdivu((unsigned)j, t.nsmag[p]) * Ns;
         cpx<T> v[R];
         if (IO & 1) {
             const T* xin = nat.in + line * nat.nls;
@@ -255,7 +267,7 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = src[swz<(IO & 4) != 0>(s0 + r * sst)];
         }
-        if (Ns > 1) {
+        if (LS ? (NSS > 1) : (Ns > 1)) {
             const int ks = k * tstep;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -295,31 +307,75 @@ __device__ __forceinline__ void pass_dispatch(int R, const cpx<T>* src, cpx<T>* 
     }
 }
 
-// All passes of a length-L FFT (t.nrad >= 1); returns the buffer holding the
-// result (for STORE_NAT the result is in nat.out and the return is unused).
-// LOAD_NAT: the first pass packs the real natural input itself (b0 unused as
-// input); STORE_NAT: the last pass unpacks into the real natural output.
-// `tw` is the twiddle table W_L^t staged in shared memory by the caller.
-template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT>
+// Compile-time factorisation of a line length (the plan's order: radix 16
+// first, then one 8, 4 or 2, then 5s, then 3s); 0 past the last pass.
+constexpr int sf_radix(int L, int p) {
+    int m = L, twos = 0, fives = 0, threes = 0;
+    while (m > 1 && m % 2 == 0) { m /= 2; ++twos; }
+    while (m > 1 && m % 5 == 0) { m /= 5; ++fives; }
+    while (m > 1 && m % 3 == 0) { m /= 3; ++threes; }
+    int i = 0;
+    for (int c = 0; c < twos / 4; ++c, ++i) if (i == p) return 16;
+    if (twos % 4 == 3) { if (i == p) return 8; ++i; }
+    if (twos % 4 == 2) { if (i == p) return 4; ++i; }
+    if (twos % 4 == 1) { if (i == p) return 2; ++i; }
+    for (int c = 0; c < fives; ++c, ++i) if (i == p) return 5;
+    for (int c = 0; c < threes; ++c, ++i) if (i == p) return 3;
+    return 0;
+}
+constexpr int sf_nrad(int L) {
+    int p = 0;
+    while (sf_radix(L, p) != 0) ++p;
+    return p;
+}
+
+// The passes of a compile-time length LS (pass P, sub-transform size NS).
+template <typename T, bool INV, int TXC, int LN, int SN, int LS, int KS, int P, int NS>
+struct StaticPasses {
+    static __device__ __forceinline__ cpx<T>* run(cpx<T>* src, cpx<T>* dst, const DirTab<T>& t, int nlines, int ls,
+                                                  int es, const cpx<T>* tw, const NatIO<T>& nat) {
+        constexpr int NR = sf_nrad(LS);
+        constexpr int R = sf_radix(LS, P);
+        constexpr bool first = P == 0, last = P == NR - 1;
+        constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
+        constexpr int IO = (first ? LN : 0) | (last ? SN : 0) | (first ? 0 : 4 * SW) | (last ? 0 : 8 * SW);
+        stockham_pass<T, R, INV, TXC, IO, LS, NS, KS>(src, dst, t, P, nlines, ls, es, tw, nat);
+        __syncthreads();
+        if constexpr (last) return dst;
+        else return StaticPasses<T, INV, TXC, LN, SN, LS, KS, P + 1, NS * R>::run(dst, src, t, nlines, ls, es, tw, nat);
+    }
+};
+
+// All passes of a length-L FFT (t.nrad >= 1, or LS with sf_nrad(LS) >= 1);
+// returns the buffer holding the result (for STORE_NAT the result is in
+// nat.out and the return is unused).  LOAD_NAT: the first pass packs the real
+// natural input itself (b0 unused as input); STORE_NAT: the last pass unpacks
+// into the real natural output.  `tw` is the twiddle table W_L^t staged in
+// shared memory by the caller.
+template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT, int LS = 0, int KS = -1>
 __device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
                              const cpx<T>* tw, const NatIO<T>& nat) {
-    // row buffers between passes are swizzled (FP32 only: 8-byte elements);
-    // the input of the first and the output of the last pass are not
-    constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
     constexpr int LN = LOAD_NAT ? 1 : 0, SN = STORE_NAT ? 2 : 0;
-    cpx<T>* src = b0;
-    cpx<T>* dst = b1;
-    for (int p = 0; p < t.nrad; ++p) {
-        const bool first = p == 0, last = p == t.nrad - 1;
-        const int R = t.radix[p];
-        if (first && last) pass_dispatch<T, INV, TXC, LN | SN>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else if (first) pass_dispatch<T, INV, TXC, LN | 8 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else if (last) pass_dispatch<T, INV, TXC, SN | 4 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        else pass_dispatch<T, INV, TXC, 12 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
-        __syncthreads();
-        cpx<T>* tmp = src; src = dst; dst = tmp;
+    if constexpr (LS > 0) {
+        return StaticPasses<T, INV, TXC, LN, SN, LS, KS, 0, 1>::run(b0, b1, t, nlines, ls, es, tw, nat);
+    } else {
+        // row buffers between passes are swizzled (FP32 only: 8-byte elements);
+        // the input of the first and the output of the last pass are not
+        constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
+        cpx<T>* src = b0;
+        cpx<T>* dst = b1;
+        for (int p = 0; p < t.nrad; ++p) {
+            const bool first = p == 0, last = p == t.nrad - 1;
+            const int R = t.radix[p];
+            if (first && last) pass_dispatch<T, INV, TXC, LN | SN>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+            else if (first) pass_dispatch<T, INV, TXC, LN | 8 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+            else if (last) pass_dispatch<T, INV, TXC, SN | 4 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+            else pass_dispatch<T, INV, TXC, 12 * SW>(R, src, dst, t, p, nlines, ls, es, tw, nat);
+            __syncthreads();
+            cpx<T>* tmp = src; src = dst; dst = tmp;
+        }
+        return src;
     }
-    return src;
 }
 
 // Forward post-processing of the mode pair (m, L - m), m in [0, L/2], of one
@@ -344,43 +400,47 @@ __device__ __forceinline__ void post_store(T* out, int oes, int kind, int n, int
     }
 }
 
-template <typename T>
+template <typename T, int LS = 0, int KS = -1>
 __device__ __forceinline__ void post_forward_pair(const cpx<T>* Z, int zes, T* out, int oes, const DirTab<T>& t,
                                                   const cpx<T>* pst, const cpx<T>* mkt, int m) {
-    const int L = t.L, n = t.n;
+    const int L = LS ? LS : t.L, n = LS ? 2 * LS : t.n;
+    const int kind = KS >= 0 ? KS : t.kind;
     const cpx<T> zm = Z[(m == L ? 0 : m) * zes];
     const cpx<T> zc = conj_(Z[(m == 0 ? 0 : L - m) * zes]);
     const cpx<T> e = scale(zm + zc, T(0.5));
     const cpx<T> dd = zm - zc;
     const cpx<T> o = mk(T(0.5) * dd.y, T(-0.5) * dd.x);            // (zm - zc) / (2i)
-    post_store<T>(out, oes, t.kind, n, L, m, e + cmul(pst[m], o), mkt[m]);
+    post_store<T>(out, oes, kind, n, L, m, e + cmul(pst[m], o), kind == KIND_P ? mk(T(1), T(0)) : mkt[m]);
     const int m2 = L - m;
-    if (m2 != m) post_store<T>(out, oes, t.kind, n, L, m2, conj_(e) + cmul(pst[m2], conj_(o)), mkt[m2]);
+    if (m2 != m)
+        post_store<T>(out, oes, kind, n, L, m2, conj_(e) + cmul(pst[m2], conj_(o)),
+                      kind == KIND_P ? mk(T(1), T(0)) : mkt[m2]);
 }
 
 // V_m of the inverse (m in [0, L]) from the real coefficients X of one line.
-template <typename T>
+template <typename T, int LS = 0, int KS = -1>
 __device__ __forceinline__ cpx<T> inv_spectrum(const T* X, int xes, const DirTab<T>& t, const cpx<T>* mkt, int m) {
-    const int L = t.L, n = t.n;
-    if (t.kind == KIND_P) {
+    const int L = LS ? LS : t.L, n = LS ? 2 * LS : t.n;
+    const int kind = KS >= 0 ? KS : t.kind;
+    if (kind == KIND_P) {
         const T im = (m > 0 && m < L) ? X[(n - m) * xes] : T(0);
         return mk(X[m * xes], im);
     }
     cpx<T> u;
-    if (t.kind == KIND_N) u = mk(X[m * xes], m > 0 ? -X[(n - m) * xes] : T(0));
-    else                  u = mk(X[(n - 1 - m) * xes], m > 0 ? -X[(m - 1) * xes] : T(0));
+    if (kind == KIND_N) u = mk(X[m * xes], m > 0 ? -X[(n - m) * xes] : T(0));
+    else                u = mk(X[(n - 1 - m) * xes], m > 0 ? -X[(m - 1) * xes] : T(0));
     return cmulc(u, mkt[m]);   // exp(+i pi m / (2n)) * U_m
 }
 
 // Inverse pre-processing of the pair (m, L - m), m in [0, L/2]: Z_m (and
 // Z_{L-m} when it differs and is < L) whose unnormalised inverse FFT gives
 // n * (x[2j] + i x[2j+1]) of the packed sequence.
-template <typename T>
+template <typename T, int LS = 0, int KS = -1>
 __device__ __forceinline__ void pre_inverse_pair(const T* X, int xes, cpx<T>* Z, int zes, const DirTab<T>& t,
                                                  const cpx<T>* pst, const cpx<T>* mkt, int m) {
-    const int L = t.L;
-    const cpx<T> vm = inv_spectrum(X, xes, t, mkt, m);
-    const cpx<T> vl = inv_spectrum(X, xes, t, mkt, L - m);
+    const int L = LS ? LS : t.L;
+    const cpx<T> vm = inv_spectrum<T, LS, KS>(X, xes, t, mkt, m);
+    const cpx<T> vl = inv_spectrum<T, LS, KS>(X, xes, t, mkt, L - m);
     {
         const cpx<T> vc = conj_(vl);
         const cpx<T> s = vm + vc;

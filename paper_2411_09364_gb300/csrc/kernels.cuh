@@ -98,6 +98,14 @@ enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
 template <typename T, typename TIn> cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st);
 template <typename T, int MODE> cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st);
+// Compile-time-size FP32 variants of the transforms (periodic rows with
+// L = 128, 256, 768; column tiles (L, TX) = (64, 32), (128, 32), (256, 16)
+// of every kind): launch and return true when the sizes have one.
+// CALES_STATIC_FFT=0 in the environment turns them off.
+bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream_t st, cudaError_t* err);
+bool launch_rows_inverse_static(const RowArgs<float>& a, int mode, cudaStream_t st, cudaError_t* err);
+bool launch_cols_static(const ColArgs<float>& a, bool inverse, cudaStream_t st, cudaError_t* err);
+bool static_fft_enabled();
 template <typename T> cudaError_t launch_zsolve(const ZArgs<T>& a, cudaStream_t st);
 template <typename T> size_t zsolve_smem(int nz, int tm, int P);
 template <typename T> size_t zsolve_reg_smem(int nz, int tm, int P);

@@ -164,6 +164,19 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
     }
 }
 
+// Double -> (hi, lo) pair as split_double_int, with fewer integer operations
+// for |d| in [2^-74, 2^128) (both parts normal floats); other values (zero,
+// tiny, huge, non-finite) take the general path.
+__device__ __forceinline__ ff split_double_fast(double d) {
+    const unsigned lw = (unsigned)__double2loint(d), hw = (unsigned)__double2hiint(d);
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (e - 949u > 201u) return split_double_int(d);
+    const unsigned sg = hw & 0x80000000u;
+    const float hi = __uint_as_float(sg | ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float lo = __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float(sg | ((e - 948u) << 23));
+    return ff{hi, lo};
+}
+
 // One point of the double-float residual (the arithmetic of k_residual_ff):
 // c the point, w e s n d up its neighbours (x-, x+, y-, y+, z-, z+), fv = f.
 // SING: singular Poisson (consistency shift subtracted, gauge sum of u kept
@@ -186,7 +199,7 @@ __device__ __forceinline__ float resid_point(float2 c, float2 w, float2 e, float
     comp += __fmaf_rn(zc.hi, dul, __fmaf_rn(zc.lo, du.hi, pz.lo));
     const ff pd = two_prod(za.hi, dd.hi);
     comp += __fmaf_rn(za.hi, ddl, __fmaf_rn(za.lo, dd.hi, pd.lo));
-    const ff fs = split_double_int(fv);
+    const ff fs = split_double_fast(fv);
     ff acc;
     float err;
     if (SING) {
@@ -239,24 +252,40 @@ __global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
     float ghi = 0.f, glo = 0.f;
     const int npair = nx >> 1;
     const int j0 = blockIdx.x * a.rows_per_cta, j1 = min(j0 + a.rows_per_cta, ny);
-    const int items = (j1 - j0) * npair;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int jr = it / npair, pi = it - jr * npair;
-        const int j = j0 + jr, i = 2 * pi;
-        const long idx = kbase + (long)j * nx + i;
-        const float4 c = ld4(u + idx);
-        const float4 s = j > 0 ? ld4(u + idx - nx) : (py_ ? ld4(u + idx + (long)(ny - 1) * nx) : sc4(gy, c));
-        const float4 n = j < ny - 1 ? ld4(u + idx + nx) : (py_ ? ld4(u + idx - (long)(ny - 1) * nx) : sc4(gy, c));
-        const float4 d = kd ? ld4(u + idx - plane) : sc4(gd, c);
-        const float4 up = ku ? ld4(u + idx + plane) : sc4(gu, c);
-        const float2 w = i > 0 ? u[idx - 1] : (px_ ? u[idx + nx - 1] : make_float2(gx * c.x, gx * c.y));
-        const float2 e = i + 2 < nx ? u[idx + 2] : (px_ ? u[idx - i] : make_float2(gx * c.z, gx * c.w));
-        const double2 fv = *reinterpret_cast<const double2*>(a.f + idx);
-        const float r0 = resid_point<SING, HELM>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up), fv.x,
-                                                 cx, cy, zc, za, csh, ghi, glo);
-        const float r1 = resid_point<SING, HELM>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up), fv.y,
-                                                 cx, cy, zc, za, csh, ghi, glo);
-        *reinterpret_cast<float2*>(a.r + idx) = make_float2(r0, r1);
+    // neighbour offsets and multipliers: a ghost reads the centre (offset 0)
+    // and scales it (Neumann mirror 1, Dirichlet -1, node 0); the tests on
+    // the multipliers are uniform per CTA (z) or per row (y)
+    const long offD = kd ? -plane : 0, offU = ku ? plane : 0;
+    const float mD = kd ? 1.f : gd, mU = ku ? 1.f : gu;
+    for (int j = j0; j < j1; ++j) {
+        const long offS = j > 0 ? -(long)nx : (py_ ? (long)(ny - 1) * nx : 0);
+        const long offN = j < ny - 1 ? (long)nx : (py_ ? -(long)(ny - 1) * nx : 0);
+        const float mS = (j > 0 || py_) ? 1.f : gy, mN = (j < ny - 1 || py_) ? 1.f : gy;
+        const long rb = kbase + (long)j * nx;
+        const float2* __restrict__ ur = u + rb;
+        for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
+            const int i = 2 * pi;
+            const float2* q = ur + i;
+            const float4 c = ld4(q);
+            float4 s = ld4(q + offS), n = ld4(q + offN), d = ld4(q + offD), up = ld4(q + offU);
+            const int ow = i > 0 ? -1 : (px_ ? nx - 1 : 0);
+            const int oe = i + 2 < nx ? 2 : (px_ ? -i : 1);
+            float2 w = q[ow], e = q[oe];
+            const double2 fv = *reinterpret_cast<const double2*>(a.f + rb + i);
+            if (mS != 1.f) s = sc4(mS, s);
+            if (mN != 1.f) n = sc4(mN, n);
+            if (mD != 1.f) d = sc4(mD, d);
+            if (mU != 1.f) up = sc4(mU, up);
+            if (!px_) {
+                if (i == 0) w = make_float2(gx * w.x, gx * w.y);
+                if (i + 2 == nx) e = make_float2(gx * e.x, gx * e.y);
+            }
+            const float r0 = resid_point<SING, HELM>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up), fv.x,
+                                                     cx, cy, zc, za, csh, ghi, glo);
+            const float r1 = resid_point<SING, HELM>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up), fv.y,
+                                                     cx, cy, zc, za, csh, ghi, glo);
+            *reinterpret_cast<float2*>(a.r + rb + i) = make_float2(r0, r1);
+        }
     }
     if (SING && a.gacc) {
         double v = (double)ghi + (double)glo;

@@ -1,419 +1,49 @@
-// Transforms of the two uniform directions (eigenfunction expansion, Sec. 2.2).
-//
-// Row kernels (x): a CTA moves `rpc` consecutive rows (contiguous in memory)
-// with one TMA bulk copy each way, packs them into complex pairs in shared
-// memory, runs the Stockham passes and the post-processing, and writes the
-// rows back.  The paper's pencil transposes (Sec. 3.1) are not needed: the
-// column kernels (y) stage a tile of TX consecutive columns x all ny rows of
-// one z-plane through shared memory with 16-byte cp.async copies, so every
-// global access is a contiguous run of TX elements while the FFT runs along y
-// inside shared memory.  Twiddles are staged in shared memory; every division
-// by a run-time size is a multiply-high by a precomputed magic.
-#include "kernels.cuh"
+// Launchers of the x and y transform kernels (templates in xy_impl.cuh): the
+// compile-time-size FP32 variants where the sizes have one, else the
+// run-time-size kernels instantiated here.
+#include "xy_impl.cuh"
+
+#include <cstdlib>
 
 namespace cales {
 
-__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
-
-// Number of table entries staged in shared memory: twiddles W_L^t (L), the
-// post-processing factors W_n^m (L + 1) and, for the cosine and sine kinds,
-// exp(-i pi m/(2n)) (L + 1).
-__host__ __device__ __forceinline__ int table_len(int L, int kind) {
-    return 2 * L + 1 + (kind != KIND_P ? L + 1 : 0);
+bool static_fft_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("CALES_STATIC_FFT");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
-// Shared-memory layout of the row kernels: [mbarrier 16 B | b0 | b1 | tw | extra];
-// b0 and b1 hold a multiple of 16 complex elements (swizzle blocks).
-template <typename T> struct RowLayout {
-    size_t b0, b1, tw, extra, total;
-    __host__ __device__ RowLayout(int rpc, int L, int n, int kind, size_t extra_per_elem) {
-        const size_t C = sizeof(cpx<T>);
-        const size_t nel = ((size_t)rpc * L + 15) & ~size_t(15);
-        b0 = 16;
-        b1 = al16(b0 + nel * C);
-        tw = al16(b1 + nel * C);
-        extra = al16(tw + (size_t)table_len(L, kind) * C);
-        total = al16(extra + (size_t)rpc * n * extra_per_elem);
-    }
-};
-
-// Twiddles W_L^t (L), then the post-processing tables W_n^m and (cosine and
-// sine kinds) exp(-i pi m/(2n)) (L + 1 each), staged contiguously in shared memory.
-template <typename T>
-__device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t) {
-    const int L = t.L;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw_s[i] = t.tw[i];
-    if (t.kind != KIND_P) {
-        for (int i = threadIdx.x; i <= L; i += blockDim.x) {
-            tw_s[L + i] = t.post[i];
-            tw_s[2 * L + 1 + i] = t.mak[i];
-        }
-    } else {
-        for (int i = threadIdx.x; i <= L; i += blockDim.x) tw_s[L + i] = t.post[i];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// x direction
-// ---------------------------------------------------------------------------
-template <typename T, typename TIn>
-__global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const DirTab<T>& t = a.t;
-    const int n = t.n, L = t.L;
-    const long row0 = (long)blockIdx.x * a.rpc;
-    const int nr = (int)min((long)a.rpc, a.nrows - row0);
-    const TIn* __restrict__ in = reinterpret_cast<const TIn*>(a.in) + row0 * n;
-    T* __restrict__ out = reinterpret_cast<T*>(a.out) + row0 * n;
-    const T sc = T(a.in_scale);
-    const int tid = threadIdx.x;
-    if (n == 1) {
-        for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
-        return;
-    }
-    const RowLayout<T> lay(a.rpc, L, n, t.kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
-    cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
-    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
-    // natural rows land in b0 (same type) or in the extra area (FP64 input)
-    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b0) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
-    const int tot = nr * n;
-    if (a.bulk) {
-        if (tid == 0) {
-            mbar_init(bar, 1);
-            mbar_expect_tx(bar, (uint32_t)(tot * sizeof(TIn)));
-            bulk_g2s(stage, in, (uint32_t)(tot * sizeof(TIn)), bar);
-        }
-        stage_twiddles(tw_s, t);
-        __syncthreads();
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
-            return;
-        }
-    } else {
-        for (int e = tid; e < tot; e += blockDim.x) stage[e] = in[e];
-        stage_twiddles(tw_s, t);
-        __syncthreads();
-    }
-    NatIO<T> nat{reinterpret_cast<const T*>(b0), nullptr, n, 1};
-    const bool fused = sizeof(TIn) == sizeof(T) && t.nrad > 0 && sc == T(1);
-    if (!fused) {
-        // explicit packing (FP64 input of an FP32 solve, or n == 2)
-        T* r0 = reinterpret_cast<T*>(sizeof(TIn) == sizeof(T) ? b1 : b0);
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int r = (int)fdivu((unsigned)e, t.nmag), s = e - r * n;
-            T v;
-            if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));
-            else v = T(stage[e]);
-            r0[r * n + pack_index(t.kind, n, s)] = v * sc * pack_sign<T>(t.kind, s);
-        }
-        __syncthreads();
-    }
-    cpx<T>* Z;
-    if (fused && t.kind == KIND_P) Z = fft_lines<T, false, 0, false, false>(b0, b1, t, nr, L, 1, tw_s, nat);
-    else if (fused) Z = fft_lines<T, false, 0, true, false>(b0, b1, t, nr, L, 1, tw_s, nat);
-    else if (sizeof(TIn) == sizeof(T)) Z = fft_lines<T, false, 0, false, false>(b1, b0, t, nr, L, 1, tw_s, nat);
-    else Z = fft_lines<T, false, 0, false, false>(b0, b1, t, nr, L, 1, tw_s, nat);
-    T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
-    const int half = L / 2 + 1;
-    const int npost = nr * half;
-    for (int idx = tid; idx < npost; idx += blockDim.x) {
-        const int r = (int)fdivu((unsigned)idx, t.hmag), m = idx - r * half;
-        post_forward_pair<T>(Z + r * L, 1, ob + r * n, 1, t, pst, mkt, m);
-    }
-    if (a.bulk) {
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            bulk_s2g(out, ob, (uint32_t)(tot * sizeof(T)));
-            bulk_commit();
-            bulk_wait_read_all();
-        }
-    } else {
-        __syncthreads();
-        for (int e = tid; e < tot; e += blockDim.x) out[e] = ob[e];
-    }
-}
-
-// One inverse-x result into an 8-byte slot according to the output mode.
-template <typename T, int MODE>
-__device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
-    if (MODE == OUT_F64) {
-        *reinterpret_cast<double*>(slot) = double(v);
-    } else if (MODE == OUT_FF_INIT) {
-        *reinterpret_cast<float2*>(slot) = make_float2(float(v), 0.f);
-    } else {
-        const float2 pr = *reinterpret_cast<const float2*>(slot);
-        const ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
-        if (MODE == OUT_FF_ACC) *reinterpret_cast<float2*>(slot) = make_float2(x.hi, x.lo);
-        else *reinterpret_cast<double*>(slot) = ff_to_double(x);
-    }
-}
-
-// Inverse along x; the output mode decides how the result is stored.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const DirTab<T>& t = a.t;
-    const int n = t.n, L = t.L;
-    const long row0 = (long)blockIdx.x * a.rpc;
-    const int nr = (int)min((long)a.rpc, a.nrows - row0);
-    const T* __restrict__ in = reinterpret_cast<const T*>(a.in) + row0 * n;
-    constexpr int OSZ = MODE == OUT_T ? (int)sizeof(T) : 8;
-    unsigned char* outp = reinterpret_cast<unsigned char*>(a.out) + row0 * n * OSZ;
-    ff shift{0.f, 0.f};
-    if (MODE >= OUT_FF_ACC && a.shift_acc) shift = ff_from_double(a.shift_acc[0] * a.shift_scale);
-    const int tot = nr * n;
-    const int tid = threadIdx.x;
-    if (n == 1) {
-        for (int e = tid; e < tot; e += blockDim.x) {
-            if (MODE == OUT_T) reinterpret_cast<T*>(outp)[e] = in[e];
-            else store8<T, MODE>(outp + (long)e * 8, in[e], shift);
-        }
-        return;
-    }
-    const RowLayout<T> lay(a.rpc, L, n, t.kind, MODE != OUT_T ? 8 : 0);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
-    cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
-    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
-    unsigned char* o8 = smem_raw + lay.extra;
-    T* x0 = reinterpret_cast<T*>(b0);
-    constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL;
-    if (a.bulk) {
-        if (tid == 0) {
-            mbar_init(bar, 1);
-            const uint32_t b_in = (uint32_t)(tot * sizeof(T));
-            const uint32_t b_out = LOAD_OUT ? (uint32_t)(tot * 8) : 0u;
-            mbar_expect_tx(bar, b_in + b_out);
-            bulk_g2s(x0, in, b_in, bar);
-            if (LOAD_OUT) bulk_g2s(o8, outp, b_out, bar);
-        }
-        stage_twiddles(tw_s, t);
-        __syncthreads();
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
-            return;
-        }
-    } else {
-        for (int e = tid; e < tot; e += blockDim.x) x0[e] = in[e];
-        if (LOAD_OUT)
-            for (int e = tid; e < tot; e += blockDim.x)
-                reinterpret_cast<float2*>(o8)[e] = reinterpret_cast<const float2*>(outp)[e];
-        stage_twiddles(tw_s, t);
-        __syncthreads();
-    }
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
-    const int half = L / 2 + 1;
-    const int npre = nr * half;
-    for (int idx = tid; idx < npre; idx += blockDim.x) {
-        const int r = (int)fdivu((unsigned)idx, t.hmag), m = idx - r * half;
-        pre_inverse_pair<T>(x0 + r * n, 1, b1 + r * L, 1, t, pst, mkt, m);
-    }
-    __syncthreads();
-    unsigned char* ob;
-    if (t.nrad > 0) {
-        // the last pass unpacks straight into natural order (real rows); a
-        // periodic row's packed pairs already are its natural order
-        T* natout = reinterpret_cast<T*>((t.nrad & 1) ? b0 : b1);
-        const NatIO<T> nat{nullptr, natout, n, 1};
-        if (t.kind == KIND_P) fft_lines<T, true, 0, false, false>(b1, b0, t, nr, L, 1, tw_s, nat);
-        else fft_lines<T, true, 0, false, true>(b1, b0, t, nr, L, 1, tw_s, nat);
-        if (MODE == OUT_T) {
-            ob = reinterpret_cast<unsigned char*>(natout);
-        } else {
-            ob = o8;
-            for (int e = tid; e < tot; e += blockDim.x) store8<T, MODE>(ob + (long)e * 8, natout[e], shift);
-        }
-    } else {
-        const T* zr = reinterpret_cast<const T*>(b1);
-        T* tmp = reinterpret_cast<T*>(b0);
-        ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(tmp) : o8;
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int r = (int)fdivu((unsigned)e, t.nmag), s2 = e - r * n;
-            const T v = zr[r * n + pack_index(t.kind, n, s2)] * pack_sign<T>(t.kind, s2);
-            if (MODE == OUT_T) tmp[e] = v;
-            else store8<T, MODE>(ob + (long)e * 8, v, shift);
-        }
-    }
-    if (a.bulk) {
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            bulk_s2g(outp, ob, (uint32_t)(tot * OSZ));
-            bulk_commit();
-            bulk_wait_read_all();
-        }
-    } else {
-        __syncthreads();
-        if (MODE == OUT_T) {
-            for (int e = tid; e < tot; e += blockDim.x) reinterpret_cast<T*>(outp)[e] = reinterpret_cast<const T*>(ob)[e];
-        } else {
-            for (int e = tid; e < tot; e += blockDim.x)
-                reinterpret_cast<double*>(outp)[e] = reinterpret_cast<const double*>(ob)[e];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// y direction: tiles of TX columns of one z-plane, in place.  With `bulk`, the
-// tile moves by 16-byte cp.async copies (all in flight), else by plain loads.
-// Shared memory: [16 B | b0 | b1 | tw].
-// ---------------------------------------------------------------------------
-template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L, int kind) {
-    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)table_len(L, kind) * sizeof(cpx<T>);
-}
-
-template <typename T, int TX, bool INV>
-__global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const DirTab<T>& t = a.t;
-    const int n = t.n, L = t.L;     // n = ny
-    const int nx = a.nx;
-    const int tiles_x = (nx + TX - 1) / TX;
-    const int plane = blockIdx.x / tiles_x;
-    const int x0 = (blockIdx.x - plane * tiles_x) * TX;
-    const int wx = min(TX, nx - x0);
-    const int tid = threadIdx.x;
-    T* __restrict__ base = reinterpret_cast<T*>(a.data) + (long)plane * n * nx + x0;
-    cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + 16);
-    cpx<T>* b1 = b0 + TX * L;
-    cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)));
-    const int tot = n * TX;
-    T* nat = reinterpret_cast<T*>(b0);                 // natural-order tile [ny][TX]
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
-    constexpr int EPC = 16 / (int)sizeof(T);
-    constexpr int CPR = TX / EPC > 0 ? TX / EPC : 1;
-    if (a.bulk) {
-        for (int e = tid; e < n * CPR; e += blockDim.x) {
-            const int s = e / CPR, c0 = (e - s * CPR) * EPC;
-            cp_async16(nat + s * TX + c0, base + (long)s * nx + (c0 < wx ? c0 : 0), c0 < wx);
-        }
-        stage_twiddles(tw_s, t);
-        cp_async_wait_all();
-    } else {
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            nat[e] = (c < wx) ? base[(long)s * nx + c] : T(0);
-        }
-        stage_twiddles(tw_s, t);
-    }
-    __syncthreads();
-    T* ob;
-    const int half = L / 2 + 1;
-    if (!INV) {
-        cpx<T>* Z;
-        if (t.nrad > 0) {
-            const NatIO<T> natio{nat, nullptr, 1, TX};
-            Z = fft_lines<T, false, TX, true, false>(b0, b1, t, TX, 1, TX, tw_s, natio);
-        } else {
-            T* r1 = reinterpret_cast<T*>(b1);
-            for (int e = tid; e < tot; e += blockDim.x) {
-                const int s = e / TX, c = e - s * TX;
-                const int d = pack_index(t.kind, n, s);
-                r1[((d >> 1) * TX + c) * 2 + (d & 1)] = nat[e] * pack_sign<T>(t.kind, s);
-            }
-            __syncthreads();
-            Z = b1;
-        }
-        ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
-        const int npost = half * TX;
-        for (int idx = tid; idx < npost; idx += blockDim.x) {
-            const int m = idx / TX, c = idx - m * TX;
-            post_forward_pair<T>(Z + c, TX, ob + c, TX, t, pst, mkt, m);
-        }
-    } else {
-        const int npre = half * TX;
-        for (int idx = tid; idx < npre; idx += blockDim.x) {
-            const int m = idx / TX, c = idx - m * TX;
-            pre_inverse_pair<T>(nat + c, TX, b1 + c, TX, t, pst, mkt, m);
-        }
-        __syncthreads();
-        if (t.nrad > 0) {
-            T* natout = reinterpret_cast<T*>((t.nrad & 1) ? b0 : b1);
-            const NatIO<T> natio{nullptr, natout, 1, TX};
-            fft_lines<T, true, TX, false, true>(b1, b0, t, TX, 1, TX, tw_s, natio);
-            ob = natout;
-        } else {
-            const T* zr = reinterpret_cast<const T*>(b1);
-            ob = reinterpret_cast<T*>(b0);
-            for (int e = tid; e < tot; e += blockDim.x) {
-                const int s = e / TX, c = e - s * TX;
-                const int d = pack_index(t.kind, n, s);
-                ob[e] = zr[((d >> 1) * TX + c) * 2 + (d & 1)] * pack_sign<T>(t.kind, s);
-            }
-        }
-    }
-    __syncthreads();
-    if (a.bulk) {
-        for (int e = tid; e < n * CPR; e += blockDim.x) {
-            const int s = e / CPR, c0 = (e - s * CPR) * EPC;
-            if (c0 < wx)
-                *reinterpret_cast<float4*>(base + (long)s * nx + c0) = *reinterpret_cast<const float4*>(ob + s * TX + c0);
-        }
-    } else {
-        for (int e = tid; e < tot; e += blockDim.x) {
-            const int s = e / TX, c = e - s * TX;
-            if (c < wx) base[(long)s * nx + c] = ob[e];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// launchers
-// ---------------------------------------------------------------------------
 template <typename T, typename TIn>
 cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
-    auto kern = k_rows_forward<T, TIn>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
-    const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
-    kern<<<grid, 256, lay.total, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t err = cudaSuccess;
+        if (launch_rows_forward_static(a, sizeof(TIn) == 8, st, &err)) return err;
+    }
+    return launch_rows_forward_v<T, TIn, 0, -1>(a, st);
 }
 
 template <typename T, int MODE>
 cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, MODE != OUT_T ? 8 : 0);
-    auto kern = k_rows_inverse<T, MODE>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
-    const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
-    kern<<<grid, 256, lay.total, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T, int TX>
-static cudaError_t launch_cols_tx(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
-    const size_t sm = col_smem<T>(TX, a.t.L, a.t.kind);
-    const unsigned grid = (unsigned)(a.nplanes * ((a.nx + TX - 1) / TX));
-    if (inverse) {
-        auto kern = k_cols<T, TX, true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<grid, 256, sm, st>>>(a);
-    } else {
-        auto kern = k_cols<T, TX, false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<grid, 256, sm, st>>>(a);
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t err = cudaSuccess;
+        if (launch_rows_inverse_static(a, MODE, st, &err)) return err;
     }
-    return cudaGetLastError();
+    return launch_rows_inverse_v<T, MODE, 0, -1>(a, st);
 }
 
 template <typename T>
 cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t err = cudaSuccess;
+        if (launch_cols_static(a, inverse, st, &err)) return err;
+    }
     switch (a.tx) {
-        case 32: return launch_cols_tx<T, 32>(a, inverse, st);
-        case 16: return launch_cols_tx<T, 16>(a, inverse, st);
-        case 8: return launch_cols_tx<T, 8>(a, inverse, st);
-        default: return launch_cols_tx<T, 4>(a, inverse, st);
+        case 32: return launch_cols_v<T, 32, 0, -1>(a, inverse, st);
+        case 16: return launch_cols_v<T, 16, 0, -1>(a, inverse, st);
+        case 8: return launch_cols_v<T, 8, 0, -1>(a, inverse, st);
+        default: return launch_cols_v<T, 4, 0, -1>(a, inverse, st);
     }
 }
 

@@ -1,912 +1,11 @@
-// z direction of the eigenfunction expansion: one tridiagonal system per mode
-// (mx, my), solved along the stretched direction (Thomas algorithm, Sec. 2.2).
-// For (sigma - alpha L) u = g with L = L_z + lambda(mx, my):
-//
-//   row k:  -A_k u[k-1] + (sigma - alpha lambda + A_k + C_k + bc) u[k] - C_k u[k+1] = g_k
-//   A_k = alpha / (dzc[k] dzf[k]),  C_k = alpha / (dzc[k+1] dzf[k])
-//
-// Pivots are carried in excess form d_k = C~_k + e_k (C~_k = C_k below the top
-// row, 0 on it) with
-//   e_k = (sigma - alpha lambda) + A_k e_{k-1} / d_{k-1}   (+ boundary terms)
-// in which every term is non-negative: no cancellation even for the
-// near-singular low modes on a strongly stretched grid.
-//
-// Layout and parallelism.  A CTA owns `tm` consecutive modes (contiguous in
-// memory) and the whole z extent.  The [nz][tm] tile is moved between global
-// and shared memory by TMA bulk copies, one row per copy.  P threads share a
-// mode, each owning a segment of about nz/P rows:
-//   A  the pivot recurrence of a segment is a product of 2x2 positive matrices
-//      (a Moebius map of e), composed in the segment and chained across the P
-//      lanes with shuffles;
-//   C  the forward elimination y_k = (g_k + A_k y_{k-1}) / d_k is affine in
-//      y_{k-1}: composed per segment, chained across lanes;
-//   E  the segment is swept with the correct incoming state, writing y_k and
-//      composing the back-substitution map x_k0 = Q + R x_k1;
-//   F  the back-substitution maps are chained from the top segment down;
-//   G  each segment back-substitutes, recomputing its pivots chunk by chunk
-//      from checkpoints, so shared memory holds only the tile.
-// Mode (0,0) of a singular Poisson problem is redone by one thread: its
-// right-hand side is projected (dzf-weighted mean removed), its last row is
-// pinned to zero and the result is gauged to zero weighted mean.
-#include "kernels.cuh"
+// FP32 instantiations of the z tridiagonal kernels (templates in z_impl.cuh).
+#include "z_impl.cuh"
 
 namespace cales {
 
-template <typename T> __device__ __forceinline__ T rcp_(T d);
-template <> __device__ __forceinline__ float rcp_<float>(float d) { return __frcp_rn(d); }
-// FP64: FP32 reciprocal refined by two Newton steps (24 -> 48 -> ~53 bits);
-// IEEE FP64 division is far slower on GB300's narrow FP64 pipe.
-template <> __device__ __forceinline__ double rcp_<double>(double d) {
-    double r = (double)__frcp_rn((float)d);
-    r = r * fma(-d, r, 2.0);
-    r = r * fma(-d, r, 2.0);
-    return r;
-}
-
-// Pivot recurrence state: e_k and 1 / d_k of the last row visited.
-template <typename T> struct Piv {
-    T e, inv;
-    const T *sA, *sC;
-    T base, ebot, etop;
-    int nz;
-    __device__ __forceinline__ T ct(int k) const { return k < nz - 1 ? sC[k] : T(0); }
-    __device__ __forceinline__ void first() {        // row 0
-        e = base + ebot + (nz == 1 ? etop : T(0));
-        inv = rcp_<T>(ct(0) + e);
-    }
-    __device__ __forceinline__ void step(int k) {     // row k >= 1 from row k-1
-        e = base + sA[k] * e * inv + (k == nz - 1 ? etop : T(0));
-        inv = rcp_<T>(ct(k) + e);
-    }
-    // start a sweep at row k0 given e of row k0-1 (ignored when k0 == 0)
-    __device__ __forceinline__ void start(int k0, T e_prev) {
-        if (k0 == 0) {
-            first();
-        } else {
-            e = e_prev;
-            inv = rcp_<T>(ct(k0 - 1) + e_prev);
-            step(k0);
-        }
-    }
-};
-
-// Serial solve of one line (the singular mode 0): raw g0 -> x into col.
-template <typename T>
-__device__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T* r0, const T* sA, const T* sC, const T* sG,
-                            const T* sO, const double* dzf, int nz, T base, bool singular, double* cacc,
-                            double cacc_scale, int sk) {
-    // coefficient tables may be skewed by one slot per segment of sk rows
-#define SKI(k) ((sk) > 0 ? (k) + (k) / (sk) : (k))
-    double gmean = 0.0;
-    if (singular) {
-        double s = 0.0, sw = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            s += dzf[k] * double(g0[k]) * double(sG[SKI(k)]);
-            sw += dzf[k];
-        }
-        gmean = s / sw;
-        if (cacc) cacc[0] += gmean * cacc_scale;
-    }
-    T e = T(0), inv = T(0), y = T(0);
-    for (int k = 0; k < nz; ++k) {
-        const T ct = k < nz - 1 ? sC[SKI(k)] : T(0);
-        e = (k == 0) ? base : base + sA[SKI(k)] * e * inv;
-        inv = rcp_<T>(ct + e);
-        const T g = T(double(g0[k]) * double(sG[SKI(k)]) - gmean);
-        if (singular && k == nz - 1) y = T(0);
-        else y = (g + (k > 0 ? sA[SKI(k)] : T(0)) * y) * inv;
-        tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] = y;
-        r0[k] = (k < nz - 1) ? ct * inv : T(0);
-    }
-    T x = T(0);
-    for (int k = nz - 1; k >= 0; --k) {
-        x = tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] + r0[k] * x;
-        tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] = x;
-    }
-    if (singular) {
-        double s = 0.0, sw = 0.0;
-        for (int k = 0; k < nz; ++k) { s += dzf[k] * double(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride]); sw += dzf[k]; }
-        const double mm = s / sw;
-        for (int k = 0; k < nz; ++k) tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] = T(double(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride]) - mm);
-    }
-    for (int k = 0; k < nz; ++k) tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] *= sO[SKI(k)];
-#undef SKI
-}
-
-// Segment stride of the shared tile (elements): m*tm rounded so that the P
-// segments of a mode fall in different banks (stride = 32/P mod 32 words for
-// FP32) while every row stays 16-byte aligned for the bulk copies.
-template <typename T> __host__ __device__ __forceinline__ int zseg_stride(int m, int tm, int P) {
-    const int words = (int)sizeof(T) / 4;
-    const int want = P <= 8 ? (32 / P) / words : 0;     // residue in elements
-    const int align = 16 / (int)sizeof(T);
-    int st = m * tm;
-    if (want > 0) {
-        int r = st % (32 / words);
-        int add = (want - r + 32 / words) % (32 / words);
-        st += add;
-    }
-    return (st + align - 1) / align * align;
-}
-
-template <typename T, int P, int CK>
-__global__ void __launch_bounds__(256) k_zsolve(ZArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TM = a.tm, nz = a.nz;
-    const int m = (nz + P - 1) / P;
-    const int nchs = (m + CK - 1) / CK;
-    const long nmodes = (long)a.nx * a.ny;
-    const int nthr = blockDim.x;
-    const int segs = zseg_stride<T>(m, TM, P);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    T* tile = reinterpret_cast<T*>(smem_raw + 16);
-    T* ck = tile + (long)segs * P;
-    T* sA = ck + (long)nchs * nthr;
-    T* sC = sA + nz;
-    T* sG = sC + nz;
-    T* sO = sG + nz;
-    T* save0 = sO + nz;
-    T* r0 = save0 + nz;
-    const long q0 = (long)blockIdx.x * TM;
-    const int w = (int)min((long)TM, nmodes - q0);
-    const int tid = threadIdx.x;
-
-    if (a.bulk && tid == 0) mbar_init(bar, 1);
-    for (int k = tid; k < nz; k += nthr) {
-        sA[k] = a.alpha * a.za[k];
-        sC[k] = a.alpha * a.zc[k];
-        double gs = double(a.scale), os = 1.0;
-        if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
-        sG[k] = T(gs);
-        sO[k] = T(os);
-    }
-    __syncthreads();
-    if (a.bulk) {
-        if (tid < 32) {
-            const uint32_t rowb = (uint32_t)(w * sizeof(T));
-            if (tid == 0) mbar_expect_tx(bar, rowb * (uint32_t)nz);
-            __syncwarp();
-            for (int k = tid; k < nz; k += 32) {
-                const int sg = k / m;
-                bulk_g2s(tile + (long)sg * segs + (long)(k - sg * m) * TM, a.data + q0 + (long)k * nmodes, rowb, bar);
-            }
-        }
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
-            return;
-        }
-    } else {
-        for (long e = tid; e < (long)nz * TM; e += nthr) {
-            const int k = (int)(e / TM), c = (int)(e - (long)k * TM);
-            const int sg = k / m;
-            tile[(long)sg * segs + (long)(k - sg * m) * TM + c] = c < w ? a.data[(long)k * nmodes + q0 + c] : T(0);
-        }
-        __syncthreads();
-    }
-    const bool sing_tile = a.singular && q0 == 0;
-    if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) save0[k] = tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * TM];
-    __syncthreads();
-
-    const int c = tid / P, s = tid - c * P;
-    const unsigned lane = tid & 31;
-    const unsigned gmask = P == 32 ? 0xffffffffu : (((1u << P) - 1u) << (lane & ~(unsigned)(P - 1)));
-    bool bad = false;
-    if (c < w) {
-        const long q = q0 + c;
-        const int my = (int)(q / a.nx), mx = (int)(q - (long)my * a.nx);
-        const T lam = a.lamx[mx] + a.lamy[my];
-        const T base = a.sigma - a.alpha * lam;
-        const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
-        const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
-        const int k0 = s * m, k1 = min(k0 + m, nz);
-        T* col = tile + (long)s * segs + c - (long)k0 * TM;   // row k of this segment at col[k * TM]
-        Piv<T> pv{T(0), T(0), sA, sC, base, ebot, etop, nz};
-
-        // A: composite pivot map of the segment
-        T g11 = T(1), g12 = T(0), g21 = T(0), g22 = T(1);
-        T e_end = T(0);
-        if (s == 0) {
-            if (k1 > 0) {
-                pv.first();
-                for (int k = 1; k < k1; ++k) pv.step(k);
-                e_end = pv.e;
-            }
-        } else {
-            for (int k = k0; k < k1; ++k) {
-                const T x = (k == nz - 1) ? etop : T(0);
-                const T am = base + sA[k] + x, bm = (base + x) * sC[k - 1], cm = sC[k - 1];
-                const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
-                const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
-                g11 = n11; g12 = n12; g21 = n21; g22 = n22;
-                if (((k - k0) & 3) == 3) {
-                    const T nrm = rcp_<T>(g11 + g12 + g21 + g22);
-                    g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
-                }
-            }
-        }
-        // B: chain the pivot maps across the lanes of the mode
-        T e_in = T(0);
-        for (int j = 1; j < P; ++j) {
-            const T t = __shfl_up_sync(gmask, e_end, 1, P);
-            if (s == j) {
-                e_in = t;
-                e_end = (g11 * t + g12) * rcp_<T>(g21 * t + g22);
-            }
-        }
-        // C: affine composite of the forward elimination over the segment
-        T al = T(1), be = T(0);
-        for (int k = k0; k < k1; ++k) {
-            if (k == k0) pv.start(k0, e_in); else pv.step(k);
-            const T ak = k > 0 ? sA[k] : T(0);
-            const T g = col[(long)k * TM] * sG[k];
-            al = ak * pv.inv * al;
-            be = (g + ak * be) * pv.inv;
-        }
-        T y_end = (s == 0) ? be : T(0);
-        T y_in = T(0);
-        for (int j = 1; j < P; ++j) {
-            const T t = __shfl_up_sync(gmask, y_end, 1, P);
-            if (s == j) {
-                y_in = t;
-                y_end = al * t + be;
-            }
-        }
-        // E: forward sweep writing y, checkpoints, back-substitution composite
-        T y = y_in, Q = T(0), R = T(1);
-        for (int k = k0; k < k1; ++k) {
-            if (k == k0) pv.start(k0, e_in); else pv.step(k);
-            if (((k - k0) % CK) == 0) ck[((k - k0) / CK) * nthr + tid] = pv.e;
-            const T ak = k > 0 ? sA[k] : T(0);
-            y = (col[(long)k * TM] * sG[k] + ak * y) * pv.inv;
-            col[(long)k * TM] = y;
-            Q += R * y;
-            R *= pv.ct(k) * pv.inv;
-            bad |= !(pv.inv > T(0));
-        }
-        // F: chain the back-substitution maps from the top segment down
-        T xs = Q, x_next = T(0);
-        for (int j = P - 2; j >= 0; --j) {
-            const T t = __shfl_down_sync(gmask, xs, 1, P);
-            if (s == j) {
-                x_next = t;
-                xs = Q + R * t;
-            }
-        }
-        // G: back-substitute the segment, chunks from the top
-        T x = x_next;
-        for (int ch = nchs - 1; ch >= 0; --ch) {
-            const int kc0 = k0 + ch * CK;
-            if (kc0 >= k1) continue;
-            const int kc1 = min(kc0 + CK, k1);
-            T rr[CK];
-            Piv<T> qv{ck[ch * nthr + tid], T(0), sA, sC, base, ebot, etop, nz};
-            qv.inv = rcp_<T>(qv.ct(kc0) + qv.e);
-#pragma unroll
-            for (int j = 0; j < CK; ++j) {
-                const int k = kc0 + j;
-                if (k < kc1) {
-                    if (j > 0) qv.step(k);
-                    rr[j] = qv.ct(k) * qv.inv;
-                }
-            }
-#pragma unroll
-            for (int j = CK - 1; j >= 0; --j) {
-                const int k = kc0 + j;
-                if (k < kc1) {
-                    x = col[(long)k * TM] + rr[j] * x;
-                    col[(long)k * TM] = x * sO[k];
-                    bad |= !isfinite(x);
-                }
-            }
-        }
-        if (sing_tile && c == 0) bad = false;
-    }
-    if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
-    __syncthreads();
-    if (sing_tile && tid == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0);
-        for (int k = 0; k < nz; ++k)
-            if (!isfinite(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * TM])) {
-                if (a.status) atomicOr(a.status, ST_NONFINITE);
-                break;
-            }
-    }
-    if (a.bulk) {
-        fence_proxy_async();
-        __syncthreads();
-        if (tid < 32) {
-            const uint32_t rowb = (uint32_t)(w * sizeof(T));
-            for (int k = tid; k < nz; k += 32) {
-                const int sg = k / m;
-                bulk_s2g(a.data + q0 + (long)k * nmodes, tile + (long)sg * segs + (long)(k - sg * m) * TM, rowb);
-            }
-            bulk_commit();
-            bulk_wait_read_all();
-        }
-    } else {
-        __syncthreads();
-        for (long e = tid; e < (long)nz * TM; e += nthr) {
-            const int k = (int)(e / TM), cc = (int)(e - (long)k * TM);
-            const int sg = k / m;
-            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[(long)sg * segs + (long)(k - sg * m) * TM + cc];
-        }
-    }
-}
-
-
-// Fast reciprocal: FP32 hardware approximation + one Newton step (about 1 ulp);
-// FP64 as rcp_ (FP32 seed + two Newton steps).
-template <typename T> __device__ __forceinline__ T frcp(T d);
-template <> __device__ __forceinline__ float frcp<float>(float d) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-    return r * __fmaf_rn(-d, r, 2.0f);
-}
-template <> __device__ __forceinline__ double frcp<double>(double d) { return rcp_<double>(d); }
-
-// Segmented Thomas with the segment's pivot reciprocals held in registers
-// (MAXM >= rows per segment).  Same phases as k_zsolve; the pivot recurrence
-// runs once per row (phase C) instead of being recomputed.  Coefficient
-// tables are skewed by one slot per segment so the P segments of a warp read
-// different banks.
-template <typename T, int P, int MAXM>
-__global__ void __launch_bounds__(256) k_zsolve_reg(ZArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TM = a.tm, nz = a.nz;
-    const int m = (nz + P - 1) / P;
-    const long nmodes = (long)a.nx * a.ny;
-    const int nthr = blockDim.x;
-    const int segs = zseg_stride<T>(m, TM, P);
-    const int nsk = nz + P;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    T* tile = reinterpret_cast<T*>(smem_raw + 16);
-    T* sA = tile + segs * P;
-    T* sC = sA + nsk;
-    T* sG = sC + nsk;
-    T* sO = sG + nsk;
-    T* save0 = sO + nsk;
-    T* r0 = save0 + nz;
-    const long q0 = (long)blockIdx.x * TM;
-    const int w = (int)min((long)TM, nmodes - q0);
-    const int tid = threadIdx.x;
-
-    if (a.bulk && tid == 0) mbar_init(bar, 1);
-    for (int k = tid; k < nz; k += nthr) {
-        const int pk = k + k / m;
-        sA[pk] = a.alpha * a.za[k];
-        sC[pk] = a.alpha * a.zc[k];
-        double gs = double(a.scale), os = 1.0;
-        if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
-        sG[pk] = T(gs);
-        sO[pk] = T(os);
-    }
-    __syncthreads();
-    if (a.bulk) {
-        if (tid < 32) {
-            const uint32_t rowb = (uint32_t)(w * sizeof(T));
-            if (tid == 0) mbar_expect_tx(bar, rowb * (uint32_t)nz);
-            __syncwarp();
-            for (int k = tid; k < nz; k += 32) {
-                const int sg = k / m;
-                bulk_g2s(tile + sg * segs + (k - sg * m) * TM, a.data + q0 + (long)k * nmodes, rowb, bar);
-            }
-        }
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, 0);
-            return;
-        }
-    } else {
-        for (int e = tid; e < nz * TM; e += nthr) {
-            const int k = e / TM, c = e - k * TM;
-            const int sg = k / m;
-            tile[sg * segs + (k - sg * m) * TM + c] = c < w ? a.data[(long)k * nmodes + q0 + c] : T(0);
-        }
-        __syncthreads();
-    }
-    const bool sing_tile = a.singular && q0 == 0;
-    if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) save0[k] = tile[(k / m) * segs + (k - (k / m) * m) * TM];
-    __syncthreads();
-
-    const int c = tid / P, s = tid - c * P;
-    const unsigned lane = tid & 31;
-    const unsigned gmask = P == 32 ? 0xffffffffu : (((1u << P) - 1u) << (lane & ~(unsigned)(P - 1)));
-    bool bad = false;
-    if (c < w) {
-        const long q = q0 + c;
-        const int my = (int)(q / a.nx), mx = (int)(q - (long)my * a.nx);
-        const T lam = a.lamx[mx] + a.lamy[my];
-        const T base = a.sigma - a.alpha * lam;
-        const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
-        const int ktop = (nz - 1) + (nz - 1) / m;
-        const T etop = a.zhi == ZBC_D ? T(2) * sC[ktop] : (a.zhi == ZBC_DF ? sC[ktop] : T(0));
-        const int k0 = s * m;
-        const int mseg = max(0, min(m, nz - k0));
-        const T* A = sA + k0 + s;
-        const T* Cc = sC + k0 + s;
-        const T* G = sG + k0 + s;
-        const T* O = sO + k0 + s;
-        T* col = tile + s * segs + c;
-        const T cprev = s > 0 ? sC[(k0 - 1) + (s - 1)] : T(0);
-#define CT(j) ((k0 + (j) < nz - 1) ? Cc[j] : T(0))
-#define XT(j) ((k0 + (j) == nz - 1) ? etop : T(0))
-
-        // A: composite pivot map of the segment (2x2 positive matrices)
-        T g11 = T(1), g12 = T(0), g21 = T(0), g22 = T(1);
-        T e_end = T(0);
-        if (s == 0) {
-            if (mseg > 0) {
-                T e = base + ebot + (nz == 1 ? etop : T(0));
-#pragma unroll
-                for (int j = 1; j < MAXM; ++j)
-                    if (j < mseg) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
-                e_end = e;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                if (j < mseg) {
-                    const T x = XT(j);
-                    const T cm = j > 0 ? Cc[j - 1] : cprev;
-                    const T am = base + A[j] + x, bm = (base + x) * cm;
-                    const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
-                    const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
-                    g11 = n11; g12 = n12; g21 = n21; g22 = n22;
-                    if ((j & 3) == 3) {
-                        const T nrm = frcp<T>(g11 + g12 + g21 + g22);
-                        g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
-                    }
-                }
-            }
-        }
-        // B: chain the pivot maps across the lanes
-        T e_in = T(0);
-#pragma unroll
-        for (int j = 1; j < P; ++j) {
-            const T t = __shfl_up_sync(gmask, e_end, 1, P);
-            if (s == j) {
-                e_in = t;
-                e_end = (g11 * t + g12) * frcp<T>(g21 * t + g22);
-            }
-        }
-        // C: pivots of the segment (kept in registers) and the affine
-        //    composite of the forward elimination
-        T inv[MAXM];
-        T al = T(1), be = T(0);
-        {
-            T e;
-            if (k0 == 0) e = base + ebot + (nz == 1 ? etop : T(0));
-            else e = base + A[0] * e_in * frcp<T>(cprev + e_in) + XT(0);
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                if (j < mseg) {
-                    if (j > 0) e = base + A[j] * e * inv[j - 1] + XT(j);
-                    inv[j] = frcp<T>(CT(j) + e);
-                    const T ak = (k0 + j > 0) ? A[j] : T(0);
-                    al = ak * inv[j] * al;
-                    be = (col[j * TM] * G[j] + ak * be) * inv[j];
-                    bad |= !(inv[j] > T(0));
-                }
-            }
-        }
-        T y_end = (s == 0) ? be : T(0);
-        T y_in = T(0);
-#pragma unroll
-        for (int j = 1; j < P; ++j) {
-            const T t = __shfl_up_sync(gmask, y_end, 1, P);
-            if (s == j) {
-                y_in = t;
-                y_end = al * t + be;
-            }
-        }
-        // E: forward sweep writing y; back-substitution composite
-        T y = y_in, Q = T(0), R = T(1);
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            if (j < mseg) {
-                const T ak = (k0 + j > 0) ? A[j] : T(0);
-                y = (col[j * TM] * G[j] + ak * y) * inv[j];
-                col[j * TM] = y;
-                Q += R * y;
-                R *= CT(j) * inv[j];
-            }
-        }
-        // F: chain the back-substitution maps from the top segment down
-        T xs = Q, x_next = T(0);
-#pragma unroll
-        for (int j = P - 2; j >= 0; --j) {
-            const T t = __shfl_down_sync(gmask, xs, 1, P);
-            if (s == j) {
-                x_next = t;
-                xs = Q + R * t;
-            }
-        }
-        // G: back-substitution
-        T x = x_next;
-#pragma unroll
-        for (int j = MAXM - 1; j >= 0; --j) {
-            if (j < mseg) {
-                x = col[j * TM] + CT(j) * inv[j] * x;
-                col[j * TM] = x * O[j];
-                bad |= !isfinite(x);
-            }
-        }
-#undef CT
-#undef XT
-        if (sing_tile && c == 0) bad = false;
-    }
-    if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
-    __syncthreads();
-    if (sing_tile && tid == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, m);
-        for (int k = 0; k < nz; ++k)
-            if (!isfinite(tile[(k / m) * segs + (k - (k / m) * m) * TM])) {
-                if (a.status) atomicOr(a.status, ST_NONFINITE);
-                break;
-            }
-    }
-    if (a.bulk) {
-        fence_proxy_async();
-        __syncthreads();
-        if (tid < 32) {
-            const uint32_t rowb = (uint32_t)(w * sizeof(T));
-            for (int k = tid; k < nz; k += 32) {
-                const int sg = k / m;
-                bulk_s2g(a.data + q0 + (long)k * nmodes, tile + sg * segs + (k - sg * m) * TM, rowb);
-            }
-            bulk_commit();
-            bulk_wait_read_all();
-        }
-    } else {
-        __syncthreads();
-        for (int e = tid; e < nz * TM; e += nthr) {
-            const int k = e / TM, cc = e - k * TM;
-            const int sg = k / m;
-            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[sg * segs + (k - sg * m) * TM + cc];
-        }
-    }
-}
-
-template <typename T>
-size_t zsolve_reg_smem(int nz, int tm, int P) {
-    const int m = (nz + P - 1) / P;
-    const size_t segs = (size_t)zseg_stride<T>(m, tm, P);
-    return 16 + (segs * P + 4 * (size_t)(nz + P) + 2 * (size_t)nz) * sizeof(T);
-}
-
-template <typename T, int P, int MAXM>
-static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
-    const size_t sm = zsolve_reg_smem<T>(a.nz, a.tm, P);
-    auto kern = k_zsolve_reg<T, P, MAXM>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const long nmodes = (long)a.nx * a.ny;
-    const unsigned grid = (unsigned)((nmodes + a.tm - 1) / a.tm);
-    kern<<<grid, a.tm * P, sm, st>>>(a);
-    return cudaGetLastError();
-}
-
-
-// ---------------------------------------------------------------------------
-// Warp-per-segment variant: a CTA owns 32 consecutive modes; warp s owns rows
-// [s*m, s*m + m) of all 32 modes, so every shared-memory row access of a warp
-// is one contiguous 128-byte (FP32) row and every coefficient read is a
-// broadcast.  The tile moves by 16-byte cp.async copies (all in flight at
-// once) and vector stores.  Segment states are chained by warp 0 through
-// shared memory.  Pivot reciprocals of a segment stay in registers.
-// ---------------------------------------------------------------------------
-// FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
-// predicates and the first/last-row conditions reduce to compile-time tests
-// on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
-// transposed) instead of the uniform forward scale.
-template <typename T, int MAXM, bool FULL, bool ADJ>
-__global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TM = 32;
-    constexpr int EPC = 16 / (int)sizeof(T);          // elements per 16-byte chunk
-    constexpr int CPR = TM / EPC;                      // chunks per row
-    const int nz = a.nz;
-    const int P = blockDim.x / 32;
-    const int m = (nz + P - 1) / P;
-    const long nmodes = (long)a.nx * a.ny;
-    const int nthr = blockDim.x;
-    T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
-    T* ch = tile + (long)P * m * TM;                   // 6 x [P][32] chain states
-    T* sA = ch + 6 * P * TM;
-    T* sC = sA + nz;
-    T* sG = sC + nz;
-    T* sO = sG + nz;
-    T* save0 = sO + nz;
-    T* r0 = save0 + nz;
-    const long q0 = (long)blockIdx.x * TM;
-    const int w = (int)min((long)TM, nmodes - q0);
-    const int tid = threadIdx.x;
-
-    for (int k = tid; k < nz; k += nthr) {
-        sA[k] = a.alpha * a.za[k];
-        sC[k] = a.alpha * a.zc[k];
-        double gs = double(a.scale), os = 1.0;
-        if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
-        sG[k] = T(gs);
-        sO[k] = T(os);
-    }
-    if (a.bulk) {
-        for (int e = tid; e < nz * CPR; e += nthr) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            cp_async16(tile + k * TM + c0, a.data + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
-        }
-        cp_async_wait_all();
-    } else {
-        for (int e = tid; e < nz * TM; e += nthr) {
-            const int k = e / TM, c = e - k * TM;
-            tile[e] = c < w ? a.data[(long)k * nmodes + q0 + c] : T(0);
-        }
-    }
-    __syncthreads();
-    const bool sing_tile = a.singular && q0 == 0;
-    if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) save0[k] = tile[k * TM];
-
-    const int s = tid >> 5, c = tid & 31;
-    const long q = q0 + (c < w ? c : 0);
-    const int my = (int)(q / a.nx), mx = (int)(q - (long)my * a.nx);
-    const T lam = a.lamx[mx] + a.lamy[my];
-    const T base = a.sigma - a.alpha * lam;
-    const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
-    const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
-    const int k0 = s * m;
-    const int mseg = max(0, min(m, nz - k0));
-    const T* A = sA + k0;
-    const T* Cc = sC + k0;
-    const T* G = sG + k0;
-    const T* O = sO + k0;
-    const T gsc = T(a.scale);
-    const bool lastseg = s == P - 1, firstseg = s == 0;
-    (void)lastseg; (void)firstseg;
-    T* col = tile + k0 * TM + c;
-    const T cprev = s > 0 ? sC[k0 - 1] : T(0);
-    T* c11 = ch;
-    T* c12 = ch + P * TM;
-    T* c21 = ch + 2 * P * TM;
-    T* c22 = ch + 3 * P * TM;
-    T* cin = ch + 4 * P * TM;
-    const int me = s * TM + c;
-#define CT(j) (FULL ? (((j) < MAXM - 1 || !lastseg) ? Cc[j] : T(0)) : ((k0 + (j) < nz - 1) ? Cc[j] : T(0)))
-#define XT(j) (FULL ? (((j) == MAXM - 1 && lastseg) ? etop : T(0)) : ((k0 + (j) == nz - 1) ? etop : T(0)))
-#define AK(j) (FULL ? (((j) > 0 || !firstseg) ? A[j] : T(0)) : ((k0 + (j) > 0) ? A[j] : T(0)))
-#define GW(j) (ADJ ? G[j] : gsc)
-#define INSEG(j) (FULL || (j) < mseg)
-    bool bad = false;
-
-    // A: composite pivot map of the segment
-    {
-        T g11 = T(1), g12 = T(0), g21 = T(0), g22 = T(1);
-        if (s == 0) {
-            T e = base + ebot + (nz == 1 ? etop : T(0));
-#pragma unroll
-            for (int j = 1; j < MAXM; ++j)
-                if (INSEG(j)) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
-            g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
-        } else {
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                if (INSEG(j)) {
-                    const T x = XT(j);
-                    const T cm = j > 0 ? Cc[j - 1] : cprev;
-                    const T am = base + A[j] + x, bm = (base + x) * cm;
-                    const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
-                    const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
-                    g11 = n11; g12 = n12; g21 = n21; g22 = n22;
-                    if ((j & 3) == 3) {
-                        const T nrm = frcp<T>(g11 + g12 + g21 + g22);
-                        g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
-                    }
-                }
-            }
-        }
-        c11[me] = g11; c12[me] = g12; c21[me] = g21; c22[me] = g22;
-    }
-    __syncthreads();
-    if (s == 0) {       // chain: e entering segment t = map_{t-1}(...map_0)
-        T e = T(0);
-        for (int t = 0; t < P; ++t) {
-            const int i = t * TM + c;
-            cin[i] = e;
-            e = (c11[i] * e + c12[i]) * frcp<T>(c21[i] * e + c22[i]);
-        }
-    }
-    __syncthreads();
-    const T e_in = cin[me];
-    // C: pivots (registers) and the affine composite of the forward sweep
-    T inv[MAXM];
-    T al = T(1), be = T(0);
-    {
-        T e;
-        if (k0 == 0) e = base + ebot + (nz == 1 ? etop : T(0));
-        else e = base + A[0] * e_in * frcp<T>(cprev + e_in) + XT(0);
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            if (INSEG(j)) {
-                if (j > 0) e = base + A[j] * e * inv[j - 1] + XT(j);
-                inv[j] = frcp<T>(CT(j) + e);
-                const T ak = AK(j);
-                al = ak * inv[j] * al;
-                be = (col[j * TM] * GW(j) + ak * be) * inv[j];
-                bad |= !(inv[j] > T(0));
-            }
-        }
-    }
-    c11[me] = al;
-    c12[me] = be;
-    __syncthreads();
-    if (s == 0) {
-        T y = T(0);
-        for (int t = 0; t < P; ++t) {
-            const int i = t * TM + c;
-            cin[i] = y;
-            y = c11[i] * y + c12[i];
-        }
-    }
-    __syncthreads();
-    // E: forward sweep writing y, back-substitution composite
-    {
-        T y = cin[me], Q = T(0), R = T(1);
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            if (INSEG(j)) {
-                const T ak = AK(j);
-                y = (col[j * TM] * GW(j) + ak * y) * inv[j];
-                col[j * TM] = y;
-                Q += R * y;
-                R *= CT(j) * inv[j];
-            }
-        }
-        c21[me] = Q;
-        c22[me] = R;
-    }
-    __syncthreads();
-    if (s == 0) {
-        T x = T(0);
-        for (int t = P - 1; t >= 0; --t) {
-            const int i = t * TM + c;
-            cin[i] = x;
-            x = c21[i] + c22[i] * x;
-        }
-    }
-    __syncthreads();
-    // G: back-substitution
-    {
-        T x = cin[me];
-#pragma unroll
-        for (int j = MAXM - 1; j >= 0; --j) {
-            if (INSEG(j)) {
-                x = col[j * TM] + CT(j) * inv[j] * x;
-                col[j * TM] = ADJ ? x * O[j] : x;
-                bad |= !isfinite(x);
-            }
-        }
-    }
-#undef CT
-#undef XT
-#undef AK
-#undef GW
-#undef INSEG
-    if ((sing_tile && c == 0) || c >= w) bad = false;
-    if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
-    __syncthreads();
-    if (sing_tile && tid == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, nz, 0, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0);
-        for (int k = 0; k < nz; ++k)
-            if (!isfinite(tile[k * TM])) {
-                if (a.status) atomicOr(a.status, ST_NONFINITE);
-                break;
-            }
-    }
-    __syncthreads();
-    if (a.bulk) {
-        for (int e = tid; e < nz * CPR; e += nthr) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            if (c0 < w)
-                *reinterpret_cast<float4*>(a.data + (long)k * nmodes + q0 + c0) =
-                    *reinterpret_cast<const float4*>(tile + k * TM + c0);
-        }
-    } else {
-        for (int e = tid; e < nz * TM; e += nthr) {
-            const int k = e / TM, cc = e - k * TM;
-            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[e];
-        }
-    }
-}
-
-template <typename T>
-size_t zsolve_w_smem(int nz, int P) {
-    const int m = (nz + P - 1) / P;
-    return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 6 * (size_t)nz) * sizeof(T);
-}
-
-template <typename T, int MAXM>
-static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
-    const size_t sm = zsolve_w_smem<T>(a.nz, a.P);
-    const bool full = a.nz == a.P * MAXM;
-    auto kern = full ? (a.adjoint ? k_zsolve_w<T, MAXM, true, true> : k_zsolve_w<T, MAXM, true, false>)
-                     : (a.adjoint ? k_zsolve_w<T, MAXM, false, true> : k_zsolve_w<T, MAXM, false, false>);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const long nmodes = (long)a.nx * a.ny;
-    const unsigned grid = (unsigned)((nmodes + 31) / 32);
-    kern<<<grid, 32 * a.P, sm, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
-size_t zsolve_smem(int nz, int tm, int P) {
-    constexpr int CK = 16;
-    const int m = (nz + P - 1) / P;
-    const int nchs = (m + CK - 1) / CK;
-    const size_t segs = (size_t)zseg_stride<T>(m, tm, P);
-    return 16 + (segs * P + (size_t)nchs * tm * P + 6 * (size_t)nz) * sizeof(T);
-}
-
-template <typename T, int P>
-static cudaError_t launch_zsolve_p(const ZArgs<T>& a, cudaStream_t st) {
-    constexpr int CK = 16;
-    const size_t sm = zsolve_smem<T>(a.nz, a.tm, P);
-    auto kern = k_zsolve<T, P, CK>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const long nmodes = (long)a.nx * a.ny;
-    const unsigned grid = (unsigned)((nmodes + a.tm - 1) / a.tm);
-    kern<<<grid, a.tm * P, sm, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_zsolve(const ZArgs<T>& a, cudaStream_t st) {
-    if (a.warp_mode) {
-        switch (a.maxm) {
-            case 16: return launch_zsolve_w<T, 16>(a, st);
-            case 32: return launch_zsolve_w<T, 32>(a, st);
-            case 64: return launch_zsolve_w<T, 64>(a, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    if (a.maxm > 0) {
-        const int key = a.P * 1000 + a.maxm;
-        switch (key) {
-            case 1016: return launch_zsolve_reg<T, 1, 16>(a, st);
-            case 2016: return launch_zsolve_reg<T, 2, 16>(a, st);
-            case 2032: return launch_zsolve_reg<T, 2, 32>(a, st);
-            case 4016: return launch_zsolve_reg<T, 4, 16>(a, st);
-            case 4032: return launch_zsolve_reg<T, 4, 32>(a, st);
-            case 8016: return launch_zsolve_reg<T, 8, 16>(a, st);
-            case 8032: return launch_zsolve_reg<T, 8, 32>(a, st);
-            case 8064: return launch_zsolve_reg<T, 8, 64>(a, st);
-            case 16032: return launch_zsolve_reg<T, 16, 32>(a, st);
-            case 16064: return launch_zsolve_reg<T, 16, 64>(a, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (a.P) {
-        case 1: return launch_zsolve_p<T, 1>(a, st);
-        case 2: return launch_zsolve_p<T, 2>(a, st);
-        case 4: return launch_zsolve_p<T, 4>(a, st);
-        case 8: return launch_zsolve_p<T, 8>(a, st);
-        default: return launch_zsolve_p<T, 16>(a, st);
-    }
-}
-
-template size_t zsolve_w_smem<double>(int, int);
 template size_t zsolve_w_smem<float>(int, int);
-template size_t zsolve_reg_smem<double>(int, int, int);
 template size_t zsolve_reg_smem<float>(int, int, int);
-template size_t zsolve_smem<double>(int, int, int);
 template size_t zsolve_smem<float>(int, int, int);
-template cudaError_t launch_zsolve<double>(const ZArgs<double>&, cudaStream_t);
 template cudaError_t launch_zsolve<float>(const ZArgs<float>&, cudaStream_t);
 
 }  // namespace cales

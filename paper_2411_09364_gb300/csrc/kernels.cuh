@@ -58,6 +58,12 @@ template <typename T> struct ZArgs {
     int* status;         // device status word (bit flags)
     double* cacc;        // singular mode 0: cacc[0] += (weighted mean of the rhs line) * cacc_scale
     double cacc_scale;
+    // Warp-per-segment kernel: the pivot entering segment s of mode q (it
+    // depends on sigma, alpha and the mode only, not on the right-hand side)
+    // at ecache[s * nmodes + q].  ecache_mode 0: computed, not kept; 1:
+    // computed and stored; 2: loaded (the composite-map phase is skipped).
+    T* ecache;
+    int ecache_mode;
 };
 
 // FP64 residual r = f - (c0 u + c1 L u) of the 7-point staggered Laplacian.

@@ -314,8 +314,20 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.status = P->status;
     za.cacc = o.cacc;
     za.cacc_scale = 1.0 / (o.scale * (double)P->nx * (double)P->ny);
+    za.ecache = nullptr;
+    za.ecache_mode = 0;
+    const int zi = sizeof(T) == 8 ? 1 : 0;
+    cales_plan_s::ZCacheKey& zk = P->zkey[zi];
+    if (za.warp_mode && za.P <= 16 && P->zcache[zi]) {
+        za.ecache = reinterpret_cast<T*>(P->zcache[zi]);
+        za.ecache_mode = (zk.valid && zk.P == za.P && zk.maxm == za.maxm && zk.sigma == o.sigma &&
+                          zk.alpha == o.alpha) ? 2 : 1;
+    }
     P->prof_begin(st, "z_solve");
     if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
+    if (za.ecache_mode == 1) {
+        zk.valid = 1; zk.P = za.P; zk.maxm = za.maxm; zk.sigma = o.sigma; zk.alpha = o.alpha;
+    }
     P->prof_end(st);
 
     if (P->ny > 1) {
@@ -453,6 +465,17 @@ void cales_plan_s::fill_resid(cales::ResidArgs& ra, const double* u, const doubl
     ra.fshift = 0.0;
 }
 
+// Segment-entry pivot cache of one precision: 16 slots per mode (the largest
+// segment count of the z kernel).  Left out when the allocation fails.
+static void alloc_zcache(cales_plan_s* P, int zi) {
+    if (P->zcache[zi]) return;
+    const size_t bytes = (size_t)P->nx * P->ny * 16 * (zi ? sizeof(double) : sizeof(float));
+    void* m = nullptr;
+    if (cudaMalloc(&m, bytes) == cudaSuccess) P->zcache[zi] = m;
+    else cudaGetLastError();
+    P->zkey[zi].valid = 0;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -527,6 +550,7 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     }
     P->precision = CALES_FP64;
     P->sweeps = 2;
+    alloc_zcache(P, 1);
     const char* pe = getenv("CALES_PROFILE");
     P->prof_on = pe && pe[0] == '1';
     *out = P;
@@ -543,6 +567,7 @@ int cales_set_precision(cales_plan_t P, int mode, int sweeps) {
     }
     P->precision = mode;
     P->sweeps = sweeps;
+    alloc_zcache(P, mode == CALES_FP64 ? 1 : 0);
     return CALES_OK;
 }
 
@@ -596,6 +621,8 @@ const char* cales_strerror(int code) {
 void cales_destroy(cales_plan_t P) {
     if (!P) return;
     for (void* p : P->owned) cudaFree(p);
+    for (void* z : P->zcache)
+        if (z) cudaFree(z);
     if (P->work) cudaFree(P->work);
     for (int i = 0; i < cales_plan_s::PROF_MAX; ++i) {
         if (P->prof[i].a) { cudaEventDestroy(P->prof[i].a); cudaEventDestroy(P->prof[i].b); }

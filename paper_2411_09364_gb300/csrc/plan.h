@@ -53,6 +53,11 @@ struct cales_plan_s {
     // y tile width, z warps per CTA, z rows per segment bound
     int sched[4] = {0, 0, 0, 0};
     float* work = nullptr;
+    // Segment-entry pivots of the z sweeps (FP32 and FP64 copies, 16 segment
+    // slots per mode) and the (sigma, alpha, P, maxm) they were computed for.
+    struct ZCacheKey { int valid = 0, P = 0, maxm = 0; double sigma = 0.0, alpha = 0.0; };
+    void* zcache[2] = {nullptr, nullptr};
+    ZCacheKey zkey[2];
     std::vector<void*> owned;
     static constexpr int PROF_MAX = 4096;
     bool prof_on = false;

@@ -685,45 +685,51 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
 #define INSEG(j) (FULL || (j) < mseg)
     bool bad = false;
 
-    // A: composite pivot map of the segment
-    {
-        T g11 = T(1), g12 = T(0), g21 = T(0), g22 = T(1);
-        if (s == 0) {
-            T e = base + ebot + (nz == 1 ? etop : T(0));
-#pragma unroll
-            for (int j = 1; j < MAXM; ++j)
-                if (INSEG(j)) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
-            g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
-        } else {
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                if (INSEG(j)) {
-                    const T x = XT(j);
-                    const T cm = j > 0 ? Cc[j - 1] : cprev;
-                    const T am = base + A[j] + x, bm = (base + x) * cm;
-                    const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
-                    const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
-                    g11 = n11; g12 = n12; g21 = n21; g22 = n22;
-                    if ((j & 3) == 3) {
-                        const T nrm = frcp<T>(g11 + g12 + g21 + g22);
-                        g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
+    T e_in;
+    if (a.ecache_mode == 2) {
+        e_in = s > 0 ? a.ecache[(long)s * nmodes + q] : T(0);
+    } else {
+        // A: composite pivot map of the segment
+        {
+            T g11 = T(1), g12 = T(0), g21 = T(0), g22 = T(1);
+            if (s == 0) {
+                T e = base + ebot + (nz == 1 ? etop : T(0));
+    #pragma unroll
+                for (int j = 1; j < MAXM; ++j)
+                    if (INSEG(j)) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
+                g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
+            } else {
+    #pragma unroll
+                for (int j = 0; j < MAXM; ++j) {
+                    if (INSEG(j)) {
+                        const T x = XT(j);
+                        const T cm = j > 0 ? Cc[j - 1] : cprev;
+                        const T am = base + A[j] + x, bm = (base + x) * cm;
+                        const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
+                        const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
+                        g11 = n11; g12 = n12; g21 = n21; g22 = n22;
+                        if ((j & 3) == 3) {
+                            const T nrm = frcp<T>(g11 + g12 + g21 + g22);
+                            g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
+                        }
                     }
                 }
             }
+            c11[me] = g11; c12[me] = g12; c21[me] = g21; c22[me] = g22;
         }
-        c11[me] = g11; c12[me] = g12; c21[me] = g21; c22[me] = g22;
-    }
-    __syncthreads();
-    if (s == 0) {       // chain: e entering segment t = map_{t-1}(...map_0)
-        T e = T(0);
-        for (int t = 0; t < P; ++t) {
-            const int i = t * TM + c;
-            cin[i] = e;
-            e = (c11[i] * e + c12[i]) * frcp<T>(c21[i] * e + c22[i]);
+        __syncthreads();
+        if (s == 0) {       // chain: e entering segment t = map_{t-1}(...map_0)
+            T e = T(0);
+            for (int t = 0; t < P; ++t) {
+                const int i = t * TM + c;
+                cin[i] = e;
+                e = (c11[i] * e + c12[i]) * frcp<T>(c21[i] * e + c22[i]);
+            }
         }
+        __syncthreads();
+        e_in = cin[me];
+        if (a.ecache_mode == 1 && s > 0 && c < w) a.ecache[(long)s * nmodes + q] = e_in;
     }
-    __syncthreads();
-    const T e_in = cin[me];
     // C: pivots (registers) and the affine composite of the forward sweep
     T inv[MAXM];
     T al = T(1), be = T(0);

@@ -99,6 +99,27 @@ def test_fp32_and_refinement(cuda_device, bc, alpha):
     assert O.rel_l2(solve_gpu(plan, f, alpha), ref) <= TOL[cs.FP32_REFINE]
 
 
+@pytest.mark.parametrize("precision", [cs.FP64, cs.FP32, cs.FP32_REFINE])
+def test_pivot_cache_follows_the_operator(cuda_device, precision):
+    """The z sweeps keep the segment-entry pivots of the last (sigma, alpha):
+    a sequence of solves with changing operators on one plan matches fresh
+    plans bit for bit, and the oracle to the precision's tolerance."""
+    nx, ny, nz = 64, 32, 300          # 300 rows: several z segments per mode
+    bc = (0, 0, 1, 1, 1, 1)
+    g, plan = pair(nx, ny, nz, bc, beta=1.8, precision=precision)
+    f = S.gaussian(31, (nz, ny, nx))
+    for alpha in (1e-3, 2e-4, None, 1e-3, None):
+        got = solve_gpu(plan, f, alpha)
+        _, fresh = pair(nx, ny, nz, bc, beta=1.8, precision=precision)
+        want = solve_gpu(fresh, f, alpha)
+        if alpha is None and precision == cs.FP32_REFINE:
+            # singular Poisson: the refinement's gauge sum is an atomic FP64 reduction
+            assert O.rel_l2(got, want) <= 1e-13, alpha
+        else:
+            assert np.array_equal(got, want), alpha
+        assert O.rel_l2(got, O.solve(f, g, alpha)) <= TOL[precision], alpha
+
+
 def test_in_place(cuda_device):
     g, plan = pair(48, 24, 20, (0, 0, 1, 1, 1, 1))
     f = S.gaussian(3, (20, 24, 48))

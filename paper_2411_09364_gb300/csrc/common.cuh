@@ -49,7 +49,12 @@ template <typename T> struct DirTab {
     unsigned nbmag[MAX_RADICES];   // fast-division magic of L / R_p
     unsigned nsmag[MAX_RADICES];   // fast-division magic of Ns_p
     unsigned nmag, l1mag, lmag, hmag;   // magics of n, L + 1, L and L/2 + 1
-    const cpx<T>* tw;     // W_L^t = exp(-2 pi i t / L), t in [0, L)
+    int twoff[MAX_RADICES];        // offset of pass p's twiddle block in tw
+    int twlen;                     // total twiddle entries
+    // Per-pass twiddles: pass p (Ns > 1) holds W_L^(r k tstep) at
+    // tw[twoff[p] + (r - 1) Ns + k], r = 1..R-1, k = 0..Ns-1, so the threads
+    // of a pass read consecutive entries (no shared-memory bank conflicts).
+    const cpx<T>* tw;
     const cpx<T>* post;   // W_n^m = exp(-2 pi i m / n), m in [0, L]
     const cpx<T>* mak;    // exp(-i pi m / (2n)),        m in [0, L]
 };
@@ -228,7 +233,7 @@ template <bool ON> __device__ __forceinline__ int swz(int i) {
 // LS > 0: the line length L = LS is a compile-time constant (n = 2 LS), and
 // so are the pass sizes (NSS = Ns of this pass); KS >= 0: compile-time kind.
 // Then every index division folds to constants and shifts.
-template <typename T, int R, bool INV, int TXC, int IO, int LS = 0, int NSS = 0, int KS = -1>
+template <typename T, int R, bool INV, int TXC, int IO, int LS = 0, int NSS = 0, int KS = -1, int TWO = 0>
 __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
                                               const DirTab<T>& t, int p, int nlines, int ls, int es,
                                               const cpx<T>* __restrict__ tw, const NatIO<T>& nat) {
@@ -237,7 +242,7 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
     constexpr int nbS = LS ? LS / R : 1;
     const int nb = LS ? nbS : t.L / R;
     const int Ns = LS ? NSS : t.nsv[p];
-    const int tstep = LS ? LS / (NSS * R) : t.tstep[p];
+    const cpx<T>* __restrict__ tp = tw + (LS ? TWO : t.twoff[p]);
     const int total = nb * (TXC > 0 ? TXC : nlines);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int line, j, k;
@@ -268,10 +273,9 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
             for (int r = 0; r < R; ++r) v[r] = src[swz<(IO & 4) != 0>(s0 + r * sst)];
         }
         if (LS ? (NSS > 1) : (Ns > 1)) {
-            const int ks = k * tstep;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const cpx<T> w = tw[r * ks];
+                const cpx<T> w = tp[(r - 1) * Ns + k];
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
@@ -328,6 +332,15 @@ constexpr int sf_nrad(int L) {
     while (sf_radix(L, p) != 0) ++p;
     return p;
 }
+// offset of pass P's twiddle block (passes with Ns > 1 hold (R - 1) Ns entries)
+constexpr int sf_twoff(int L, int P) {
+    int off = 0, ns = 1;
+    for (int q = 0; q < P; ++q) {
+        if (ns > 1) off += (sf_radix(L, q) - 1) * ns;
+        ns *= sf_radix(L, q);
+    }
+    return off;
+}
 
 // The passes of a compile-time length LS (pass P, sub-transform size NS).
 template <typename T, bool INV, int TXC, int LN, int SN, int LS, int KS, int P, int NS>
@@ -339,7 +352,7 @@ struct StaticPasses {
         constexpr bool first = P == 0, last = P == NR - 1;
         constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
         constexpr int IO = (first ? LN : 0) | (last ? SN : 0) | (first ? 0 : 4 * SW) | (last ? 0 : 8 * SW);
-        stockham_pass<T, R, INV, TXC, IO, LS, NS, KS>(src, dst, t, P, nlines, ls, es, tw, nat);
+        stockham_pass<T, R, INV, TXC, IO, LS, NS, KS, sf_twoff(LS, P)>(src, dst, t, P, nlines, ls, es, tw, nat);
         __syncthreads();
         if constexpr (last) return dst;
         else return StaticPasses<T, INV, TXC, LN, SN, LS, KS, P + 1, NS * R>::run(dst, src, t, nlines, ls, es, tw, nat);
@@ -351,7 +364,7 @@ struct StaticPasses {
 // nat.out and the return is unused).  LOAD_NAT: the first pass packs the real
 // natural input itself (b0 unused as input); STORE_NAT: the last pass unpacks
 // into the real natural output.  `tw` is the twiddle table W_L^t staged in
-// shared memory by the caller.
+// shared memory by the caller (per-pass layout of DirTab::tw).
 template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT, int LS = 0, int KS = -1>
 __device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
                              const cpx<T>* tw, const NatIO<T>& nat) {

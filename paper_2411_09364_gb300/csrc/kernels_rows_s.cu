@@ -23,7 +23,7 @@ static cudaError_t rows_inv_l(const RowArgs<float>& a, int mode, cudaStream_t st
 }
 
 bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream_t st, cudaError_t* err) {
-    if (!static_fft_enabled() || a.t.kind != KIND_P) return false;
+    if (!static_fft_enabled() || a.t.kind != KIND_P || !radices_match(a.t, a.t.L)) return false;
     switch (a.t.L) {
         case 128: *err = rows_fwd_l<128>(a, in_f64, st); return true;
         case 256: *err = rows_fwd_l<256>(a, in_f64, st); return true;
@@ -33,7 +33,8 @@ bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream
 }
 
 bool launch_rows_inverse_static(const RowArgs<float>& a, int mode, cudaStream_t st, cudaError_t* err) {
-    if (!static_fft_enabled() || a.t.kind != KIND_P || mode < OUT_T || mode > OUT_FF_FINAL) return false;
+    if (!static_fft_enabled() || a.t.kind != KIND_P || mode < OUT_T || mode > OUT_FF_FINAL || !radices_match(a.t, a.t.L))
+        return false;
     switch (a.t.L) {
         case 128: *err = rows_inv_l<128>(a, mode, st); return true;
         case 256: *err = rows_inv_l<256>(a, mode, st); return true;

@@ -50,13 +50,9 @@ bool factorize(int L, int* radix, int& nrad) {
     int m = L;
     int twos = 0;
     while (m % 2 == 0) { m /= 2; ++twos; }
-    // radix 16 first (fewer shared-memory passes), CALES_MAXRADIX=8 keeps the
-    // radix-8 factorisation
-    static const int maxr = [] {
-        const char* e = getenv("CALES_MAXRADIX");
-        return (e && atoi(e) == 8) ? 8 : 16;
-    }();
-    while (maxr == 16 && twos >= 4) { radix[nrad++] = 16; twos -= 4; }
+    // radix 16 first (fewer shared-memory passes); the compile-time-size
+    // kernels use the same order (sf_radix)
+    while (twos >= 4) { radix[nrad++] = 16; twos -= 4; }
     while (twos >= 3) { radix[nrad++] = 8; twos -= 3; }
     if (twos == 2) radix[nrad++] = 4;
     if (twos == 1) radix[nrad++] = 2;
@@ -80,12 +76,26 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
     d.L = n >= 2 ? n / 2 : 1;
     if (!factorize(d.L, d.radix, d.nrad)) return CALES_EUNSUPPORTED;
     const int L = d.L;
-    std::vector<double2> tw(L), post(L + 1), mak(L + 1);
-    std::vector<float2> twf(L), postf(L + 1), makf(L + 1);
-    for (int t = 0; t < L; ++t) {
-        double c, s;
-        cis_frac(t, L, c, s);
-        tw[t] = make_double2(c, -s);
+    // per-pass twiddles W_L^(r k tstep) at twoff[p] + (r - 1) Ns + k
+    std::vector<double2> tw, post(L + 1), mak(L + 1);
+    std::vector<float2> twf, postf(L + 1), makf(L + 1);
+    {
+        int ns = 1;
+        for (int p = 0; p < d.nrad; ++p) {
+            const int R = d.radix[p], tstep = L / (ns * R);
+            d.twoff[p] = (int)tw.size();
+            if (ns > 1)
+                for (int r = 1; r < R; ++r)
+                    for (int k = 0; k < ns; ++k) {
+                        double c, s;
+                        cis_frac((int)(((long long)r * k * tstep) % L), L, c, s);
+                        tw.push_back(make_double2(c, -s));
+                    }
+            ns *= R;
+        }
+        d.twlen = (int)tw.size();
+        if (tw.empty()) tw.push_back(make_double2(1.0, 0.0));
+        twf.resize(tw.size());
     }
     for (int m = 0; m <= L; ++m) {
         double c, s;
@@ -110,7 +120,7 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
         lam[q] = -(4.0 / (h * h)) * sv * sv;
         lamf[q] = (float)lam[q];
     }
-    for (int i = 0; i < L; ++i) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+    for (size_t i = 0; i < tw.size(); ++i) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
     for (int i = 0; i <= L; ++i) {
         postf[i] = make_float2((float)post[i].x, (float)post[i].y);
         makf[i] = make_float2((float)mak[i].x, (float)mak[i].y);
@@ -140,8 +150,10 @@ template <> DirTab<double> DirHost::tab<double>() const {
         t.tstep[i] = i < nrad ? L / (ns * radix[i]) : 1;
         t.nbmag[i] = i < nrad ? div_magic((unsigned)(L / radix[i])) : 0u;
         t.nsmag[i] = div_magic((unsigned)ns);
+        t.twoff[i] = twoff[i];
         if (i < nrad) ns *= radix[i];
     }
+    t.twlen = twlen;
     t.nmag = div_magic((unsigned)n);
     t.l1mag = div_magic((unsigned)(L + 1));
     t.lmag = div_magic((unsigned)L);
@@ -162,8 +174,10 @@ template <> DirTab<float> DirHost::tab<float>() const {
         t.tstep[i] = i < nrad ? L / (ns * radix[i]) : 1;
         t.nbmag[i] = i < nrad ? div_magic((unsigned)(L / radix[i])) : 0u;
         t.nsmag[i] = div_magic((unsigned)ns);
+        t.twoff[i] = twoff[i];
         if (i < nrad) ns *= radix[i];
     }
+    t.twlen = twlen;
     t.nmag = div_magic((unsigned)n);
     t.l1mag = div_magic((unsigned)(L + 1));
     t.lmag = div_magic((unsigned)L);

@@ -9,6 +9,8 @@
 struct DirHost {
     int n = 1, kind = 0, L = 1, nrad = 0;
     int radix[cales::MAX_RADICES] = {0};
+    int twoff[cales::MAX_RADICES] = {0};
+    int twlen = 0;
     double2* tw_d = nullptr;
     double2* post_d = nullptr;
     double2* mak_d = nullptr;

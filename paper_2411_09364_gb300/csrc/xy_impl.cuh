@@ -23,41 +23,42 @@ template <int D> __device__ __forceinline__ int sdiv(int x, unsigned mag) {
     return D > 0 ? (int)((unsigned)x / (unsigned)(D > 0 ? D : 1)) : (int)fdivu((unsigned)x, mag);
 }
 
-// Number of table entries staged in shared memory: twiddles W_L^t (L), the
-// post-processing factors W_n^m (L + 1) and, for the cosine and sine kinds,
-// exp(-i pi m/(2n)) (L + 1).
-__host__ __device__ __forceinline__ int table_len(int L, int kind) {
-    return 2 * L + 1 + (kind != KIND_P ? L + 1 : 0);
+// Number of table entries staged in shared memory: the per-pass twiddles
+// (twlen), the post-processing factors W_n^m (L + 1) and, for the cosine and
+// sine kinds, exp(-i pi m/(2n)) (L + 1).
+__host__ __device__ __forceinline__ int table_len(int twlen, int L, int kind) {
+    return twlen + L + 1 + (kind != KIND_P ? L + 1 : 0);
 }
 
 // Shared-memory layout of the row kernels: [mbarrier 16 B | b0 | b1 | tw | extra];
 // b0 and b1 hold a multiple of 16 complex elements (swizzle blocks).
 template <typename T> struct RowLayout {
     size_t b0, b1, tw, extra, total;
-    __host__ __device__ RowLayout(int rpc, int L, int n, int kind, size_t extra_per_elem) {
+    __host__ __device__ RowLayout(int rpc, int L, int n, int kind, int twlen, size_t extra_per_elem) {
         const size_t C = sizeof(cpx<T>);
         const size_t nel = ((size_t)rpc * L + 15) & ~size_t(15);
         b0 = 16;
         b1 = al16(b0 + nel * C);
         tw = al16(b1 + nel * C);
-        extra = al16(tw + (size_t)table_len(L, kind) * C);
+        extra = al16(tw + (size_t)table_len(twlen, L, kind) * C);
         total = al16(extra + (size_t)rpc * n * extra_per_elem);
     }
 };
 
-// Twiddles W_L^t (L), then the post-processing tables W_n^m and (cosine and
-// sine kinds) exp(-i pi m/(2n)) (L + 1 each), staged contiguously in shared memory.
+// The per-pass twiddles (twlen), then the post-processing tables W_n^m and
+// (cosine and sine kinds) exp(-i pi m/(2n)) (L + 1 each), staged
+// contiguously in shared memory.
 template <typename T>
 __device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t) {
-    const int L = t.L;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw_s[i] = t.tw[i];
+    const int L = t.L, tl = t.twlen;
+    for (int i = threadIdx.x; i < tl; i += blockDim.x) tw_s[i] = t.tw[i];
     if (t.kind != KIND_P) {
         for (int i = threadIdx.x; i <= L; i += blockDim.x) {
-            tw_s[L + i] = t.post[i];
-            tw_s[2 * L + 1 + i] = t.mak[i];
+            tw_s[tl + i] = t.post[i];
+            tw_s[tl + L + 1 + i] = t.mak[i];
         }
     } else {
-        for (int i = threadIdx.x; i <= L; i += blockDim.x) tw_s[L + i] = t.post[i];
+        for (int i = threadIdx.x; i <= L; i += blockDim.x) tw_s[tl + i] = t.post[i];
     }
 }
 
@@ -81,15 +82,15 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
     // natural rows land in b0 (same type) or in the extra area (FP64 input)
     TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b0) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
+    const cpx<T>* pst = tw_s + t.twlen;
+    const cpx<T>* mkt = tw_s + t.twlen + L + 1;
     const int tot = nr * n;
     if (a.bulk) {
         if (tid == 0) {
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         }
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, kind, MODE != OUT_T ? 8 : 0);
+    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, MODE != OUT_T ? 8 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
@@ -222,8 +223,8 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         stage_twiddles(tw_s, t);
         __syncthreads();
     }
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
+    const cpx<T>* pst = tw_s + t.twlen;
+    const cpx<T>* mkt = tw_s + t.twlen + L + 1;
     const int half = L / 2 + 1;
     const int npre = nr * half;
     for (int idx = tid; idx < npre; idx += blockDim.x) {
@@ -280,8 +281,8 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
 // tile moves by 16-byte cp.async copies (all in flight), else by plain loads.
 // Shared memory: [16 B | b0 | b1 | tw].
 // ---------------------------------------------------------------------------
-template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L, int kind) {
-    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)table_len(L, kind) * sizeof(cpx<T>);
+template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX, int L, int kind, int twlen) {
+    return al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)) + (size_t)table_len(twlen, L, kind) * sizeof(cpx<T>);
 }
 
 template <typename T, int TX, bool INV, int LS = 0, int KS = -1>
@@ -303,8 +304,8 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + al16(16 + 2 * (size_t)TX * L * sizeof(cpx<T>)));
     const int tot = n * TX;
     T* nat = reinterpret_cast<T*>(b0);                 // natural-order tile [ny][TX]
-    const cpx<T>* pst = tw_s + L;
-    const cpx<T>* mkt = tw_s + 2 * L + 1;
+    const cpx<T>* pst = tw_s + t.twlen;
+    const cpx<T>* mkt = tw_s + t.twlen + L + 1;
     constexpr int EPC = 16 / (int)sizeof(T);
     constexpr int CPR = TX / EPC > 0 ? TX / EPC : 1;
     if (a.bulk) {
@@ -382,12 +383,20 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     }
 }
 
+// The compile-time-size kernels assume the plan factorised L as sf_radix does.
+template <typename T> inline bool radices_match(const DirTab<T>& t, int L) {
+    if (t.L != L || t.nrad != sf_nrad(L)) return false;
+    for (int p = 0; p < t.nrad; ++p)
+        if (t.radix[p] != sf_radix(L, p)) return false;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // launchers of one variant
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn, int LS, int KS>
 cudaError_t launch_rows_forward_v(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
     auto kern = k_rows_forward<T, TIn, LS, KS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -397,7 +406,7 @@ cudaError_t launch_rows_forward_v(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int MODE, int LS, int KS>
 cudaError_t launch_rows_inverse_v(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, MODE != OUT_T ? 8 : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, MODE != OUT_T ? 8 : 0);
     auto kern = k_rows_inverse<T, MODE, LS, KS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);
@@ -407,7 +416,7 @@ cudaError_t launch_rows_inverse_v(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int TX, int LS, int KS>
 cudaError_t launch_cols_v(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
-    const size_t sm = col_smem<T>(TX, a.t.L, a.t.kind);
+    const size_t sm = col_smem<T>(TX, a.t.L, a.t.kind, a.t.twlen);
     const unsigned grid = (unsigned)(a.nplanes * ((a.nx + TX - 1) / TX));
     auto kern = inverse ? k_cols<T, TX, true, LS, KS> : k_cols<T, TX, false, LS, KS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -602,12 +602,14 @@ static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
 // once) and vector stores.  Segment states are chained by warp 0 through
 // shared memory.  Pivot reciprocals of a segment stay in registers.
 // ---------------------------------------------------------------------------
+template <typename T> struct alignas(2 * sizeof(T)) ZPair { T a, c; };
+
 // FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
 // predicates and the first/last-row conditions reduce to compile-time tests
 // on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
 // transposed) instead of the uniform forward scale.
 template <typename T, int MAXM, bool FULL, bool ADJ>
-__global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TM = 32;
     constexpr int EPC = 16 / (int)sizeof(T);          // elements per 16-byte chunk
@@ -625,6 +627,9 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     T* sO = sG + nz;
     T* save0 = sO + nz;
     T* r0 = save0 + nz;
+    // (A_k, C_k) pairs with A_0 = 0 and C_{nz-1} = 0: one 8-byte (FP32) or
+    // 16-byte (FP64) load per row and no first/last-row tests
+    ZPair<T>* sAC = reinterpret_cast<ZPair<T>*>(r0 + nz);
     const long q0 = (long)blockIdx.x * TM;
     const int w = (int)min((long)TM, nmodes - q0);
     const int tid = threadIdx.x;
@@ -632,6 +637,10 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     for (int k = tid; k < nz; k += nthr) {
         sA[k] = a.alpha * a.za[k];
         sC[k] = a.alpha * a.zc[k];
+        ZPair<T> pr;
+        pr.a = k > 0 ? sA[k] : T(0);
+        pr.c = k < nz - 1 ? sC[k] : T(0);
+        sAC[k] = pr;
         double gs = double(a.scale), os = 1.0;
         if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
         sG[k] = T(gs);
@@ -663,24 +672,20 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
     const int k0 = s * m;
     const int mseg = max(0, min(m, nz - k0));
-    const T* A = sA + k0;
-    const T* Cc = sC + k0;
+    const ZPair<T>* AC = sAC + k0;
     const T* G = sG + k0;
     const T* O = sO + k0;
     const T gsc = T(a.scale);
     const bool lastseg = s == P - 1, firstseg = s == 0;
     (void)lastseg; (void)firstseg;
     T* col = tile + k0 * TM + c;
-    const T cprev = s > 0 ? sC[k0 - 1] : T(0);
     T* c11 = ch;
     T* c12 = ch + P * TM;
     T* c21 = ch + 2 * P * TM;
     T* c22 = ch + 3 * P * TM;
     T* cin = ch + 4 * P * TM;
     const int me = s * TM + c;
-#define CT(j) (FULL ? (((j) < MAXM - 1 || !lastseg) ? Cc[j] : T(0)) : ((k0 + (j) < nz - 1) ? Cc[j] : T(0)))
 #define XT(j) (FULL ? (((j) == MAXM - 1 && lastseg) ? etop : T(0)) : ((k0 + (j) == nz - 1) ? etop : T(0)))
-#define AK(j) (FULL ? (((j) > 0 || !firstseg) ? A[j] : T(0)) : ((k0 + (j) > 0) ? A[j] : T(0)))
 #define GW(j) (ADJ ? G[j] : gsc)
 #define INSEG(j) (FULL || (j) < mseg)
     bool bad = false;
@@ -696,15 +701,15 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
                 T e = base + ebot + (nz == 1 ? etop : T(0));
     #pragma unroll
                 for (int j = 1; j < MAXM; ++j)
-                    if (INSEG(j)) e = base + A[j] * e * frcp<T>(CT(j - 1) + e) + XT(j);
+                    if (INSEG(j)) e = base + AC[j].a * e * frcp<T>(AC[j - 1].c + e) + XT(j);
                 g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
             } else {
     #pragma unroll
                 for (int j = 0; j < MAXM; ++j) {
                     if (INSEG(j)) {
                         const T x = XT(j);
-                        const T cm = j > 0 ? Cc[j - 1] : cprev;
-                        const T am = base + A[j] + x, bm = (base + x) * cm;
+                        const T cm = AC[j - 1].c;              // k0 + j - 1 >= 0 for s > 0
+                        const T am = base + AC[j].a + x, bm = (base + x) * cm;
                         const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
                         const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
                         g11 = n11; g12 = n12; g21 = n21; g22 = n22;
@@ -736,15 +741,15 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     {
         T e;
         if (k0 == 0) e = base + ebot + (nz == 1 ? etop : T(0));
-        else e = base + A[0] * e_in * frcp<T>(cprev + e_in) + XT(0);
+        else e = base + AC[0].a * e_in * frcp<T>(AC[-1].c + e_in) + XT(0);
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
             if (INSEG(j)) {
-                if (j > 0) e = base + A[j] * e * inv[j - 1] + XT(j);
-                inv[j] = frcp<T>(CT(j) + e);
-                const T ak = AK(j);
-                al = ak * inv[j] * al;
-                be = (col[j * TM] * GW(j) + ak * be) * inv[j];
+                const ZPair<T> ac = AC[j];
+                if (j > 0) e = base + ac.a * e * inv[j - 1] + XT(j);
+                inv[j] = frcp<T>(ac.c + e);
+                al = ac.a * inv[j] * al;
+                be = (col[j * TM] * GW(j) + ac.a * be) * inv[j];
                 bad |= !(inv[j] > T(0));
             }
         }
@@ -767,11 +772,11 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
             if (INSEG(j)) {
-                const T ak = AK(j);
-                y = (col[j * TM] * GW(j) + ak * y) * inv[j];
+                const ZPair<T> ac = AC[j];
+                y = (col[j * TM] * GW(j) + ac.a * y) * inv[j];
                 col[j * TM] = y;
                 Q += R * y;
-                R *= CT(j) * inv[j];
+                R *= ac.c * inv[j];
             }
         }
         c21[me] = Q;
@@ -789,19 +794,18 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
     __syncthreads();
     // G: back-substitution
     {
-        T x = cin[me];
+        T x = cin[me], xs = T(0);
 #pragma unroll
         for (int j = MAXM - 1; j >= 0; --j) {
             if (INSEG(j)) {
-                x = col[j * TM] + CT(j) * inv[j] * x;
+                x = col[j * TM] + AC[j].c * inv[j] * x;
                 col[j * TM] = ADJ ? x * O[j] : x;
-                bad |= !isfinite(x);
+                xs += x;
             }
         }
+        bad |= !isfinite(xs);
     }
-#undef CT
 #undef XT
-#undef AK
 #undef GW
 #undef INSEG
     if ((sing_tile && c == 0) || c >= w) bad = false;
@@ -835,7 +839,7 @@ __global__ void __launch_bounds__(512) k_zsolve_w(ZArgs<T> a) {
 template <typename T>
 size_t zsolve_w_smem(int nz, int P) {
     const int m = (nz + P - 1) / P;
-    return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 6 * (size_t)nz) * sizeof(T);
+    return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 8 * (size_t)nz) * sizeof(T);
 }
 
 template <typename T, int MAXM>

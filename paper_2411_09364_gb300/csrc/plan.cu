@@ -353,7 +353,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     RowArgs<T> ri = ra;
     ri.in = work;
     ri.out = out;
-    ri.rpc = rows_per_cta<T>(P->nx, MODE != OUT_T ? 8 : 0, P->sched[0]);
+    ri.rpc = rows_per_cta<T>(P->nx, 0, P->sched[0]);
     ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
                ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
     ri.shift_acc = o.shift_acc;

@@ -190,22 +190,24 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         }
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, MODE != OUT_T ? 8 : 0);
+    // Shared memory holds the spectra and the FFT buffers only; the 8-byte
+    // results (FP64 or double-float pairs) are read-modified-written in
+    // global memory by coalesced accesses, the pairs to update having been
+    // prefetched into L2 at the start so they arrive during the FFT.
+    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
-    unsigned char* o8 = smem_raw + lay.extra;
     T* x0 = reinterpret_cast<T*>(b0);
     constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL;
     if (a.bulk) {
         if (tid == 0) {
+            if (LOAD_OUT) bulk_prefetch_l2(outp, (uint32_t)(tot * 8));
             mbar_init(bar, 1);
             const uint32_t b_in = (uint32_t)(tot * sizeof(T));
-            const uint32_t b_out = LOAD_OUT ? (uint32_t)(tot * 8) : 0u;
-            mbar_expect_tx(bar, b_in + b_out);
+            mbar_expect_tx(bar, b_in);
             bulk_g2s(x0, in, b_in, bar);
-            if (LOAD_OUT) bulk_g2s(o8, outp, b_out, bar);
         }
         stage_twiddles(tw_s, t);
         __syncthreads();
@@ -217,9 +219,6 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         }
     } else {
         for (int e = tid; e < tot; e += blockDim.x) x0[e] = in[e];
-        if (LOAD_OUT)
-            for (int e = tid; e < tot; e += blockDim.x)
-                reinterpret_cast<float2*>(o8)[e] = reinterpret_cast<const float2*>(outp)[e];
         stage_twiddles(tw_s, t);
         __syncthreads();
     }
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         pre_inverse_pair<T, LS, KS>(x0 + r * n, 1, b1 + r * L, 1, t, pst, mkt, m);
     }
     __syncthreads();
-    unsigned char* ob;
+    T* ob;
     if (nrad > 0) {
         // the last pass unpacks straight into natural order (real rows); a
         // periodic row's packed pairs already are its natural order
@@ -240,39 +239,33 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         const NatIO<T> nat{nullptr, natout, n, 1};
         if (kind == KIND_P) fft_lines<T, true, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
         else fft_lines<T, true, 0, false, true, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
-        if (MODE == OUT_T) {
-            ob = reinterpret_cast<unsigned char*>(natout);
-        } else {
-            ob = o8;
-            for (int e = tid; e < tot; e += blockDim.x) store8<T, MODE>(ob + (long)e * 8, natout[e], shift);
+        if (MODE != OUT_T) {
+            for (int e = tid; e < tot; e += blockDim.x) store8<T, MODE>(outp + (long)e * 8, natout[e], shift);
+            return;
         }
+        ob = natout;
     } else {
         const T* zr = reinterpret_cast<const T*>(b1);
-        T* tmp = reinterpret_cast<T*>(b0);
-        ob = MODE == OUT_T ? reinterpret_cast<unsigned char*>(tmp) : o8;
+        ob = reinterpret_cast<T*>(b0);
         for (int e = tid; e < tot; e += blockDim.x) {
             const int r = sdiv<LS ? 2 * LS : 0>(e, t.nmag), s2 = e - r * n;
             const T v = zr[r * n + pack_index(kind, n, s2)] * pack_sign<T>(kind, s2);
-            if (MODE == OUT_T) tmp[e] = v;
-            else store8<T, MODE>(ob + (long)e * 8, v, shift);
+            if (MODE == OUT_T) ob[e] = v;
+            else store8<T, MODE>(outp + (long)e * 8, v, shift);
         }
+        if (MODE != OUT_T) return;
     }
     if (a.bulk) {
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
-            bulk_s2g(outp, ob, (uint32_t)(tot * OSZ));
+            bulk_s2g(outp, ob, (uint32_t)(tot * sizeof(T)));
             bulk_commit();
             bulk_wait_read_all();
         }
     } else {
         __syncthreads();
-        if (MODE == OUT_T) {
-            for (int e = tid; e < tot; e += blockDim.x) reinterpret_cast<T*>(outp)[e] = reinterpret_cast<const T*>(ob)[e];
-        } else {
-            for (int e = tid; e < tot; e += blockDim.x)
-                reinterpret_cast<double*>(outp)[e] = reinterpret_cast<const double*>(ob)[e];
-        }
+        for (int e = tid; e < tot; e += blockDim.x) reinterpret_cast<T*>(outp)[e] = ob[e];
     }
 }
 
@@ -406,7 +399,7 @@ cudaError_t launch_rows_forward_v(const RowArgs<T>& a, cudaStream_t st) {
 
 template <typename T, int MODE, int LS, int KS>
 cudaError_t launch_rows_inverse_v(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, MODE != OUT_T ? 8 : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, 0);
     auto kern = k_rows_inverse<T, MODE, LS, KS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);

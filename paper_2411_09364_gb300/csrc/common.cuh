@@ -195,11 +195,16 @@ __device__ __forceinline__ int unpack_src(int kind, int n, int d) {
 }
 
 // Real natural-order lines: element s of line l at base[l * nls + s * nes].
+// in64: FP64 input lines read from global memory and truncated to T (IO bit
+// 16 of a first pass), for the FP32 solve of an FP64 right-hand side.
 template <typename T> struct NatIO {
     const T* in;
     T* out;
     int nls, nes;
+    const double* in64;
 };
+
+__device__ __forceinline__ float trunc_double_int(double d);
 
 // ---------------------------------------------------------------------------
 // One Stockham autosort pass of radix R over a set of lines in shared memory
@@ -229,7 +234,8 @@ template <bool ON> __device__ __forceinline__ int swz(int i) {
 }
 
 // IO bits: 1 = first pass packs the real natural input, 2 = last pass unpacks
-// into the real natural output, 4 = source swizzled, 8 = destination swizzled.
+// into the real natural output, 4 = source swizzled, 8 = destination swizzled,
+// 16 = the natural input is FP64 in global memory (NatIO::in64).
 // LS > 0: the line length L = LS is a compile-time constant (n = 2 LS), and
 // so are the pass sizes (NSS = Ns of this pass); KS >= 0: compile-time kind.
 // Then every index division folds to constants and shifts.
@@ -259,7 +265,24 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
         if (LS) k = (int)((unsigned)j % (unsigned)(NSS > 0 ? NSS : 1));
         else k = j - (int)fdivu((unsigned)j, t.nsmag[p]) * Ns;
         cpx<T> v[R];
-        if (IO & 1) {
+        if ((IO & 16) && (IO & 1)) {
+            const double* xin = nat.in64 + line * nat.nls;
+            if (kind == KIND_P && nat.nes == 1) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const double2 d = *reinterpret_cast<const double2*>(xin + 2 * (j + r * nb));
+                    v[r] = mk(T(trunc_double_int(d.x)), T(trunc_double_int(d.y)));
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int q = j + r * nb;
+                    const int s0 = unpack_src(kind, n, 2 * q), s1 = unpack_src(kind, n, 2 * q + 1);
+                    v[r] = mk(T(trunc_double_int(xin[s0 * nat.nes])) * pack_sign<T>(kind, s0),
+                              T(trunc_double_int(xin[s1 * nat.nes])) * pack_sign<T>(kind, s1));
+                }
+            }
+        } else if (IO & 1) {
             const T* xin = nat.in + line * nat.nls;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -365,10 +388,10 @@ struct StaticPasses {
 // natural input itself (b0 unused as input); STORE_NAT: the last pass unpacks
 // into the real natural output.  `tw` is the twiddle table W_L^t staged in
 // shared memory by the caller (per-pass layout of DirTab::tw).
-template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT, int LS = 0, int KS = -1>
+template <typename T, bool INV, int TXC, bool LOAD_NAT, bool STORE_NAT, int LS = 0, int KS = -1, bool IN64 = false>
 __device__ cpx<T>* fft_lines(cpx<T>* b0, cpx<T>* b1, const DirTab<T>& t, int nlines, int ls, int es,
                              const cpx<T>* tw, const NatIO<T>& nat) {
-    constexpr int LN = LOAD_NAT ? 1 : 0, SN = STORE_NAT ? 2 : 0;
+    constexpr int LN = LOAD_NAT ? (IN64 ? 17 : 1) : 0, SN = STORE_NAT ? 2 : 0;
     if constexpr (LS > 0) {
         return StaticPasses<T, INV, TXC, LN, SN, LS, KS, 0, 1>::run(b0, b1, t, nlines, ls, es, tw, nat);
     } else {

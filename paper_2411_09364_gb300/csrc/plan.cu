@@ -286,7 +286,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ra.in = in;
     ra.out = work;
     ra.nrows = nrows;
-    ra.rpc = rows_per_cta<T>(P->nx, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0, P->sched[0]);
+    ra.rpc = rows_per_cta<T>(P->nx, 0, P->sched[0]);
     ra.in_scale = 1.0;
     ra.shift_acc = nullptr;
     ra.shift_scale = 0.0;

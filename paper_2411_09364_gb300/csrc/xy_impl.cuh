@@ -82,21 +82,27 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
-    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    // FP64 input of an FP32 solve is read by the first Stockham pass straight
+    // from global memory (prefetched into L2 while the tables are staged);
+    // input of the compute type arrives by one TMA bulk copy into b0.
+    constexpr bool IN64 = sizeof(TIn) == 8 && sizeof(T) == 4;
+    const RowLayout<T> lay(a.rpc, L, n, kind, t.twlen, 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     cpx<T>* b0 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b0);
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
-    // natural rows land in b0 (same type) or in the extra area (FP64 input)
-    TIn* stage = sizeof(TIn) == sizeof(T) ? reinterpret_cast<TIn*>(b0) : reinterpret_cast<TIn*>(smem_raw + lay.extra);
     const cpx<T>* pst = tw_s + t.twlen;
     const cpx<T>* mkt = tw_s + t.twlen + L + 1;
     const int tot = nr * n;
-    if (a.bulk) {
+    if (IN64) {
+        if (tid == 0 && a.bulk) bulk_prefetch_l2(in, (uint32_t)(tot * sizeof(TIn)));
+        stage_twiddles(tw_s, t);
+        __syncthreads();
+    } else if (a.bulk) {
         if (tid == 0) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)(tot * sizeof(TIn)));
-            bulk_g2s(stage, in, (uint32_t)(tot * sizeof(TIn)), bar);
+            bulk_g2s(b0, in, (uint32_t)(tot * sizeof(TIn)), bar);
         }
         stage_twiddles(tw_s, t);
         __syncthreads();
@@ -107,28 +113,32 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
             return;
         }
     } else {
+        TIn* stage = reinterpret_cast<TIn*>(b0);
         for (int e = tid; e < tot; e += blockDim.x) stage[e] = in[e];
         stage_twiddles(tw_s, t);
         __syncthreads();
     }
-    NatIO<T> nat{reinterpret_cast<const T*>(b0), nullptr, n, 1};
-    const bool fused = sizeof(TIn) == sizeof(T) && nrad > 0 && sc == T(1);
+    NatIO<T> nat{reinterpret_cast<const T*>(b0), nullptr, n, 1, reinterpret_cast<const double*>(in)};
+    // (the fused FP64 read uses 16-byte loads: only with aligned rows)
+    const bool fused = nrad > 0 && sc == T(1) && (!IN64 || a.bulk);
     if (!fused) {
-        // explicit packing (FP64 input of an FP32 solve, or n == 2)
-        T* r0 = reinterpret_cast<T*>(sizeof(TIn) == sizeof(T) ? b1 : b0);
+        // explicit packing (n == 2, or a scaled input)
+        T* r0 = reinterpret_cast<T*>(IN64 ? b0 : b1);
+        const T* s32 = reinterpret_cast<const T*>(b0);
         for (int e = tid; e < tot; e += blockDim.x) {
             const int r = sdiv<LS ? 2 * LS : 0>(e, t.nmag), s = e - r * n;
             T v;
-            if (sizeof(TIn) == 8 && sizeof(T) == 4) v = T(trunc_double_int(double(stage[e])));
-            else v = T(stage[e]);
+            if (IN64) v = T(trunc_double_int(double(in[e])));
+            else v = s32[e];
             r0[r * n + pack_index(kind, n, s)] = v * sc * pack_sign<T>(kind, s);
         }
         __syncthreads();
     }
     cpx<T>* Z;
-    if (fused && kind == KIND_P) Z = fft_lines<T, false, 0, false, false, LS, KS>(b0, b1, t, nr, L, 1, tw_s, nat);
+    if (fused && IN64) Z = fft_lines<T, false, 0, true, false, LS, KS, true>(b0, b1, t, nr, L, 1, tw_s, nat);
+    else if (fused && kind == KIND_P) Z = fft_lines<T, false, 0, false, false, LS, KS>(b0, b1, t, nr, L, 1, tw_s, nat);
     else if (fused) Z = fft_lines<T, false, 0, true, false, LS, KS>(b0, b1, t, nr, L, 1, tw_s, nat);
-    else if (sizeof(TIn) == sizeof(T)) Z = fft_lines<T, false, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
+    else if (!IN64) Z = fft_lines<T, false, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
     else Z = fft_lines<T, false, 0, false, false, LS, KS>(b0, b1, t, nr, L, 1, tw_s, nat);
     T* ob = reinterpret_cast<T*>(Z == b0 ? b1 : b0);
     const int half = L / 2 + 1;
@@ -389,7 +399,7 @@ template <typename T> inline bool radices_match(const DirTab<T>& t, int L) {
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn, int LS, int KS>
 cudaError_t launch_rows_forward_v(const RowArgs<T>& a, cudaStream_t st) {
-    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, sizeof(TIn) != sizeof(T) ? sizeof(TIn) : 0);
+    const RowLayout<T> lay(a.rpc, a.t.L > 0 ? a.t.L : 1, a.t.n, a.t.kind, a.t.twlen, 0);
     auto kern = k_rows_forward<T, TIn, LS, KS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     const unsigned grid = (unsigned)((a.nrows + a.rpc - 1) / a.rpc);

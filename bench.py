@@ -83,7 +83,7 @@ class Clocks:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -160,12 +160,93 @@ def cpu_baseline_leg():
     while True:
         O.solve(f, g)
         reps += 1
-        if time.perf_counter() - t0 > 10.0 or reps >= 20:
+        if time.perf_counter() - t0 > 12.0 or reps >= 200:
             break
     dt = (time.perf_counter() - t0) / reps
     return {"value": nx * ny * nz / dt / 1e9, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
             "kind": "oracle", "sample": f"FP64 oracle solve of the same duct family at {nx}x{ny}x{nz}, "
                                         f"{reps} repetitions ({dt:.2f} s each)"}
+
+
+def run_configs(args):
+    """Timings of the other workloads of the solver (one JSON line each): the
+    small channel (L2-resident), the 512x256x192 channel in FP64 / FP32 /
+    FP32 + refinement, the 16-domain RK3 substep graph and the differentiable
+    256x128x128 solve (forward + backward).  Not the headline line."""
+    import torch
+    from paper_2411_09364_gb300 import autograd as AG
+    from paper_2411_09364_gb300 import batch as B
+    from paper_2411_09364_gb300 import solver as cs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    # channel 64x32x32, P,P,N, uniform z, FP64: fits L2, latency-bound
+    plan = cs.channel_plan(64, 32, 32, beta=0.0)
+    f = torch.from_numpy(S.gaussian(1000, (32, 32, 64))).to(dev)
+    p = torch.empty_like(f)
+    ms = timed(lambda: plan.poisson(f, p), 200)
+    emit({"workload": "channel_poisson_64x32x32", "mode": "fp64", "ms": ms, "solves_per_s": 1e3 / ms,
+          "gpoints_per_s": f.numel() / ms / 1e6, "l2": "fits L2 (warm)"})
+    # channel 512x256x192, P,P,N, tanh beta = 1.8
+    plan = cs.channel_plan(512, 256, 192, beta=1.8)
+    f64 = torch.from_numpy(S.gaussian(2000, (192, 256, 512))).to(dev)
+    out = {}
+    for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
+        plan.set_precision(mode, 2)
+        fi = f64 if mode != cs.FP32 else f64.float()
+        po = torch.empty_like(fi)
+        ms = timed(lambda: plan.poisson(fi, po), 20)
+        out[name] = po.double()
+        rel = (float(torch.linalg.vector_norm(out[name] - out["fp64"]) / torch.linalg.vector_norm(out["fp64"]))
+               if name != "fp64" else 0.0)
+        emit({"workload": "channel_poisson_512x256x192", "mode": name, "ms": ms,
+              "gpoints_per_s": fi.numel() / ms / 1e6, "rel_err_vs_fp64_gpu": rel,
+              "min_traffic_roofline_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+    # 16 channel domains x {u, v, w Helmholtz, p Poisson}, FP32 + refinement, one CUDA graph
+    alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
+    batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
+    fs = [torch.from_numpy(S.gaussian(4000 + i, pl.shape)).to(dev) for i, pl in enumerate(plans)]
+    us = [torch.empty_like(x) for x in fs]
+    st = batch.capture(fs, us)
+    for _ in range(3):
+        batch.launch(st)
+    st.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(10):
+        batch.launch(st)
+    b.record(st)
+    st.synchronize()
+    ms = a.elapsed_time(b) / 10
+    pts = sum(pl.numel for pl in plans)
+    emit({"workload": "rk3_substep_16_channel_domains", "mode": "fp32_refine", "ms": ms,
+          "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
+    # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
+    plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
+    fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)
+    wd = torch.from_numpy(S.gaussian(5001, (128, 128, 256))).to(dev, torch.float32)
+
+    def fwd_bwd():
+        fd.grad = None
+        (wd * AG.poisson_solve(fd, plan)).sum().backward()
+    ms = timed(fwd_bwd, 20)
+    emit({"workload": "differentiable_poisson_256x128x128", "mode": "fp32 forward+backward", "ms": ms,
+          "gpoints_per_s": fd.numel() / ms / 1e6})
 
 
 def main():
@@ -179,9 +260,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="512x256x192 channel variant (profiling)")
     ap.add_argument("--shape", default=None, help="NX,NY,NZ: the duct at another size (profiling case)")
+    ap.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.configs:
+        return run_configs(args)
 
     import torch
     import torch.distributed as dist
@@ -341,7 +425,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "bc": "P x, N y (DCT-II), N z tanh",
                    "precision": f"FP32 solves + {args.sweeps} double-float refinement sweeps",
-                   "l2": "inputs larger than L2 (f and p 3.2 GB each), no flush needed",
+                   "l2": f"inputs larger than L2 (f and p {npts * 8 / 1e9:.1f} GB each), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "fp64": {"value": npts * world / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64, "unit": UNIT},
         "rel_err_refine_vs_fp64_gpu": rel,

@@ -177,19 +177,21 @@ __device__ __forceinline__ ff split_double_fast(double d) {
     return ff{hi, lo};
 }
 
-// One point of the double-float residual (the arithmetic of k_residual_ff):
-// c the point, w e s n d up its neighbours (x-, x+, y-, y+, z-, z+), fv = f.
-// SING: singular Poisson (consistency shift subtracted, gauge sum of u kept
-// as an unnormalised (hi, lo) pair); HELM: the c0 u term of Eq. 18.
-template <bool SING, bool HELM>
-__device__ __forceinline__ float resid_point(float2 c, float2 w, float2 e, float2 s, float2 n, float2 d, float2 up,
-                                             double fv, ff cx, ff cy, ff zc, ff za, ff csh, float& ghi, float& glo) {
-    const ff de = two_sum(e.x, -c.x), dw = two_sum(w.x, -c.x);
+// One point of the double-float residual (the arithmetic of k_residual_ff)
+// with its x differences given: de = e - c and dw = w - c of the hi parts as
+// exact pairs, lxe / lxw the differences of the lo parts; c the point,
+// s n d up its y and z neighbours, fv = f.  SING: singular Poisson
+// (consistency shift subtracted); GAUGE: the gauge sum of u is kept as an
+// unnormalised (hi, lo) pair; HELM: the c0 u term of Eq. 18.
+template <bool SING, bool HELM, bool GAUGE>
+__device__ __forceinline__ float resid_point(float2 c, ff de, ff dw, float lxe, float lxw, float2 s, float2 n,
+                                             float2 d, float2 up, double fv, ff cx, ff cy, ff zc, ff za, ff csh,
+                                             float& ghi, float& glo) {
     const ff dn = two_sum(n.x, -c.x), ds = two_sum(s.x, -c.x);
     const ff du = two_sum(up.x, -c.x), dd = two_sum(d.x, -c.x);
     const ff sx = two_sum(de.hi, dw.hi), sy = two_sum(dn.hi, ds.hi);
-    const float sxl = sx.lo + de.lo + dw.lo + ((e.y - c.y) + (w.y - c.y));
-    const float syl = sy.lo + dn.lo + ds.lo + ((n.y - c.y) + (s.y - c.y));
+    const float sxl = sx.lo + de.lo + dw.lo + (lxe + lxw);
+    const float syl = sy.lo + dn.lo + ds.lo + __fmaf_rn(-2.f, c.y, n.y + s.y);
     const float dul = du.lo + (up.y - c.y), ddl = dd.lo + (d.y - c.y);
     const ff px = two_prod(cx.hi, sx.hi);
     float comp = __fmaf_rn(cx.hi, sxl, __fmaf_rn(cx.lo, sx.hi, px.lo));
@@ -217,7 +219,7 @@ __device__ __forceinline__ float resid_point(float2 c, float2 w, float2 e, float
     acc = two_sum(acc.hi, -py.hi); err += acc.lo;
     acc = two_sum(acc.hi, -pz.hi); err += acc.lo;
     acc = two_sum(acc.hi, -pd.hi); err += acc.lo;
-    if (SING) {
+    if (GAUGE) {
         const ff g = two_sum(ghi, c.x);
         ghi = g.hi;
         glo += g.lo + c.y;
@@ -234,7 +236,7 @@ __device__ __forceinline__ float4 sc4(float g, float4 v) { return make_float4(g 
 // aligned u and f): the centre pair, both y and both z neighbour pairs and
 // f come in one vector load each, the x neighbours of the pair in two 8-byte
 // loads.  A CTA covers whole rows of one z-plane.
-template <bool SING, bool HELM>
+template <bool SING, bool HELM, bool GAUGE>
 __global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
     const int nx = a.nx, ny = a.ny;
     const long plane = (long)nx * ny;
@@ -280,14 +282,19 @@ __global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
                 if (i == 0) w = make_float2(gx * w.x, gx * w.y);
                 if (i + 2 == nx) e = make_float2(gx * e.x, gx * e.y);
             }
-            const float r0 = resid_point<SING, HELM>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up), fv.x,
-                                                     cx, cy, zc, za, csh, ghi, glo);
-            const float r1 = resid_point<SING, HELM>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up), fv.y,
-                                                     cx, cy, zc, za, csh, ghi, glo);
+            // x differences of the pair: the centre-to-centre one serves both
+            // points (negated for the second: TwoSum is odd under negation)
+            const ff d01 = two_sum(c.z, -c.x);
+            const float l01 = c.w - c.y;
+            const ff dw0 = two_sum(w.x, -c.x), de1 = two_sum(e.x, -c.z);
+            const float r0 = resid_point<SING, HELM, GAUGE>(lo2(c), d01, dw0, l01, w.y - c.y, lo2(s), lo2(n), lo2(d),
+                                                            lo2(up), fv.x, cx, cy, zc, za, csh, ghi, glo);
+            const float r1 = resid_point<SING, HELM, GAUGE>(hi2(c), de1, ff_neg(d01), e.y - c.w, -l01, hi2(s), hi2(n),
+                                                            hi2(d), hi2(up), fv.y, cx, cy, zc, za, csh, ghi, glo);
             *reinterpret_cast<float2*>(a.r + rb + i) = make_float2(r0, r1);
         }
     }
-    if (SING && a.gacc) {
+    if (GAUGE && a.gacc) {
         double v = (double)ghi + (double)glo;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -316,10 +323,12 @@ cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     const bool sing = a.gacc != nullptr || a.cshift != nullptr;
     const bool helm = a.c0h != 0.f;
     if (!vec) k_residual_ff<<<grid, 256, 0, st>>>(a);
-    else if (sing && !helm) k_residual_ff2<true, false><<<grid, 256, 0, st>>>(a);
-    else if (sing) k_residual_ff2<true, true><<<grid, 256, 0, st>>>(a);
-    else if (helm) k_residual_ff2<false, true><<<grid, 256, 0, st>>>(a);
-    else k_residual_ff2<false, false><<<grid, 256, 0, st>>>(a);
+    else if (a.gacc && !helm) k_residual_ff2<true, false, true><<<grid, 256, 0, st>>>(a);
+    else if (a.gacc) k_residual_ff2<true, true, true><<<grid, 256, 0, st>>>(a);
+    else if (sing && !helm) k_residual_ff2<true, false, false><<<grid, 256, 0, st>>>(a);
+    else if (sing) k_residual_ff2<true, true, false><<<grid, 256, 0, st>>>(a);
+    else if (helm) k_residual_ff2<false, true, false><<<grid, 256, 0, st>>>(a);
+    else k_residual_ff2<false, false, false><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -413,12 +413,14 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
         ra.zc = P->zc_d;
         ra.c1 = c1;
         ra.cshift = sing ? P->acc : nullptr;
-        ra.gacc = sing ? P->acc + 1 : nullptr;
+        // the gauge of p is measured by the last sweep only: the operator
+        // annihilates constants, so earlier iterates may carry any mean
+        ra.gacc = (sing && s == ns - 1) ? P->acc + 1 : nullptr;
         ra.dzf = P->dzf_d;
         P->prof_begin(st, "residual");
         if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
         P->prof_end(st);
-        o.shift_acc = sing ? P->acc + 1 : nullptr;
+        o.shift_acc = (sing && s == ns - 1) ? P->acc + 1 : nullptr;
         o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
         rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, P->work, p, P->work, o, st)
                            : pipeline<float, float, OUT_FF_ACC>(P, P->work, p, P->work, o, st);
@@ -743,10 +745,10 @@ extern "C" int cales_poisson_solve_noalloc(cales_plan_t P, const void* f, void* 
         ra.zc = P->zc_d;
         ra.c1 = 1.0;
         ra.cshift = sing ? acc : nullptr;
-        ra.gacc = sing ? acc + 1 : nullptr;
+        ra.gacc = (sing && s == ns - 1) ? acc + 1 : nullptr;
         ra.dzf = P->dzf_d;
         if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
-        o.shift_acc = sing ? acc + 1 : nullptr;
+        o.shift_acc = (sing && s == ns - 1) ? acc + 1 : nullptr;
         o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
         rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, work, p, work, o, st)
                            : pipeline<float, float, OUT_FF_ACC>(P, work, p, work, o, st);

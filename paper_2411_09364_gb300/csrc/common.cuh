@@ -614,6 +614,28 @@ __device__ __forceinline__ ff ff_from_double(double v) {
 }
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
+// hi + lo (a normalised pair) as a double without FP64 instructions: hi's bit
+// pattern widened to a double, then lo, scaled to units of the double's last
+// place by an exact power-of-two multiply and rounded to an integer, added to
+// (same signs) or subtracted from (opposite signs) that pattern as a 64-bit
+// integer.  hi + lo never leaves hi's binade upward; when hi is a power of
+// two and lo has the opposite sign the result lies one binade lower, where the
+// last place is half as large.  Tiny, huge, zero or non-finite hi take the
+// FP64 path.
+__device__ __forceinline__ double ff_to_double_bits(ff x) {
+    const unsigned hb = __float_as_uint(x.hi), lb = __float_as_uint(x.lo);
+    const unsigned eh = (hb >> 23) & 0xffu;
+    if (eh < 60u || eh > 253u) return ff_to_double(x);
+    const unsigned mant = hb & 0x7fffffu;
+    const unsigned long long bits = ((unsigned long long)((hb & 0x80000000u) | ((eh + 896u) << 20) | (mant >> 3)) << 32) |
+                                    (unsigned long long)(mant << 29);
+    const bool opp = ((lb ^ hb) & 0x80000000u) && x.lo != 0.f;
+    const unsigned down = (mant == 0u && opp) ? 1u : 0u;
+    const float sc = __uint_as_float((306u + down - eh) << 23);        // 2^(179 - eh (+1))
+    const unsigned long long l = __float2uint_rn(fabsf(x.lo) * sc);
+    return __longlong_as_double((long long)(opp ? bits - l : bits + l));
+}
+
 // 2^k as a float for k in [-126, 127] (bit construction, no FP64 / MUFU).
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 

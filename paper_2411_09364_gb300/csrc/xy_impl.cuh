@@ -172,7 +172,37 @@ __device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
         const float2 pr = *reinterpret_cast<const float2*>(slot);
         const ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
         if (MODE == OUT_FF_ACC) *reinterpret_cast<float2*>(slot) = make_float2(x.hi, x.lo);
-        else *reinterpret_cast<double*>(slot) = ff_to_double(x);
+        else *reinterpret_cast<double*>(slot) = ff_to_double_bits(x);
+    }
+}
+
+// The 8-byte results of a CTA's rows: pair updates load U pairs per thread
+// before computing any (more loads in flight per thread).
+template <typename T, int MODE>
+__device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, int tot, ff shift) {
+    if (MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL) {
+        constexpr int U = 4;
+        const int bd = blockDim.x;
+        float2* po = reinterpret_cast<float2*>(outp);
+        for (int e0 = threadIdx.x; e0 < tot; e0 += U * bd) {
+            float2 pr[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * bd;
+                if (e < tot) pr[u] = po[e];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * bd;
+                if (e < tot) {
+                    const ff x = ff_add(ff{pr[u].x, pr[u].y}, ff_sub(ff{float(vals[e]), 0.f}, shift));
+                    if (MODE == OUT_FF_ACC) po[e] = make_float2(x.hi, x.lo);
+                    else reinterpret_cast<double*>(outp)[e] = ff_to_double_bits(x);
+                }
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) store8<T, MODE>(outp + (long)e * 8, vals[e], shift);
     }
 }
 
@@ -250,7 +280,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         if (kind == KIND_P) fft_lines<T, true, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
         else fft_lines<T, true, 0, false, true, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
         if (MODE != OUT_T) {
-            for (int e = tid; e < tot; e += blockDim.x) store8<T, MODE>(outp + (long)e * 8, natout[e], shift);
+            store8_rows<T, MODE>(outp, natout, tot, shift);
             return;
         }
         ob = natout;

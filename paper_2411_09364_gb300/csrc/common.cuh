@@ -226,8 +226,12 @@ __device__ __forceinline__ float trunc_double_int(double d);
 // R = 8 with Ns = 1, 2, 4, 8, R = 4 with Ns = 1) land in 16 distinct 8-byte
 // bank pairs per half-warp instead of piling into R-way conflicts.  Buffers
 // hold a multiple of 16 elements so the map stays inside them.
-template <bool ON> __device__ __forceinline__ int swz(int i) {
+// FAST: when the first pass is radix 16 (the only pass with Ns < 16), the
+// plain map sw(b) = b & 15 already separates its stride-16 writes, for two
+// integer operations instead of six.
+template <bool ON, bool FAST = false> __device__ __forceinline__ int swz(int i) {
     if (!ON) return i;
+    if (FAST) return i ^ ((i >> 4) & 15);
     const int b = i >> 4;
     const int lo = b & 7;
     return i ^ (lo | (((__popc(lo) ^ (b >> 3)) & 1) << 3));
@@ -235,7 +239,8 @@ template <bool ON> __device__ __forceinline__ int swz(int i) {
 
 // IO bits: 1 = first pass packs the real natural input, 2 = last pass unpacks
 // into the real natural output, 4 = source swizzled, 8 = destination swizzled,
-// 16 = the natural input is FP64 in global memory (NatIO::in64).
+// 16 = the natural input is FP64 in global memory (NatIO::in64), 32 = the
+// swizzle is the radix-16-first one (swz FAST).
 // LS > 0: the line length L = LS is a compile-time constant (n = 2 LS), and
 // so are the pass sizes (NSS = Ns of this pass); KS >= 0: compile-time kind.
 // Then every index division folds to constants and shifts.
@@ -293,7 +298,7 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
         } else {
             const int s0 = line * ls + j * es, sst = nb * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = src[swz<(IO & 4) != 0>(s0 + r * sst)];
+            for (int r = 0; r < R; ++r) v[r] = src[swz<(IO & 4) != 0, (IO & 32) != 0>(s0 + r * sst)];
         }
         if (LS ? (NSS > 1) : (Ns > 1)) {
 #pragma unroll
@@ -316,7 +321,7 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
         } else {
             const int d0 = line * ls + base * es, dstp = Ns * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[swz<(IO & 8) != 0>(d0 + r * dstp)] = v[r];
+            for (int r = 0; r < R; ++r) dst[swz<(IO & 8) != 0, (IO & 32) != 0>(d0 + r * dstp)] = v[r];
         }
     }
 }
@@ -374,7 +379,9 @@ struct StaticPasses {
         constexpr int R = sf_radix(LS, P);
         constexpr bool first = P == 0, last = P == NR - 1;
         constexpr int SW = (TXC == 0 && sizeof(T) == 4) ? 1 : 0;
-        constexpr int IO = (first ? LN : 0) | (last ? SN : 0) | (first ? 0 : 4 * SW) | (last ? 0 : 8 * SW);
+        constexpr int FAST = (SW && sf_radix(LS, 0) == 16) ? 32 : 0;
+        constexpr int IO = (first ? LN : 0) | (last ? SN : 0) | (first ? 0 : 4 * SW) | (last ? 0 : 8 * SW) |
+                           ((first && last) ? 0 : FAST);
         stockham_pass<T, R, INV, TXC, IO, LS, NS, KS, sf_twoff(LS, P)>(src, dst, t, P, nlines, ls, es, tw, nat);
         __syncthreads();
         if constexpr (last) return dst;

@@ -372,57 +372,47 @@ def main():
 
     # --- end to end through the C ABI with host buffers ----------------------
     # Every step copies its right-hand side from pinned host memory, solves and
-    # copies the solution back.  Two device buffer sets alternate so the copies
-    # of one step overlap the solve of the other (copy engines vs SMs).
+    # copies the solution back.  NB device buffer sets rotate so the copies of
+    # one step overlap the solves of the others (copy engines vs SMs); with
+    # three sets the device-to-host copy of step i and the host-to-device copy
+    # of step i + NB need not finish before the next solve starts.
+    NB = 3
     f_pin = f_host.pin_memory()
-    p_pins = [torch.empty_like(f_pin).pin_memory() for _ in range(2)]
-    fds = [torch.empty_like(f) for _ in range(2)]
-    pds = [torch.empty_like(f) for _ in range(2)]
-    # each direction's copy is split into NC chunks on NC streams (several
-    # copy engines in flight)
-    NC = 2
-    h2ds = [torch.cuda.Stream(dev) for _ in range(NC)]
-    d2hs = [torch.cuda.Stream(dev) for _ in range(NC)]
-    copied = [[torch.cuda.Event() for _ in range(NC)] for _ in range(2)]
-    solved = [torch.cuda.Event() for _ in range(2)]
-    freed = [[torch.cuda.Event() for _ in range(NC)] for _ in range(2)]
-    f_pin_c = f_pin.view(-1).chunk(NC)
-    p_pin_c = [x.view(-1).chunk(NC) for x in p_pins]
-    fd_c = [x.view(-1).chunk(NC) for x in fds]
-    pd_c = [x.view(-1).chunk(NC) for x in pds]
-    for b in range(2):
-        for c in range(NC):
-            freed[b][c].record(d2hs[c])
+    p_pins = [torch.empty_like(f_pin).pin_memory() for _ in range(NB)]
+    fds = [torch.empty_like(f) for _ in range(NB)]
+    pds = [torch.empty_like(f) for _ in range(NB)]
+    h2d = torch.cuda.Stream(dev)
+    d2h = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event() for _ in range(NB)]
+    solved = [torch.cuda.Event() for _ in range(NB)]
+    freed = [torch.cuda.Event() for _ in range(NB)]
+    for b in range(NB):
+        freed[b].record(d2h)
 
     def e2e_step(i):
-        b = i % 2
-        for c in range(NC):
-            for cc in range(NC):
-                h2ds[c].wait_event(freed[b][cc])
-            with torch.cuda.stream(h2ds[c]):
-                fd_c[b][c].copy_(f_pin_c[c], non_blocking=True)
-            copied[b][c].record(h2ds[c])
-            stream.wait_event(copied[b][c])
+        b = i % NB
+        h2d.wait_event(freed[b])
+        with torch.cuda.stream(h2d):
+            fds[b].copy_(f_pin, non_blocking=True)
+        copied[b].record(h2d)
+        stream.wait_event(copied[b])
         plan.poisson(fds[b], pds[b], stream=stream)
         solved[b].record(stream)
-        for c in range(NC):
-            d2hs[c].wait_event(solved[b])
-            with torch.cuda.stream(d2hs[c]):
-                p_pin_c[b][c].copy_(pd_c[b][c], non_blocking=True)
-            freed[b][c].record(d2hs[c])
+        d2h.wait_event(solved[b])
+        with torch.cuda.stream(d2h):
+            p_pins[b].copy_(pds[b], non_blocking=True)
+        freed[b].record(d2h)
 
-    for i in range(2):
+    for i in range(NB):
         e2e_step(i)
     barrier()
     torch.cuda.synchronize(dev)
-    e2e_steps = max(2, min(args.steps, 6))
+    e2e_steps = max(NB, min(args.steps, 9))
     ev0.record(stream)
-    for h in h2ds:
-        h.wait_event(ev0)
+    h2d.wait_event(ev0)
     for i in range(e2e_steps):
         e2e_step(i)
-    for d in d2hs:
-        stream.wait_stream(d)
+    stream.wait_stream(d2h)
     ev1.record(stream)
     barrier()
     ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / e2e_steps)

@@ -44,7 +44,7 @@ __all__ = [
     "BC_P", "BC_N", "BC_D", "BC_DF", "BC_NAMES", "Grid", "cell_spacings",
     "face_spacings", "apply_L", "apply_M", "fwd_matrix", "inv_matrix",
     "eigenvalues", "z_operator", "thomas", "is_singular", "weighted_mean",
-    "project", "solve", "solve_T", "dense_matrix", "dense_solve", "residual",
+    "project", "solve", "solve_z_lines", "solve_T", "dense_matrix", "dense_solve", "residual",
     "rel_l2", "divergence", "gradient", "divergence_T", "gradient_T",
 ]
 
@@ -340,6 +340,18 @@ def solve(f: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     if sing:
         p = p - weighted_mean(p, g)
     return np.ascontiguousarray(p)
+
+
+def solve_z_lines(f: np.ndarray, g: Grid, alpha: float) -> np.ndarray:
+    """u with (I - alpha L_z) u = f on every (i, j) line independently: the
+    viscous term implicit along the wall-normal direction only (Eq. 21,
+    Sec. 2.2; the paper's wall-normal "y" is the stretched z here).  One
+    tridiagonal per line with the R2 z boundary rows, scalar Thomas; x and y
+    boundary kinds play no part."""
+    sub, diag, sup = z_operator(g)
+    rhs = np.asarray(f, dtype=np.float64).reshape(g.nz, -1)
+    u = thomas(-alpha * sub, 1.0 - alpha * diag, -alpha * sup, rhs)
+    return np.ascontiguousarray(u.reshape(g.nz, g.ny, g.nx))
 
 
 def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:

@@ -245,6 +245,32 @@ def test_helmholtz_small_alpha_returns_rhs():
     assert O.rel_l2(O.solve(f, g, 1e-12), f) < 1e-9
 
 
+@pytest.mark.parametrize("zlo,zhi", [(O.BC_N, O.BC_N), (O.BC_D, O.BC_D), (O.BC_D, O.BC_N), (O.BC_N, O.BC_D),
+                                     (O.BC_DF, O.BC_DF)])
+@pytest.mark.parametrize("alpha", [1e-4, 2e-2])
+def test_z_line_solves_against_stencil_and_full_method(zlo, zhi, alpha):
+    """Eq. 21 (implicit along z only): every line's stencil residual, through
+    apply_M on a 1 x 1 x nz grid, vanishes; and the full expansion method on a
+    single line (one mode, lambda = 0) gives the same line."""
+    nz = 23
+    g = make_grid(3, 2, nz, (O.BC_P, O.BC_P, O.BC_N, O.BC_N, zlo, zhi), beta=1.6)
+    f = RNG.standard_normal((nz, 2, 3))
+    u = O.solve_z_lines(f, g, alpha)
+    g1 = O.Grid(1, 1, nz, g.dx, g.dy, g.dzc, g.dzf, (O.BC_P, O.BC_P, O.BC_P, O.BC_P, zlo, zhi))
+    for j in range(2):
+        for i in range(3):
+            line = u[:, j, i].reshape(nz, 1, 1)
+            fl = f[:, j, i].reshape(nz, 1, 1)
+            assert np.allclose(O.apply_M(line, g1, alpha), fl, atol=1e-12)
+            assert O.rel_l2(O.solve(fl, g1, alpha), line) <= 1e-13
+
+
+def test_z_line_solve_small_alpha_returns_rhs():
+    g = make_grid(4, 3, 16, (O.BC_N, O.BC_N, O.BC_D, O.BC_D, O.BC_D, O.BC_N))
+    f = RNG.standard_normal((16, 3, 4))
+    assert O.rel_l2(O.solve_z_lines(f, g, 1e-12), f) < 1e-9
+
+
 def test_staggered_div_grad_is_laplacian_and_projection():
     g = make_grid(8, 6, 10, (O.BC_P, O.BC_P, O.BC_P, O.BC_P, O.BC_N, O.BC_N), beta=1.8)
     phi = RNG.standard_normal((10, 6, 8))

@@ -236,6 +236,23 @@ def run_configs(args):
     pts = sum(pl.numel for pl in plans)
     emit({"workload": "rk3_substep_16_channel_domains", "mode": "fp32_refine", "ms": ms,
           "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
+    # wall-normal implicit line solves (Eq. 21) on the bench grid, Dirichlet walls
+    w = WORKLOAD
+    zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
+    dzc, dzf = cs.cell_spacings(zf)
+    plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 1, 1, 2, 2), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
+                   cs.FP64)
+    fz = torch.from_numpy(make_rhs(w["nx"], w["ny"], w["nz"], zf, w["seed"])).to(dev)
+    for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32")):
+        plan.set_precision(mode)
+        fi = fz if mode == cs.FP64 else fz.float()
+        uo = torch.empty_like(fi)
+        ms = timed(lambda: plan.helmholtz_z(1e-4, fi, uo), 10)
+        emit({"workload": f"z_line_helmholtz_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
+              "gpoints_per_s": fi.numel() / ms / 1e6,
+              "hbm_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+    del fz, plan
+    torch.cuda.empty_cache()
     # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
     plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
     fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)

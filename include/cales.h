@@ -115,6 +115,17 @@ int cales_poisson_solve_adjoint(cales_plan_t plan, const void* w, void* g, void*
 int cales_helmholtz_solve_adjoint(cales_plan_t plan, double alpha, const void* w, void* g, void* stream);
 
 /*
+ * Wall-normal implicit step, Eq. 21 (viscous term implicit along the
+ * stretched direction only): (I - alpha L_z) u = f on every (i, j) line
+ * independently, one tridiagonal system per line with the plan's z grid and
+ * z boundary kinds (x and y kinds play no part).  alpha >= 0.  f and u are
+ * device arrays of nx*ny*nz elements, double for CALES_FP64 and
+ * CALES_FP32_REFINE plans (solved in FP64: one sweep per line, no
+ * refinement needed), float for CALES_FP32 plans; f == u is allowed.
+ */
+int cales_helmholtz_z_solve(cales_plan_t plan, double alpha, const void* f, void* u, void* stream);
+
+/*
  * Poisson solve like cales_poisson_solve with FP32 solves and double-float
  * refinement (the plan's refine_sweeps), for callers that cannot allocate
  * device memory when they solve: code running inside CUDA stream capture,

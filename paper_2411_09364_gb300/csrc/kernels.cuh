@@ -40,6 +40,7 @@ template <typename T> struct ColArgs {
 // L = L_z + lambda_x(mx) + lambda_y(my).
 template <typename T> struct ZArgs {
     T* data;             // [nz][nmodes] in place (nmodes = nx * ny)
+    const T* src;        // warp-per-segment kernel: input read from here (null: data)
     const T* lamx;       // [nx]
     const T* lamy;       // [ny]
     const T* za;         // [nz] coupling to k-1 (1 / (dzc[k] dzf[k]))
@@ -64,6 +65,7 @@ template <typename T> struct ZArgs {
     // computed and stored; 2: loaded (the composite-map phase is skipped).
     T* ecache;
     int ecache_mode;
+    long ecache_stride;  // nmodes; 0 when every line has the same pivots (line solves)
 };
 
 // FP64 residual r = f - (c0 u + c1 L u) of the 7-point staggered Laplacian.

@@ -313,6 +313,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
 
     ZArgs<T> za;
     za.data = work;
+    za.src = nullptr;
     za.lamx = sizeof(T) == 8 ? (const T*)P->X.lam_d : (const T*)P->X.lam_f;
     za.lamy = sizeof(T) == 8 ? (const T*)P->Y.lam_d : (const T*)P->Y.lam_f;
     za.za = sizeof(T) == 8 ? (const T*)P->za_d : (const T*)P->za_f;
@@ -337,6 +338,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
         za.ecache_mode = (zk.valid && zk.P == za.P && zk.maxm == za.maxm && zk.sigma == o.sigma &&
                           zk.alpha == o.alpha) ? 2 : 1;
     }
+    za.ecache_stride = (long)P->nx * P->ny;
     P->prof_begin(st, "z_solve");
     if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
     if (za.ecache_mode == 1) {
@@ -481,6 +483,54 @@ void cales_plan_s::fill_resid(cales::ResidArgs& ra, const double* u, const doubl
     ra.fshift = 0.0;
 }
 
+// Line solves of the wall-normal implicit step (Eq. 21): the z kernel on the
+// physical field with every eigenvalue zero and no transform scaling.
+template <typename T>
+static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t st) {
+    ZArgs<T> za;
+    za.data = u;
+    za.src = f;
+    za.lamx = sizeof(T) == 8 ? (const T*)P->zero_d : (const T*)P->zero_f;
+    za.lamy = za.lamx;
+    za.za = sizeof(T) == 8 ? (const T*)P->za_d : (const T*)P->za_f;
+    za.zc = sizeof(T) == 8 ? (const T*)P->zc_d : (const T*)P->zc_f;
+    za.dzf = P->dzf_d;
+    za.nx = P->nx; za.ny = P->ny; za.nz = P->nz;
+    za.zlo = P->bc[4]; za.zhi = P->bc[5];
+    za.singular = 0;
+    za.adjoint = 0;
+    choose_zt<T>(P->nz, za.tm, za.P, za.maxm, za.warp_mode, P->sched[2], P->sched[3]);
+    za.bulk = (aligned16(u) && aligned16(f) && ((size_t)P->nx * P->ny * sizeof(T)) % 16 == 0 &&
+               (za.tm * sizeof(T)) % 16 == 0) ? 1 : 0;
+    za.sigma = T(1); za.alpha = T(alpha); za.scale = T(1);
+    za.status = P->status;
+    za.cacc = nullptr;
+    za.cacc_scale = 0.0;
+    za.ecache = nullptr;
+    za.ecache_mode = 0;
+    za.ecache_stride = 0;
+    const int zi = sizeof(T) == 8 ? 1 : 0;
+    cales_plan_s::ZCacheKey& lk = P->lkey[zi];
+    if (za.warp_mode && za.P <= 16 && P->lcache[zi]) {
+        za.ecache = reinterpret_cast<T*>(P->lcache[zi]);
+        za.ecache_mode = (lk.valid && lk.P == za.P && lk.maxm == za.maxm && lk.alpha == alpha) ? 2 : 1;
+    }
+    if (!za.warp_mode) {
+        // the other z kernels work in place
+        if (f != u && cudaMemcpyAsync(u, f, (size_t)P->nx * P->ny * P->nz * sizeof(T), cudaMemcpyDeviceToDevice,
+                                      st) != cudaSuccess)
+            return CALES_ECUDA;
+        za.src = nullptr;
+    }
+    P->prof_begin(st, "z_lines");
+    if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+    if (za.ecache_mode == 1) {
+        lk.valid = 1; lk.P = za.P; lk.maxm = za.maxm; lk.sigma = 1.0; lk.alpha = alpha;
+    }
+    return CALES_OK;
+}
+
 // Segment-entry pivot cache of one precision: 16 slots per mode (the largest
 // segment count of the z kernel).  Left out when the allocation fails.
 static void alloc_zcache(cales_plan_s* P, int zi) {
@@ -553,10 +603,15 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         P->idzc_f = dev_upload(idzcf, P->owned);
         std::vector<double> acc(4, 0.0);
         P->acc = dev_upload(acc, P->owned);
+        const int nzero = nx > ny ? nx : ny;
+        P->zero_d = dev_upload(std::vector<double>(nzero, 0.0), P->owned);
+        P->zero_f = dev_upload(std::vector<float>(nzero, 0.0f), P->owned);
+        P->lcache[1] = dev_upload(std::vector<double>(16, 0.0), P->owned);
+        P->lcache[0] = dev_upload(std::vector<float>(16, 0.0f), P->owned);
         P->dzf_sum = 0.0;
         for (int k = 0; k < nz; ++k) P->dzf_sum += dzf[k];
         if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status || !P->acc || !P->idzf_d ||
-            !P->idzc_d || !P->idzf_f || !P->idzc_f)
+            !P->idzc_d || !P->idzf_f || !P->idzc_f || !P->zero_d || !P->zero_f)
             rc = CALES_ENOMEM;
     }
     if (rc == CALES_OK && cudaDeviceSynchronize() != cudaSuccess) rc = CALES_ECUDA;
@@ -593,6 +648,13 @@ int cales_poisson_solve(cales_plan_t P, const void* f, void* p, void* stream) {
 
 int cales_helmholtz_solve(cales_plan_t P, double alpha, const void* f, void* u, void* stream) {
     return solve_common(P, true, alpha, false, f, u, stream);
+}
+
+int cales_helmholtz_z_solve(cales_plan_t P, double alpha, const void* f, void* u, void* stream) {
+    if (!P || !f || !u || !(alpha >= 0.0) || !std::isfinite(alpha)) return CALES_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (P->precision == CALES_FP32) return z_lines<float>(P, alpha, (const float*)f, (float*)u, st);
+    return z_lines<double>(P, alpha, (const double*)f, (double*)u, st);
 }
 
 int cales_poisson_solve_adjoint(cales_plan_t P, const void* w, void* g, void* stream) {

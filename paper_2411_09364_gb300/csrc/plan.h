@@ -42,6 +42,8 @@ struct cales_plan_s {
     double* zc_d = nullptr;
     double* dzf_d = nullptr;
     float* za_f = nullptr;
+    double* zero_d = nullptr;    // max(nx, ny) zeros: the eigenvalues of the line solves
+    float* zero_f = nullptr;
     float* zc_f = nullptr;
     int* status = nullptr;
     double* acc = nullptr;       // [0] consistency constant, [1] gauge sum (refinement)
@@ -60,6 +62,9 @@ struct cales_plan_s {
     struct ZCacheKey { int valid = 0, P = 0, maxm = 0; double sigma = 0.0, alpha = 0.0; };
     void* zcache[2] = {nullptr, nullptr};
     ZCacheKey zkey[2];
+    // the same for the line solves (all eigenvalues zero: 16 values per precision)
+    void* lcache[2] = {nullptr, nullptr};
+    ZCacheKey lkey[2];
     std::vector<void*> owned;
     static constexpr int PROF_MAX = 4096;
     bool prof_on = false;

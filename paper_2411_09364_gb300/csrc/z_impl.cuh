@@ -632,6 +632,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
     ZPair<T>* sAC = reinterpret_cast<ZPair<T>*>(r0 + nz);
     const long q0 = (long)blockIdx.x * TM;
     const int w = (int)min((long)TM, nmodes - q0);
+    const T* __restrict__ in = a.src ? a.src : a.data;
     const int tid = threadIdx.x;
 
     for (int k = tid; k < nz; k += nthr) {
@@ -649,13 +650,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
     if (a.bulk) {
         for (int e = tid; e < nz * CPR; e += nthr) {
             const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            cp_async16(tile + k * TM + c0, a.data + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
+            cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
         }
         cp_async_wait_all();
     } else {
         for (int e = tid; e < nz * TM; e += nthr) {
             const int k = e / TM, c = e - k * TM;
-            tile[e] = c < w ? a.data[(long)k * nmodes + q0 + c] : T(0);
+            tile[e] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
         }
     }
     __syncthreads();
@@ -692,7 +693,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
 
     T e_in;
     if (a.ecache_mode == 2) {
-        e_in = s > 0 ? a.ecache[(long)s * nmodes + q] : T(0);
+        e_in = s > 0 ? a.ecache[a.ecache_stride ? (long)s * a.ecache_stride + q : (long)s] : T(0);
     } else {
         // A: composite pivot map of the segment
         {
@@ -733,7 +734,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
         }
         __syncthreads();
         e_in = cin[me];
-        if (a.ecache_mode == 1 && s > 0 && c < w) a.ecache[(long)s * nmodes + q] = e_in;
+        // (stride 0: every lane of every CTA stores the same value)
+        if (a.ecache_mode == 1 && s > 0 && c < w)
+            a.ecache[a.ecache_stride ? (long)s * a.ecache_stride + q : (long)s] = e_in;
     }
     // C: pivots (registers) and the affine composite of the forward sweep
     T inv[MAXM];

@@ -110,6 +110,13 @@ class Plan:
                 "cales_helmholtz_solve")
         return out
 
+    def helmholtz_z(self, alpha, f, out=None, stream=None):
+        """(I - alpha L_z) u = f on every (i, j) line (wall-normal implicit step, Eq. 21)."""
+        pf, po, out = self._io(f, out)
+        N.check(N.lib().cales_helmholtz_z_solve(self._h, float(alpha), pf, po, _stream(stream)),
+                "cales_helmholtz_z_solve")
+        return out
+
     def poisson_adjoint(self, w, out=None, stream=None):
         pf, po, out = self._io(w, out)
         N.check(N.lib().cales_poisson_solve_adjoint(self._h, pf, po, _stream(stream)),
@@ -188,6 +195,10 @@ def cales_poisson_solve(plan: Plan, f, p, stream=None):
 
 def cales_helmholtz_solve(plan: Plan, alpha, f, u, stream=None):
     return plan.helmholtz(alpha, f, u, stream)
+
+
+def cales_helmholtz_z_solve(plan: Plan, alpha, f, u, stream=None):
+    plan.helmholtz_z(alpha, f, u, stream)
 
 
 def cales_poisson_solve_adjoint(plan: Plan, w, g, stream=None):

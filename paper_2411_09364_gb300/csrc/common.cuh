@@ -24,14 +24,20 @@ template <typename T> struct cpx { T x, y; };
 template <typename T> __device__ __forceinline__ cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
 template <typename T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+// Products with explicit rounding (no compiler contraction): every kernel
+// variant that runs the same transform steps gets bit-identical results.
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
-    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return mk(fma_(a.x, b.x, -mul_(a.y, b.y)), fma_(a.x, b.y, mul_(a.y, b.x)));
 }
 template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {   // a * conj(b)
-    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    return mk(fma_(a.x, b.x, mul_(a.y, b.y)), fma_(a.y, b.x, -mul_(a.x, b.y)));
 }
 template <typename T> __device__ __forceinline__ cpx<T> conj_(cpx<T> a) { return mk(a.x, -a.y); }
-template <typename T> __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return mk(mul_(a.x, s), mul_(a.y, s)); }
 // multiply by -i (forward) or +i (inverse)
 template <typename T, bool INV> __device__ __forceinline__ cpx<T> rot90(cpx<T> a) {
     return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
@@ -120,7 +126,7 @@ template <typename T, bool INV> struct Bfly<T, 5, INV> {
 // multiply by W16^e = exp(-2 pi i e / 16) (forward) or its conjugate (inverse)
 template <typename T, bool INV> __device__ __forceinline__ cpx<T> w16(cpx<T> a, T wr, T wi) {
     const T w2 = INV ? -wi : wi;
-    return mk(a.x * wr - a.y * w2, a.x * w2 + a.y * wr);
+    return cmul(a, mk(wr, w2));
 }
 
 template <typename T, bool INV> struct Bfly<T, 16, INV> {
@@ -164,11 +170,11 @@ template <typename T, bool INV> struct Bfly<T, 8, INV> {
 #pragma unroll
         for (int r = 0; r < 4; ++r) { a[r] = v[r] + v[r + 4]; b[r] = v[r] - v[r + 4]; }
         // b[r] *= W8^r
-        b[1] = INV ? mk(r2 * (b[1].x - b[1].y), r2 * (b[1].x + b[1].y))
-                   : mk(r2 * (b[1].x + b[1].y), r2 * (b[1].y - b[1].x));
+        b[1] = INV ? mk(mul_(r2, b[1].x - b[1].y), mul_(r2, b[1].x + b[1].y))
+                   : mk(mul_(r2, b[1].x + b[1].y), mul_(r2, b[1].y - b[1].x));
         b[2] = rot90<T, INV>(b[2]);
-        b[3] = INV ? mk(-r2 * (b[3].x + b[3].y), r2 * (b[3].x - b[3].y))
-                   : mk(r2 * (b[3].y - b[3].x), -r2 * (b[3].x + b[3].y));
+        b[3] = INV ? mk(mul_(-r2, b[3].x + b[3].y), mul_(r2, b[3].x - b[3].y))
+                   : mk(mul_(r2, b[3].y - b[3].x), mul_(-r2, b[3].x + b[3].y));
         Bfly<T, 4, INV>::run(a);
         Bfly<T, 4, INV>::run(b);
         v[0] = a[0]; v[2] = a[1]; v[4] = a[2]; v[6] = a[3];
@@ -509,6 +515,11 @@ constexpr long MBAR_MAX_POLLS = 1L << 22;
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+// One line of global memory into L2 (no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* g) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(g));
+}
+
 // Bring [g, g + bytes) into L2 ahead of plain loads (16-byte aligned, size a
 // multiple of 16); no completion to wait for.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* g, uint32_t bytes) {

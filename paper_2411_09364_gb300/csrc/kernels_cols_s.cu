@@ -18,7 +18,15 @@ bool launch_cols_static(const ColArgs<float>& a, bool inverse, cudaStream_t st, 
     if (!static_fft_enabled() || !radices_match(a.t, a.t.L)) return false;
     if (a.t.L == 64 && a.tx == 32) { *err = cols_l<64, 32>(a, inverse, st); return true; }
     if (a.t.L == 128 && a.tx == 32) { *err = cols_l<128, 32>(a, inverse, st); return true; }
-    if (a.t.L == 256 && a.tx == 16) { *err = cols_l<256, 16>(a, inverse, st); return true; }
+    if (a.t.L == 256 && a.tx == 16) {
+        // one-buffer variant (global-memory packing and unpacking)
+        switch (a.t.kind) {
+            case KIND_P: *err = launch_cols_g<256, KIND_P>(a, inverse, st); break;
+            case KIND_N: *err = launch_cols_g<256, KIND_N>(a, inverse, st); break;
+            default: *err = launch_cols_g<256, KIND_D>(a, inverse, st); break;
+        }
+        return true;
+    }
     return false;
 }
 

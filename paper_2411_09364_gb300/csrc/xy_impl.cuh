@@ -416,6 +416,144 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// y direction, one buffer: for L = 16 x LS2 (two passes, the second of radix
+// LS2 <= 16) with TX = 16 columns and 256 threads, every pass has at most one
+// butterfly per thread, so both passes run in place (read, barrier, write) in
+// a single shared-memory buffer.  The natural-order column data never enters
+// shared memory: the first forward pass packs it straight from global memory
+// (rows prefetched into L2 at the start) and the post-processing writes the
+// result rows to global memory; the inverse reads its input rows in the
+// pre-processing and its last pass unpacks straight to global memory.
+// Shared memory: [buffer L x 16 complex | tables] ~ 38 KB for L = 256.
+// ---------------------------------------------------------------------------
+template <int LS, int KS, bool INV>
+__global__ void __launch_bounds__(256) k_cols_g(ColArgs<float> a) {
+    constexpr int TX = 16, R1 = 16, R2 = LS / 16, NB1 = LS / R1, NB2 = LS / R2, n = 2 * LS;
+    static_assert(sf_nrad(LS) == 2 && sf_radix(LS, 0) == 16 && NB1 * TX <= 256 && NB2 * TX <= 256, "shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DirTab<float>& t = a.t;
+    const int nx = a.nx;
+    const int tiles_x = (nx + TX - 1) / TX;
+    const int plane = blockIdx.x / tiles_x;
+    const int x0 = (blockIdx.x - plane * tiles_x) * TX;
+    const int wx = min(TX, nx - x0);
+    const int tid = threadIdx.x;
+    float* __restrict__ base = reinterpret_cast<float*>(a.data) + (long)plane * n * nx + x0;
+    cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* tw_s = buf + LS * TX;
+    const cpx<float>* pst = tw_s + t.twlen;
+    const cpx<float>* mkt = tw_s + t.twlen + LS + 1;
+    const int c = tid & (TX - 1);
+    const bool live = c < wx;
+    for (int s = tid; s < n; s += blockDim.x) prefetch_l2(base + (long)s * nx);
+    stage_twiddles(tw_s, t);
+    __syncthreads();
+    const cpx<float>* tp2 = tw_s + t.twoff[1];
+    if (!INV) {
+        // pass 1 (radix 16, Ns = 1): pack the natural rows from global memory
+        {
+            const int j = tid / TX;
+            cpx<float> v[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int q = j + r * NB1;
+                const int s0 = unpack_src(KS, n, 2 * q), s1 = unpack_src(KS, n, 2 * q + 1);
+                v[r] = live ? mk(base[(long)s0 * nx + c] * pack_sign<float>(KS, s0),
+                                 base[(long)s1 * nx + c] * pack_sign<float>(KS, s1))
+                            : mk(0.f, 0.f);
+            }
+            Bfly<float, R1, false>::run(v);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) buf[(j * R1 + r) * TX + c] = v[r];
+        }
+        __syncthreads();
+        // pass 2 (radix LS/16, Ns = 16) in place
+        {
+            const int j = tid / TX, k = j & 15;
+            const bool act = j < NB2;
+            cpx<float> v[R2];
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) v[r] = buf[(j + r * NB2) * TX + c];
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], tp2[(r - 1) * 16 + k]);
+                Bfly<float, R2, false>::run(v);
+                const int b0 = (j - k) * R2 + k;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) buf[(b0 + r * 16) * TX + c] = v[r];
+            }
+        }
+        __syncthreads();
+        // post-processing of the mode pairs straight to the global rows
+        const int half = LS / 2 + 1;
+        for (int idx = tid; idx < half * TX; idx += blockDim.x) {
+            const int m = idx / TX, cc = idx - m * TX;
+            if (cc < wx) post_forward_pair<float, LS, KS>(buf + cc, TX, base + cc, nx, t, pst, mkt, m);
+        }
+    } else {
+        // pre-processing from the global rows
+        const int half = LS / 2 + 1;
+        for (int idx = tid; idx < half * TX; idx += blockDim.x) {
+            const int m = idx / TX, cc = idx - m * TX;
+            if (cc < wx) {
+                pre_inverse_pair<float, LS, KS>(base + cc, nx, buf + cc, TX, t, pst, mkt, m);
+            } else {
+                buf[m * TX + cc] = mk(0.f, 0.f);
+                if (LS - m != m && LS - m < LS) buf[(LS - m) * TX + cc] = mk(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        // pass 1 (radix 16, Ns = 1) in place
+        {
+            const int j = tid / TX;
+            cpx<float> v[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[r] = buf[(j + r * NB1) * TX + c];
+            __syncthreads();
+            Bfly<float, R1, true>::run(v);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) buf[(j * R1 + r) * TX + c] = v[r];
+        }
+        __syncthreads();
+        // pass 2 (radix LS/16, Ns = 16): unpack straight to the global rows
+        {
+            const int j = tid / TX, k = j & 15;
+            if (j < NB2) {
+                cpx<float> v[R2];
+#pragma unroll
+                for (int r = 0; r < R2; ++r) v[r] = buf[(j + r * NB2) * TX + c];
+#pragma unroll
+                for (int r = 1; r < R2; ++r) v[r] = cmulc(v[r], tp2[(r - 1) * 16 + k]);
+                Bfly<float, R2, true>::run(v);
+                const int b0 = (j - k) * R2 + k;
+                if (live) {
+#pragma unroll
+                    for (int r = 0; r < R2; ++r) {
+                        const int q = b0 + r * 16;
+                        const int s0 = unpack_src(KS, n, 2 * q), s1 = unpack_src(KS, n, 2 * q + 1);
+                        base[(long)s0 * nx + c] = v[r].x * pack_sign<float>(KS, s0);
+                        base[(long)s1 * nx + c] = v[r].y * pack_sign<float>(KS, s1);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int LS, int KS>
+cudaError_t launch_cols_g(const ColArgs<float>& a, bool inverse, cudaStream_t st) {
+    const size_t sm = (size_t)LS * 16 * sizeof(cpx<float>) + (size_t)table_len(a.t.twlen, LS, KS) * sizeof(cpx<float>);
+    const unsigned grid = (unsigned)(a.nplanes * ((a.nx + 15) / 16));
+    auto kern = inverse ? k_cols_g<LS, KS, true> : k_cols_g<LS, KS, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<grid, 256, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
 // The compile-time-size kernels assume the plan factorised L as sf_radix does.
 template <typename T> inline bool radices_match(const DirTab<T>& t, int L) {
     if (t.L != L || t.nrad != sf_nrad(L)) return false;

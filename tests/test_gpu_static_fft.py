@@ -28,6 +28,9 @@ CASES = [
     (512, 256, 20, (0, 0, 1, 1, 1, 1)),
     (1536, 512, 8, (0, 0, 2, 2, 2, 1)),
     (512, 128, 16, (0, 0, 2, 2, 1, 1)),
+    (64, 512, 6, (0, 0, 0, 0, 1, 1)),      # y n = 512 periodic: the one-buffer column kernel
+    (96, 512, 5, (0, 0, 1, 1, 1, 1)),      # y n = 512 cosine
+    (40, 512, 4, (0, 0, 2, 2, 2, 2)),      # y n = 512 sine, a partial 16-column tile
 ]
 MODES = [cs.FP32, cs.FP32_REFINE]
 

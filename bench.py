@@ -253,6 +253,27 @@ def run_configs(args):
               "hbm_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
     del fz, plan
     torch.cuda.empty_cache()
+    # Smagorinsky / van Driest eddy viscosity (Eq. 4) on a channel of the bench size
+    w = WORKLOAD
+    zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
+    dzc, dzf = cs.cell_spacings(zf)
+    plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
+                   cs.FP64)
+    shp = (w["nz"], w["ny"], w["nx"])
+    for mode, name in ((cs.FP32, "fp32"), (cs.FP64, "fp64")):
+        plan.set_precision(mode)
+        dt = torch.float32 if mode == cs.FP32 else torch.float64
+        uu = torch.from_numpy(S.gaussian(6000, shp)).to(dev, dt)
+        vv = torch.from_numpy(S.gaussian(6001, shp)).to(dev, dt)
+        ww = torch.zeros((w["nz"] + 1, w["ny"], w["nx"]), dtype=dt, device=dev)
+        nt = torch.empty_like(uu)
+        ms = timed(lambda: plan.eddy_viscosity(0.1, 1e-4, 0.05, uu, vv, ww, nt), 10)
+        emit({"workload": f"eddy_viscosity_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
+              "gpoints_per_s": uu.numel() / ms / 1e6,
+              "hbm_frac": (uu.numel() * 4 * uu.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+        del uu, vv, ww, nt
+    del plan
+    torch.cuda.empty_cache()
     # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
     plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
     fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)

@@ -173,6 +173,23 @@ int cales_divergence_adjoint(cales_plan_t plan, const void* d, const void* uin, 
 int cales_gradient_adjoint(cales_plan_t plan, const void* gx, const void* gy, const void* gz, void* phi, void* stream);
 
 /*
+ * Smagorinsky eddy viscosity with van Driest damping, Eq. 4 (Sec. 2.1; model
+ * evaluated at the cell centres, Sec. 2.2): nu_t = (cs Delta D)^2 |S| with
+ * |S| = sqrt(2 S_ij S_ij), D = 1 - exp(-y+/25).  Same plans and layouts as
+ * the projection operators above (periodic x and y, walls in z); u, v, w
+ * are the staggered velocity, nut is written at the cell centres [nz][ny][nx].
+ * The diagonal strain rates are formed at the centres, the off-diagonal ones
+ * on the four surrounding cell edges and averaged to the centre; u and v
+ * take no-slip ghosts (minus the first interior value, at the mirror
+ * distances dzc[0], dzc[nz]) and w is zero on the wall faces.  Filter width
+ * Delta = (dx dy dzf_k)^(1/3); y+ = (distance of the centre to the nearer
+ * wall) * utau / nu.  cs >= 0, nu > 0, utau >= 0.  FP32 plans compute in
+ * FP32 (float arrays), the others in FP64 (double arrays).
+ */
+int cales_eddy_viscosity(cales_plan_t plan, double cs, double nu, double utau, const void* u, const void* v,
+                         const void* w, void* nut, void* stream);
+
+/*
  * Learned closure trained through the projection (the paper motivates
  * machine-learned closures built on the solver, Sec. 1).  FP32, plan layout
  * as above.  theta: device [3][27] taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1).

@@ -24,6 +24,7 @@ SIGNATURES = {
     "cales_poisson_solve": (C.c_int, [vp, vp, vp, vp]),
     "cales_helmholtz_solve": (C.c_int, [vp, C.c_double, vp, vp, vp]),
     "cales_helmholtz_z_solve": (C.c_int, [vp, C.c_double, vp, vp, vp]),
+    "cales_eddy_viscosity": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, vp]),
     "cales_poisson_solve_adjoint": (C.c_int, [vp, vp, vp, vp]),
     "cales_poisson_solve_noalloc": (C.c_int, [vp, vp, vp, vp]),
     "cales_helmholtz_solve_adjoint": (C.c_int, [vp, C.c_double, vp, vp, vp]),

@@ -3,6 +3,8 @@
 #include "kernels.cuh"
 #include "plan.h"
 
+#include <cmath>
+
 
 
 using namespace cales;
@@ -21,10 +23,40 @@ template <typename T> static GridArgs<T> gargs(cales_plan_t P) {
     return g;
 }
 
+template <typename T>
+static SgsArgs<T> sgs_args(cales_plan_t P, double cs, double nu, double utau, const void* u, const void* v,
+                           const void* w, void* nut) {
+    SgsArgs<T> a;
+    a.u = (const T*)u; a.v = (const T*)v; a.w = (const T*)w; a.nut = (T*)nut;
+    a.nx = P->nx; a.ny = P->ny; a.nz = P->nz;
+    a.idx = T(1.0 / P->dx);
+    a.idy = T(1.0 / P->dy);
+    a.idzf = sizeof(T) == 8 ? (const T*)P->idzf_d : (const T*)P->idzf_f;
+    a.idzc = sizeof(T) == 8 ? (const T*)P->idzc_d : (const T*)P->idzc_f;
+    a.zcen = P->zcen_d;
+    a.dzf = P->dzf_d;
+    a.lz = P->dzf_sum; a.dx = P->dx; a.dy = P->dy;
+    a.cs = cs; a.nu = nu; a.utau = utau;
+    return a;
+}
+
 #define CALES_DISPATCH(P, CALL_D, CALL_F) \
     ((P)->precision == CALES_FP32 ? (CALL_F) : (CALL_D))
 
 extern "C" {
+
+int cales_eddy_viscosity(cales_plan_t P, double cs, double nu, double utau, const void* u, const void* v,
+                         const void* w, void* nut, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (!u || !v || !w || !nut || !(cs >= 0.0) || !(nu > 0.0) || !(utau >= 0.0) || !std::isfinite(cs) ||
+        !std::isfinite(nu) || !std::isfinite(utau))
+        return CALES_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (P->precision == CALES_FP32) e = launch_eddy_viscosity<float>(sgs_args<float>(P, cs, nu, utau, u, v, w, nut), st);
+    else e = launch_eddy_viscosity<double>(sgs_args<double>(P, cs, nu, utau, u, v, w, nut), st);
+    return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
 
 int cales_divergence(cales_plan_t P, const void* u, const void* v, const void* w, void* d, void* stream) {
     if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;

@@ -101,6 +101,21 @@ struct ResidFFArgs {
     int rows_per_cta;    // set by the launcher
 };
 
+// Smagorinsky / van Driest eddy viscosity at the cell centres of a channel.
+template <typename T> struct SgsArgs {
+    const T* u;          // x-faces [nz][ny][nx]
+    const T* v;          // y-faces [nz][ny][nx]
+    const T* w;          // z-faces [nz+1][ny][nx], w[0] = w[nz] = 0
+    T* nut;              // centres [nz][ny][nx]
+    int nx, ny, nz;
+    T idx, idy;
+    const T* idzf;       // 1/dzf [nz]
+    const T* idzc;       // 1/dzc [nz+1]
+    const double* zcen;  // cell-centre heights [nz] (bottom wall at 0)
+    const double* dzf;   // [nz]
+    double lz, dx, dy, cs, nu, utau;
+};
+
 enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
 
 template <typename T, typename TIn> cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st);
@@ -119,6 +134,7 @@ template <typename T> size_t zsolve_smem(int nz, int tm, int P);
 template <typename T> size_t zsolve_reg_smem(int nz, int tm, int P);
 template <typename T> size_t zsolve_w_smem(int nz, int P);
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
+template <typename T> cudaError_t launch_eddy_viscosity(const SgsArgs<T>& a, cudaStream_t st);
 cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st);
 
 // ---- projection operators and learned-closure kernels ----

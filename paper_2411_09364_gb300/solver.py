@@ -117,6 +117,19 @@ class Plan:
                 "cales_helmholtz_z_solve")
         return out
 
+    def eddy_viscosity(self, cs, nu, utau, u, v, w, out=None, stream=None):
+        """Smagorinsky / van Driest eddy viscosity at the cell centres (Eq. 4)."""
+        n = self.numel
+        nw = self.nx * self.ny * (self.nz + 1)
+        pu, pv = _ptr(u, self.dtype, n, "u"), _ptr(v, self.dtype, n, "v")
+        pw = _ptr(w, self.dtype, nw, "w")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=u.device)
+        po = _ptr(out, self.dtype, n, "out")
+        N.check(N.lib().cales_eddy_viscosity(self._h, float(cs), float(nu), float(utau), pu, pv, pw, po,
+                                             _stream(stream)), "cales_eddy_viscosity")
+        return out
+
     def poisson_adjoint(self, w, out=None, stream=None):
         pf, po, out = self._io(w, out)
         N.check(N.lib().cales_poisson_solve_adjoint(self._h, pf, po, _stream(stream)),

@@ -195,96 +195,107 @@ def run_configs(args):
     def emit(d):
         print(json.dumps(d), flush=True)
 
-    # channel 64x32x32, P,P,N, uniform z, FP64: fits L2, latency-bound
-    plan = cs.channel_plan(64, 32, 32, beta=0.0)
-    f = torch.from_numpy(S.gaussian(1000, (32, 32, 64))).to(dev)
-    p = torch.empty_like(f)
-    ms = timed(lambda: plan.poisson(f, p), 200)
-    emit({"workload": "channel_poisson_64x32x32", "mode": "fp64", "ms": ms, "solves_per_s": 1e3 / ms,
-          "gpoints_per_s": f.numel() / ms / 1e6, "l2": "fits L2 (warm)"})
-    # channel 512x256x192, P,P,N, tanh beta = 1.8
-    plan = cs.channel_plan(512, 256, 192, beta=1.8)
-    f64 = torch.from_numpy(S.gaussian(2000, (192, 256, 512))).to(dev)
-    out = {}
-    for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
-        plan.set_precision(mode, 2)
-        fi = f64 if mode != cs.FP32 else f64.float()
-        po = torch.empty_like(fi)
-        ms = timed(lambda: plan.poisson(fi, po), 20)
-        out[name] = po.double()
-        rel = (float(torch.linalg.vector_norm(out[name] - out["fp64"]) / torch.linalg.vector_norm(out["fp64"]))
-               if name != "fp64" else 0.0)
-        emit({"workload": "channel_poisson_512x256x192", "mode": name, "ms": ms,
-              "gpoints_per_s": fi.numel() / ms / 1e6, "rel_err_vs_fp64_gpu": rel,
-              "min_traffic_roofline_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
-    # 16 channel domains x {u, v, w Helmholtz, p Poisson}, FP32 + refinement, one CUDA graph
-    alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
-    batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
-    fs = [torch.from_numpy(S.gaussian(4000 + i, pl.shape)).to(dev) for i, pl in enumerate(plans)]
-    us = [torch.empty_like(x) for x in fs]
-    st = batch.capture(fs, us)
-    for _ in range(3):
-        batch.launch(st)
-    st.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    for _ in range(10):
-        batch.launch(st)
-    b.record(st)
-    st.synchronize()
-    ms = a.elapsed_time(b) / 10
-    pts = sum(pl.numel for pl in plans)
-    emit({"workload": "rk3_substep_16_channel_domains", "mode": "fp32_refine", "ms": ms,
-          "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
-    # wall-normal implicit line solves (Eq. 21) on the bench grid, Dirichlet walls
-    w = WORKLOAD
-    zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
-    dzc, dzf = cs.cell_spacings(zf)
-    plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 1, 1, 2, 2), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
-                   cs.FP64)
-    fz = torch.from_numpy(make_rhs(w["nx"], w["ny"], w["nz"], zf, w["seed"])).to(dev)
-    for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32")):
-        plan.set_precision(mode)
-        fi = fz if mode == cs.FP64 else fz.float()
-        uo = torch.empty_like(fi)
-        ms = timed(lambda: plan.helmholtz_z(1e-4, fi, uo), 10)
-        emit({"workload": f"z_line_helmholtz_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
-              "gpoints_per_s": fi.numel() / ms / 1e6,
-              "hbm_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
-    del fz, plan
-    torch.cuda.empty_cache()
-    # Smagorinsky / van Driest eddy viscosity (Eq. 4) on a channel of the bench size
-    w = WORKLOAD
-    zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
-    dzc, dzf = cs.cell_spacings(zf)
-    plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
-                   cs.FP64)
-    shp = (w["nz"], w["ny"], w["nx"])
-    for mode, name in ((cs.FP32, "fp32"), (cs.FP64, "fp64")):
-        plan.set_precision(mode)
-        dt = torch.float32 if mode == cs.FP32 else torch.float64
-        uu = torch.from_numpy(S.gaussian(6000, shp)).to(dev, dt)
-        vv = torch.from_numpy(S.gaussian(6001, shp)).to(dev, dt)
-        ww = torch.zeros((w["nz"] + 1, w["ny"], w["nx"]), dtype=dt, device=dev)
-        nt = torch.empty_like(uu)
-        ms = timed(lambda: plan.eddy_viscosity(0.1, 1e-4, 0.05, uu, vv, ww, nt), 10)
-        emit({"workload": f"eddy_viscosity_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
-              "gpoints_per_s": uu.numel() / ms / 1e6,
-              "hbm_frac": (uu.numel() * 4 * uu.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
-        del uu, vv, ww, nt
-    del plan
-    torch.cuda.empty_cache()
-    # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
-    plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
-    fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)
-    wd = torch.from_numpy(S.gaussian(5001, (128, 128, 256))).to(dev, torch.float32)
+    def want(tag):
+        return args.only is None or args.only in tag
 
-    def fwd_bwd():
-        fd.grad = None
-        (wd * AG.poisson_solve(fd, plan)).sum().backward()
-    ms = timed(fwd_bwd, 20)
-    emit({"workload": "differentiable_poisson_256x128x128", "mode": "fp32 forward+backward", "ms": ms,
-          "gpoints_per_s": fd.numel() / ms / 1e6})
+    if want("channel_poisson_64x32x32"):
+        # channel 64x32x32, P,P,N, uniform z, FP64: fits L2, latency-bound
+        plan = cs.channel_plan(64, 32, 32, beta=0.0)
+        f = torch.from_numpy(S.gaussian(1000, (32, 32, 64))).to(dev)
+        p = torch.empty_like(f)
+        ms = timed(lambda: plan.poisson(f, p), 200)
+        emit({"workload": "channel_poisson_64x32x32", "mode": "fp64", "ms": ms, "solves_per_s": 1e3 / ms,
+              "gpoints_per_s": f.numel() / ms / 1e6, "l2": "fits L2 (warm)"})
+    if want("channel_poisson_512x256x192"):
+        # channel 512x256x192, P,P,N, tanh beta = 1.8
+        plan = cs.channel_plan(512, 256, 192, beta=1.8)
+        f64 = torch.from_numpy(S.gaussian(2000, (192, 256, 512))).to(dev)
+        out = {}
+        for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
+            plan.set_precision(mode, 2)
+            fi = f64 if mode != cs.FP32 else f64.float()
+            po = torch.empty_like(fi)
+            ms = timed(lambda: plan.poisson(fi, po), 20)
+            out[name] = po.double()
+            rel = (float(torch.linalg.vector_norm(out[name] - out["fp64"]) / torch.linalg.vector_norm(out["fp64"]))
+                   if name != "fp64" else 0.0)
+            emit({"workload": "channel_poisson_512x256x192", "mode": name, "ms": ms,
+                  "gpoints_per_s": fi.numel() / ms / 1e6, "rel_err_vs_fp64_gpu": rel,
+                  "min_traffic_roofline_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+    if want("rk3_substep"):
+        # 16 channel domains x {u, v, w Helmholtz, p Poisson}, FP32 + refinement, one CUDA graph
+        alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
+        batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
+        fs = [torch.from_numpy(S.gaussian(4000 + i, pl.shape)).to(dev) for i, pl in enumerate(plans)]
+        us = [torch.empty_like(x) for x in fs]
+        st = batch.capture(fs, us)
+        for _ in range(3):
+            batch.launch(st)
+        st.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(10):
+            batch.launch(st)
+        b.record(st)
+        st.synchronize()
+        ms = a.elapsed_time(b) / 10
+        pts = sum(pl.numel for pl in plans)
+        emit({"workload": "rk3_substep_16_channel_domains", "mode": "fp32_refine", "ms": ms,
+              "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
+    if want("z_line_helmholtz"):
+        # wall-normal implicit line solves (Eq. 21) on the bench grid, Dirichlet walls
+        w = WORKLOAD
+        zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
+        dzc, dzf = cs.cell_spacings(zf)
+        plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 1, 1, 2, 2), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
+                       cs.FP64)
+        fz = torch.from_numpy(make_rhs(w["nx"], w["ny"], w["nz"], zf, w["seed"])).to(dev)
+        for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32")):
+            plan.set_precision(mode)
+            fi = fz if mode == cs.FP64 else fz.float()
+            uo = torch.empty_like(fi)
+            ms = timed(lambda: plan.helmholtz_z(1e-4, fi, uo), 10)
+            emit({"workload": f"z_line_helmholtz_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
+                  "gpoints_per_s": fi.numel() / ms / 1e6,
+                  "hbm_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+        del fz, plan
+        torch.cuda.empty_cache()
+    if want("eddy_viscosity"):
+        # Smagorinsky / van Driest eddy viscosity (Eq. 4) on a channel of the bench size
+        w = WORKLOAD
+        zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
+        dzc, dzf = cs.cell_spacings(zf)
+        plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
+                       cs.FP64)
+        shp = (w["nz"], w["ny"], w["nx"])
+        for mode, name in ((cs.FP32, "fp32"), (cs.FP64, "fp64")):
+            plan.set_precision(mode)
+            dt = torch.float32 if mode == cs.FP32 else torch.float64
+            uu = torch.from_numpy(S.gaussian(6000, shp)).to(dev, dt)
+            vv = torch.from_numpy(S.gaussian(6001, shp)).to(dev, dt)
+            ww = torch.from_numpy(S.gaussian(6002, (w["nz"] + 1, w["ny"], w["nx"]))).to(dev, dt)
+            ww[0].zero_()
+            ww[-1].zero_()
+            nt = torch.empty_like(uu)
+            ms = timed(lambda: plan.eddy_viscosity(0.1, 1e-4, 0.05, uu, vv, ww, nt), 10)
+            emit({"workload": f"eddy_viscosity_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
+                  "gpoints_per_s": uu.numel() / ms / 1e6,
+                  "hbm_frac": (uu.numel() * 4 * uu.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
+            del uu, vv, ww, nt
+        del plan
+        torch.cuda.empty_cache()
+    if want("differentiable_poisson"):
+        # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
+        plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
+        fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)
+        wd = torch.from_numpy(S.gaussian(5001, (128, 128, 256))).to(dev, torch.float32)
+
+        def fwd_bwd():
+            fd.grad = None
+            (wd * AG.poisson_solve(fd, plan)).sum().backward()
+        ms = timed(fwd_bwd, 20)
+        emit({"workload": "differentiable_poisson_256x128x128", "mode": "fp32 forward+backward", "ms": ms,
+              "gpoints_per_s": fd.numel() / ms / 1e6})
 
 
 def main():
@@ -299,6 +310,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="512x256x192 channel variant (profiling)")
     ap.add_argument("--shape", default=None, help="NX,NY,NZ: the duct at another size (profiling case)")
     ap.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each)")
+    ap.add_argument("--only", default=None, help="with --configs: only the workloads whose name contains this")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

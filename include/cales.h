@@ -184,7 +184,13 @@ int cales_gradient_adjoint(cales_plan_t plan, const void* gx, const void* gy, co
  * distances dzc[0], dzc[nz]) and w is zero on the wall faces.  Filter width
  * Delta = (dx dy dzf_k)^(1/3); y+ = (distance of the centre to the nearer
  * wall) * utau / nu.  cs >= 0, nu > 0, utau >= 0.  FP32 plans compute in
- * FP32 (float arrays), the others in FP64 (double arrays).
+ * FP32 (float arrays), the others in FP64 (double arrays).  The per-plane
+ * coefficients (cs Delta D)^2 go through a plan-owned scratch array, so one
+ * plan serves one eddy-viscosity call at a time (like its solves).  Arrays
+ * 16-byte aligned with nx a multiple of 4 (FP32) / 2 (FP64) take vector
+ * loads; any other alignment is served by a scalar kernel.  Returns
+ * CALES_EINVAL for NULL arrays or parameters out of range, CALES_ECUDA when
+ * the launch fails (nz > 65535 included).
  */
 int cales_eddy_viscosity(cales_plan_t plan, double cs, double nu, double utau, const void* u, const void* v,
                          const void* w, void* nut, void* stream);

@@ -35,6 +35,7 @@ static SgsArgs<T> sgs_args(cales_plan_t P, double cs, double nu, double utau, co
     a.idzc = sizeof(T) == 8 ? (const T*)P->idzc_d : (const T*)P->idzc_f;
     a.zcen = P->zcen_d;
     a.dzf = P->dzf_d;
+    a.coef = P->sgs_coef;
     a.lz = P->dzf_sum; a.dx = P->dx; a.dy = P->dy;
     a.cs = cs; a.nu = nu; a.utau = utau;
     return a;

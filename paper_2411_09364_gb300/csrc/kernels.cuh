@@ -113,6 +113,7 @@ template <typename T> struct SgsArgs {
     const T* idzc;       // 1/dzc [nz+1]
     const double* zcen;  // cell-centre heights [nz] (bottom wall at 0)
     const double* dzf;   // [nz]
+    double* coef;        // [nz] scratch: (C_s Delta D)^2 per plane
     double lz, dx, dy, cs, nu, utau;
 };
 

@@ -6,90 +6,157 @@
 // width Delta_k = (dx dy dzf_k)^(1/3); y* = (distance of the centre to the
 // nearer wall) u_tau / nu.  No-slip ghosts: u and v mirror to minus the first
 // interior value at the distances dzc[0] and dzc[nz]; w = 0 on the wall faces.
-// One thread per cell; a CTA covers part of one z-plane and forms that plane's
-// coefficient (C_s Delta D)^2 once, in FP64.
+//
+// Two launches: the plane coefficients (C_s Delta D)^2 in FP64 (nz threads),
+// then one thread per VW consecutive cells of an x-row, reading each of the
+// 17 neighbouring rows of u, v, w it needs as one 16-byte vector (plus a
+// scalar at either end where the stencil reaches i-1 or i+VW).  The sum of
+// the four edge values of S_ij is formed from differences before scaling:
+// 8 S_12 = (du/dy summed over the two x-faces) + (dv/dx over the two y-faces),
+// and likewise for S_13 and S_23 with the z spacing below and above; the
+// x-differences are shared by a thread's neighbouring cells.  Each CTA hints
+// plane k+2 into L2, so the demand loads of a plane find it there.
 #include "kernels.cuh"
 
 namespace cales {
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_eddy_visc(SgsArgs<T> a) {
-    const int k = blockIdx.y;
-    __shared__ T coef_s;
-    if (threadIdx.x == 0) {
-        const double zc = a.zcen[k];
-        const double d = fmin(zc, a.lz - zc);
-        const double damp = 1.0 - exp(-d * a.utau / (25.0 * a.nu));
-        const double c = a.cs * cbrt(a.dx * a.dy * a.dzf[k]) * damp;
-        coef_s = T(c * c);
+__global__ void k_sgs_coef(double* __restrict__ coef, const double* __restrict__ zcen,
+                           const double* __restrict__ dzf, int nz, double lz, double dx, double dy,
+                           double cs, double nu, double utau) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nz) return;
+    const double d = fmin(zcen[k], lz - zcen[k]);
+    const double damp = 1.0 - exp(-d * utau / (25.0 * nu));
+    const double c = cs * cbrt(dx * dy * dzf[k]) * damp;
+    coef[k] = c * c;
+}
+
+// x[1 .. VW] = row[i0 .. i0+VW-1]  (16-byte vector for VW > 1)
+template <typename T, int VW>
+__device__ __forceinline__ void sgs_load_mid(T* x, const T* __restrict__ row, int i0) {
+    if constexpr (VW == 1) {
+        x[1] = row[i0];
+    } else if constexpr (VW == 2) {
+        const double2 q = *reinterpret_cast<const double2*>(row + i0);
+        x[1] = q.x; x[2] = q.y;
+    } else {
+        const float4 q = *reinterpret_cast<const float4*>(row + i0);
+        x[1] = q.x; x[2] = q.y; x[3] = q.z; x[4] = q.w;
     }
-    __syncthreads();
-    const T coef = coef_s;
+}
+
+// x[0] = row[i0-1], x[1 .. VW] = row[i0 ..], x[VW+1] = row[i0+VW] (periodic in x);
+// the ends only where the stencil needs them
+template <typename T, int VW, bool LEFT, bool RIGHT>
+__device__ __forceinline__ void sgs_load_row(T* x, const T* __restrict__ row, int i0, int im, int ip) {
+    sgs_load_mid<T, VW>(x, row, i0);
+    if constexpr (LEFT) x[0] = row[im];
+    if constexpr (RIGHT) x[VW + 1] = row[ip];
+}
+
+template <typename T, int VW>
+__global__ void __launch_bounds__(256) k_eddy_visc(SgsArgs<T> a) {
+    const int k = blockIdx.z;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long plane = (long)nx * ny;
-    const T idx = a.idx, idy = a.idy;
-    const T idzf = a.idzf[k], izlo = a.idzc[k], izhi = a.idzc[k + 1];
-    const T h = T(0.5), q = T(0.25);
-    const T* __restrict__ u = a.u;
-    const T* __restrict__ v = a.v;
-    const T* __restrict__ w = a.w;
-    const long kb = (long)k * plane;
-    const long kd = k > 0 ? kb - plane : -1, ku = k < nz - 1 ? kb + plane : -1;   // -1: the wall ghost
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nx), i = (int)(e - (long)j * nx);
-        const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-        const int jm = j > 0 ? j - 1 : ny - 1, jp = j < ny - 1 ? j + 1 : 0;
-        const long r0 = (long)j * nx, rm = (long)jm * nx, rp = (long)jp * nx;
-        // u at (j-1, j, j+1) x (i-1, i) of plane k; v at (j-1, j) x (i-1, i, i+1)
-        const T u_c = u[kb + r0 + i], u_w = u[kb + r0 + im];
-        const T u_s = u[kb + rm + i], u_sw = u[kb + rm + im], u_n = u[kb + rp + i], u_nw = u[kb + rp + im];
-        const T v_c = v[kb + r0 + i], v_s = v[kb + rm + i];
-        const T v_w = v[kb + r0 + im], v_sw = v[kb + rm + im], v_e = v[kb + r0 + ip], v_se = v[kb + rm + ip];
-        // z neighbours of u (i-1, i) and v (j-1, j), wall ghosts -value
-        const T u_d = kd >= 0 ? u[kd + r0 + i] : -u_c, u_dw = kd >= 0 ? u[kd + r0 + im] : -u_w;
-        const T u_u = ku >= 0 ? u[ku + r0 + i] : -u_c, u_uw = ku >= 0 ? u[ku + r0 + im] : -u_w;
-        const T v_d = kd >= 0 ? v[kd + r0 + i] : -v_c, v_ds = kd >= 0 ? v[kd + rm + i] : -v_s;
-        const T v_u = ku >= 0 ? v[ku + r0 + i] : -v_c, v_us = ku >= 0 ? v[ku + rm + i] : -v_s;
-        // w on the faces k (below) and k+1 (above): (i-1, i, i+1) at j and (j-1, j+1) at i
-        const long wb = kb, wa = kb + plane;
-        const T wb_c = w[wb + r0 + i], wb_w = w[wb + r0 + im], wb_e = w[wb + r0 + ip];
-        const T wb_s = w[wb + rm + i], wb_n = w[wb + rp + i];
-        const T wa_c = w[wa + r0 + i], wa_w = w[wa + r0 + im], wa_e = w[wa + r0 + ip];
-        const T wa_s = w[wa + rm + i], wa_n = w[wa + rp + i];
-        // diagonal components at the centre
-        const T s11 = (u_c - u_w) * idx;
-        const T s22 = (v_c - v_s) * idy;
-        const T s33 = (wa_c - wb_c) * idzf;
-        // S12 on the four z-edges around the centre
-        const T e11 = h * ((u_n - u_c) * idy + (v_e - v_c) * idx);
-        const T e01 = h * ((u_nw - u_w) * idy + (v_c - v_w) * idx);
-        const T e10 = h * ((u_c - u_s) * idy + (v_se - v_s) * idx);
-        const T e00 = h * ((u_w - u_sw) * idy + (v_s - v_sw) * idx);
-        const T s12 = q * (e00 + e10 + e01 + e11);
-        // S13 on the y-edges (x-face i-1/2, i+1/2) x (z-face k, k+1)
-        const T f_i_lo = h * ((u_c - u_d) * izlo + (wb_e - wb_c) * idx);
-        const T f_i_hi = h * ((u_u - u_c) * izhi + (wa_e - wa_c) * idx);
-        const T f_w_lo = h * ((u_w - u_dw) * izlo + (wb_c - wb_w) * idx);
-        const T f_w_hi = h * ((u_uw - u_w) * izhi + (wa_c - wa_w) * idx);
-        const T s13 = q * (f_i_lo + f_i_hi + f_w_lo + f_w_hi);
-        // S23 on the x-edges (y-face j-1/2, j+1/2) x (z-face k, k+1)
-        const T g_j_lo = h * ((v_c - v_d) * izlo + (wb_n - wb_c) * idy);
-        const T g_j_hi = h * ((v_u - v_c) * izhi + (wa_n - wa_c) * idy);
-        const T g_s_lo = h * ((v_s - v_ds) * izlo + (wb_c - wb_s) * idy);
-        const T g_s_hi = h * ((v_us - v_s) * izhi + (wa_c - wa_s) * idy);
-        const T s23 = q * (g_j_lo + g_j_hi + g_s_lo + g_s_hi);
-        const T ss = s11 * s11 + s22 * s22 + s33 * s33 + T(2) * (s12 * s12 + s13 * s13 + s23 * s23);
-        a.nut[kb + e] = coef * sqrt(T(2) * ss);
+    if (j >= ny || i0 >= nx) return;
+    const size_t plane = (size_t)nx * ny;
+    const int im = i0 > 0 ? i0 - 1 : nx - 1, ip = i0 + VW < nx ? i0 + VW : 0;
+    const int jm = j > 0 ? j - 1 : ny - 1, jp = j < ny - 1 ? j + 1 : 0;
+    const size_t r0 = (size_t)j * nx, rs = (size_t)jm * nx, rn = (size_t)jp * nx;
+    const T* __restrict__ u = a.u + (size_t)k * plane;
+    const T* __restrict__ v = a.v + (size_t)k * plane;
+    const T* __restrict__ wb = a.w + (size_t)k * plane;     // face below the centre
+    const T* __restrict__ wa = wb + plane;                  // face above
+    constexpr int N = VW + 2;
+    // u: centre row j and rows j-1, j+1 (i-1 .. i); z neighbours of row j
+    T uc[N], us[N], un[N], ud[N], uu[N];
+    // v: rows j and j-1 (i-1 .. i+1); their z neighbours (i only)
+    T vc[N], vs[N], vd[N], vds[N], vu[N], vus[N];
+    // w below / above: row j (i-1 .. i+1) and rows j-1, j+1 (i only)
+    T bc[N], bs[N], bn[N], ac[N], as[N], an[N];
+    sgs_load_row<T, VW, true, false>(uc, u + r0, i0, im, ip);
+    sgs_load_row<T, VW, true, false>(us, u + rs, i0, im, ip);
+    sgs_load_row<T, VW, true, false>(un, u + rn, i0, im, ip);
+    sgs_load_row<T, VW, true, true>(vc, v + r0, i0, im, ip);
+    sgs_load_row<T, VW, true, true>(vs, v + rs, i0, im, ip);
+    sgs_load_row<T, VW, true, true>(bc, wb + r0, i0, im, ip);
+    sgs_load_row<T, VW, false, false>(bs, wb + rs, i0, im, ip);
+    sgs_load_row<T, VW, false, false>(bn, wb + rn, i0, im, ip);
+    sgs_load_row<T, VW, true, true>(ac, wa + r0, i0, im, ip);
+    sgs_load_row<T, VW, false, false>(as, wa + rs, i0, im, ip);
+    sgs_load_row<T, VW, false, false>(an, wa + rn, i0, im, ip);
+    if (k > 0) {
+        sgs_load_row<T, VW, true, false>(ud, u - plane + r0, i0, im, ip);
+        sgs_load_row<T, VW, false, false>(vd, v - plane + r0, i0, im, ip);
+        sgs_load_row<T, VW, false, false>(vds, v - plane + rs, i0, im, ip);
+    } else {                                                // no-slip ghost below the bottom wall
+#pragma unroll
+        for (int m = 0; m <= VW; ++m) { ud[m] = -uc[m]; vd[m] = -vc[m]; vds[m] = -vs[m]; }
+    }
+    if (k < nz - 1) {
+        sgs_load_row<T, VW, true, false>(uu, u + plane + r0, i0, im, ip);
+        sgs_load_row<T, VW, false, false>(vu, v + plane + r0, i0, im, ip);
+        sgs_load_row<T, VW, false, false>(vus, v + plane + rs, i0, im, ip);
+    } else {                                                // ghost above the top wall
+#pragma unroll
+        for (int m = 0; m <= VW; ++m) { uu[m] = -uc[m]; vu[m] = -vc[m]; vus[m] = -vs[m]; }
+    }
+    // the next CTAs of this column of the grid work on plane k+1, whose rows
+    // are all in L2 by now; start plane k+2 (u, v and the face above it) on
+    // its way from HBM
+    if (k + 2 < nz) {
+        prefetch_l2(u + 2 * plane + r0 + i0);
+        prefetch_l2(v + 2 * plane + r0 + i0);
+        prefetch_l2(wa + 2 * plane + r0 + i0);
+    }
+    const T coef = T(a.coef[k]);
+    const T idx = a.idx, idy = a.idy, idzf = a.idzf[k], izlo = a.idzc[k], izhi = a.idzc[k + 1];
+    // differences and sums shared by the x-neighbouring cells of this thread
+    T dns[N], dlo[N], dhi[N], sv[N], sw[N];
+#pragma unroll
+    for (int m = 0; m <= VW; ++m) { dns[m] = un[m] - us[m]; dlo[m] = uc[m] - ud[m]; dhi[m] = uu[m] - uc[m]; }
+#pragma unroll
+    for (int m = 0; m < N; ++m) { sv[m] = vc[m] + vs[m]; sw[m] = bc[m] + ac[m]; }
+    T out[VW];
+#pragma unroll
+    for (int t = 0; t < VW; ++t) {
+        const int c = t + 1, w = t, e = t + 2;              // cells i, i-1, i+1
+        const T s11 = (uc[c] - uc[w]) * idx;
+        const T s22 = (vc[c] - vs[c]) * idy;
+        const T s33 = (ac[c] - bc[c]) * idzf;
+        const T a12 = (dns[c] + dns[w]) * idy + (sv[e] - sv[w]) * idx;
+        const T a13 = (dlo[c] + dlo[w]) * izlo + (dhi[c] + dhi[w]) * izhi + (sw[e] - sw[w]) * idx;
+        const T a23 = ((vc[c] - vd[c]) + (vs[c] - vds[c])) * izlo + ((vu[c] - vc[c]) + (vus[c] - vs[c])) * izhi +
+                      ((bn[c] + an[c]) - (bs[c] + as[c])) * idy;
+        // 2 S_ij S_ij = 2 (s11^2 + s22^2 + s33^2) + (a12^2 + a13^2 + a23^2) / 16
+        const T ss2 = T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(0.0625) * (a12 * a12 + a13 * a13 + a23 * a23);
+        out[t] = coef * sqrt(ss2);
+    }
+    T* __restrict__ dst = a.nut + (size_t)k * plane + r0 + i0;
+    if constexpr (VW == 1) {
+        dst[0] = out[0];
+    } else if constexpr (VW == 2) {
+        *reinterpret_cast<double2*>(dst) = make_double2(out[0], out[1]);
+    } else {
+        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
     }
 }
 
 template <typename T>
 cudaError_t launch_eddy_viscosity(const SgsArgs<T>& a, cudaStream_t st) {
-    const long plane = (long)a.nx * a.ny;
-    long bx = (plane + 255) / 256;
-    if (bx > 2048) bx = 2048;
-    dim3 grid((unsigned)bx, (unsigned)a.nz);
-    k_eddy_visc<T><<<grid, 256, 0, st>>>(a);
+    if (a.nz > 65535 || a.ny > 8 * 65535) return cudaErrorInvalidValue;
+    k_sgs_coef<<<(a.nz + 127) / 128, 128, 0, st>>>(a.coef, a.zcen, a.dzf, a.nz, a.lz, a.dx, a.dy, a.cs, a.nu,
+                                                    a.utau);
+    constexpr int VV = 16 / (int)sizeof(T);
+    const bool aligned = ((uintptr_t)a.u | (uintptr_t)a.v | (uintptr_t)a.w | (uintptr_t)a.nut) % 16 == 0;
+    const bool vec = aligned && a.nx % VV == 0;
+    const int groups = vec ? a.nx / VV : a.nx;
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((groups + 31) / 32), (unsigned)((a.ny + 7) / 8), (unsigned)a.nz);
+    if (vec) k_eddy_visc<T, VV><<<grid, block, 0, st>>>(a);
+    else k_eddy_visc<T, 1><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

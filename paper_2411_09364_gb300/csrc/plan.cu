@@ -607,6 +607,7 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         double zacc = 0.0;
         for (int k = 0; k < nz; ++k) { zcen[k] = zacc + 0.5 * dzf[k]; zacc += dzf[k]; }
         P->zcen_d = dev_upload(zcen, P->owned);
+        P->sgs_coef = dev_upload(std::vector<double>(nz, 0.0), P->owned);
         const int nzero = nx > ny ? nx : ny;
         P->zero_d = dev_upload(std::vector<double>(nzero, 0.0), P->owned);
         P->zero_f = dev_upload(std::vector<float>(nzero, 0.0f), P->owned);
@@ -615,7 +616,8 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         P->dzf_sum = 0.0;
         for (int k = 0; k < nz; ++k) P->dzf_sum += dzf[k];
         if (!P->za_d || !P->zc_d || !P->dzf_d || !P->za_f || !P->zc_f || !P->status || !P->acc || !P->idzf_d ||
-            !P->idzc_d || !P->idzf_f || !P->idzc_f || !P->zero_d || !P->zero_f || !P->zcen_d)
+            !P->idzc_d || !P->idzf_f || !P->idzc_f || !P->zero_d || !P->zero_f || !P->zcen_d ||
+            !P->sgs_coef)
             rc = CALES_ENOMEM;
     }
     if (rc == CALES_OK && cudaDeviceSynchronize() != cudaSuccess) rc = CALES_ECUDA;

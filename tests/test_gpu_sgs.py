@@ -31,7 +31,7 @@ def _velocity(seed, nx, ny, nz):
     return u, v, w
 
 
-@pytest.mark.parametrize("shape", [(48, 20, 33), (128, 64, 64)])
+@pytest.mark.parametrize("shape", [(48, 20, 33), (128, 64, 64), (50, 20, 17), (54, 12, 9)])
 @pytest.mark.parametrize("precision,tol", [(cs.FP64, 1e-12), (cs.FP32, 1e-5)])
 def test_eddy_viscosity_against_oracle(cuda_device, shape, precision, tol):
     nx, ny, nz = shape
@@ -44,6 +44,27 @@ def test_eddy_viscosity_against_oracle(cuda_device, shape, precision, tol):
     ref = O.eddy_viscosity(u, v, w, g, 0.1, 1e-3, 0.06)
     assert O.rel_l2(nut.double().cpu().numpy(), ref) <= tol
     assert np.max(np.abs(nut.double().cpu().numpy() - ref)) <= 10 * tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision,tol", [(cs.FP64, 1e-12), (cs.FP32, 1e-5)])
+def test_eddy_viscosity_unaligned_views(cuda_device, precision, tol):
+    """Views one element into their storage: the kernel takes its scalar path."""
+    nx, ny, nz = 48, 20, 9
+    g, plan = _pair(nx, ny, nz, precision)
+    u, v, w = _velocity(8300, nx, ny, nz)
+    dt = plan.dtype
+
+    def shifted(x):
+        buf = torch.empty(x.size + 1, dtype=dt, device="cuda")
+        view = buf[1:].view(x.shape)
+        view.copy_(torch.from_numpy(x))
+        return view
+
+    out = shifted(np.zeros((nz, ny, nx)))
+    nut = plan.eddy_viscosity(0.17, 2e-3, 0.05, shifted(u), shifted(v), shifted(w), out)
+    torch.cuda.synchronize()
+    assert nut.data_ptr() == out.data_ptr()
+    assert O.rel_l2(out.double().cpu().numpy(), O.eddy_viscosity(u, v, w, g, 0.17, 2e-3, 0.05)) <= tol
 
 
 def test_eddy_viscosity_rejects_bad_arguments(cuda_device):

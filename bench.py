@@ -198,6 +198,12 @@ def run_configs(args):
     def want(tag):
         return args.only is None or args.only in tag
 
+    # the bench grid (or --shape) for the line solves and the eddy viscosity
+    wl = dict(WORKLOAD)
+    if args.shape:
+        sx, sy, sz = (int(v) for v in args.shape.split(","))
+        wl.update(nx=sx, ny=sy, nz=sz, lx=wl["lx"] * sx / wl["nx"], ly=wl["ly"] * sy / wl["ny"])
+
     if want("channel_poisson_64x32x32"):
         # channel 64x32x32, P,P,N, uniform z, FP64: fits L2, latency-bound
         plan = cs.channel_plan(64, 32, 32, beta=0.0)
@@ -244,7 +250,7 @@ def run_configs(args):
               "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
     if want("z_line_helmholtz"):
         # wall-normal implicit line solves (Eq. 21) on the bench grid, Dirichlet walls
-        w = WORKLOAD
+        w = wl
         zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
         dzc, dzf = cs.cell_spacings(zf)
         plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 1, 1, 2, 2), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,
@@ -262,7 +268,7 @@ def run_configs(args):
         torch.cuda.empty_cache()
     if want("eddy_viscosity"):
         # Smagorinsky / van Driest eddy viscosity (Eq. 4) on a channel of the bench size
-        w = WORKLOAD
+        w = wl
         zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
         dzc, dzf = cs.cell_spacings(zf)
         plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc, dzf,

@@ -13,3 +13,4 @@ finite differences).  No function is "parity unpinned".
 from .cales_oracle import *  # noqa: F401,F403
 from .closure_oracle import *  # noqa: F401,F403
 from .sgs_oracle import *  # noqa: F401,F403
+from .rk3_oracle import *  # noqa: F401,F403

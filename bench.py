@@ -290,6 +290,39 @@ def run_configs(args):
             del uu, vv, ww, nt
         del plan
         torch.cuda.empty_cache()
+    if want("rk3_step_channel"):
+        # one explicit RK3 time step (three substeps of Eqs. 7-10, each with the
+        # eddy viscosity of Eq. 4) on the bench grid as a channel; seeded
+        # Gaussian velocity and pressure drawn on the device
+        w = wl
+        zf = S.tanh_faces(w["nz"], w["beta"], w["lz"])
+        dzc, dzf = cs.cell_spacings(zf)
+        plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc,
+                       dzf, cs.FP32)
+        shp, shw = (w["nz"], w["ny"], w["nx"]), (w["nz"] + 1, w["ny"], w["nx"])
+        for mode, name in ((cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
+            plan.set_precision(mode, 2)
+            dt = torch.float32 if mode == cs.FP32 else torch.float64
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(7000)
+            uu, vv, pp = (torch.randn(shp, generator=gen, device=dev, dtype=dt) for _ in range(3))
+            ww = torch.randn(shw, generator=gen, device=dev, dtype=dt)
+            ww[0].zero_()
+            ww[-1].zero_()
+            nut = plan.eddy_viscosity(0.1, 1e-4, 0.05, uu, vv, ww)
+            ru, rv, rw = torch.zeros_like(uu), torch.zeros_like(uu), torch.zeros_like(ww)
+            work = plan.rk3_work(dev)
+
+            def rk3_step():
+                for s in range(3):
+                    plan.rk3_substep(s, 2e-4, 1e-4, 0.1, 0.05, uu, vv, ww, pp, nut, ru, rv, rw, work)
+            ms = timed(rk3_step, 3)
+            emit({"workload": f"rk3_step_channel_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
+                  "ms_per_substep": ms / 3, "gpoints_per_s": uu.numel() / ms / 1e6,
+                  "finite": bool(torch.isfinite(uu).all().item())})
+            del uu, vv, ww, pp, nut, ru, rv, rw, work
+        del plan
+        torch.cuda.empty_cache()
     if want("differentiable_poisson"):
         # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
         plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)

@@ -196,6 +196,38 @@ int cales_eddy_viscosity(cales_plan_t plan, double cs, double nu, double utau, c
                          const void* w, void* nut, void* stream);
 
 /*
+ * One substep (stage 0, 1, 2) of the low-storage RK3 pressure-correction
+ * scheme with explicit viscous terms, Sec. 2.2 Eqs. 7-10 and Algorithm 1:
+ *   R^k       = H^k + nu L u^k,  H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j (Eq. 11;
+ *               signs from Eqs. 2-3)
+ *   u*        = u^k + dt (alpha_k R^k + beta_k R^{k-1} - gamma_k grad p^{k-1/2})   (Eq. 7)
+ *   L phi     = div u* / (gamma_k dt)                                          (Eq. 8)
+ *   u^{k+1}   = u* - gamma_k dt grad phi                                       (Eq. 9)
+ *   p^{k+1/2} = p^{k-1/2} + phi                                                (Eq. 10)
+ *   nu_t^{k+1} from u^{k+1} as cales_eddy_viscosity (Eq. 4)
+ * with Wray's alpha = (8/15, 5/12, 3/4), beta = (0, -17/60, -5/12),
+ * gamma = alpha + beta.  Channel plans only (periodic x and y, Neumann z for
+ * the pressure; the velocity has no-slip walls, ghosts as in
+ * cales_eddy_viscosity; nu_t beyond a wall repeats the first interior value).
+ * Advection is in divergence form with mean interpolation; the off-diagonal
+ * stresses sit on cell edges with nu_t averaged from the four centres.
+ *   u, v [nz][ny][nx], w [nz+1][ny][nx] (w[0] = w[nz] = 0): in u^k, out u^{k+1}
+ *   p [nz][ny][nx]: in p^{k-1/2}, out p^{k+1/2}
+ *   nut [nz][ny][nx]: in nu_t^k, out nu_t^{k+1} (also used as scratch)
+ *   ru, rv [nz][ny][nx], rw [nz+1][ny][nx]: in R^{k-1} (not read at stage 0),
+ *     out R^k, for the next stage
+ *   work: 3 nx ny nz + nx ny (nz+1) elements (u*, v*, w*, phi), not aliased
+ * Element type: float for CALES_FP32 plans, double otherwise (the Poisson
+ * solve runs in the plan's precision mode).  All arrays are device memory
+ * owned by the caller.  Returns CALES_EUNSUPPORTED for other boundary
+ * layouts, CALES_EINVAL for a stage outside 0..2, dt or nu not positive,
+ * cs or utau negative or any NULL array, CALES_ECUDA on launch failure.
+ */
+int cales_rk3_substep(cales_plan_t plan, int stage, double dt, double nu, double cs, double utau, void* u,
+                      void* v, void* w, void* p, void* nut, void* ru, void* rv, void* rw, void* work,
+                      void* stream);
+
+/*
  * Learned closure trained through the projection (the paper motivates
  * machine-learned closures built on the solver, Sec. 1).  FP32, plan layout
  * as above.  theta: device [3][27] taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1).

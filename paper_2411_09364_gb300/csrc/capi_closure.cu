@@ -41,6 +41,42 @@ static SgsArgs<T> sgs_args(cales_plan_t P, double cs, double nu, double utau, co
     return a;
 }
 
+// Wray's low-storage RK3 coefficients (Sec. 2.2, below Eq. 10): alpha_k,
+// beta_k, gamma_k = alpha_k + beta_k; the three gammas sum to one.
+static const double kRk3Alpha[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+static const double kRk3Beta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+// One explicit substep (Eqs. 7-10, then Eq. 4): predictor, divergence of u*,
+// Poisson solve for phi' = gamma dt phi, correction u = u* - grad phi',
+// p += phi' / (gamma dt), nu_t from the new velocity.  d = div u* is staged
+// in the nut array, whose old values the predictor has consumed.
+template <typename T>
+static int rk3_substep(cales_plan_t P, int stage, double dt, double nu, double cs, double utau, T* u, T* v, T* w,
+                       T* p, T* nut, T* ru, T* rv, T* rw, T* work, cudaStream_t st) {
+    const size_t n = (size_t)P->nx * P->ny * P->nz, nw = (size_t)P->nx * P->ny * (P->nz + 1);
+    T* us = work;
+    T* vs = us + n;
+    T* ws = vs + n;
+    T* phi = ws + nw;
+    const double al = kRk3Alpha[stage], be = kRk3Beta[stage], ga = al + be;
+    const GridArgs<T> g = gargs<T>(P);
+    MomArgs<T> m;
+    m.u = u; m.v = v; m.w = w; m.nut = nut; m.p = p;
+    m.us = us; m.vs = vs; m.ws = ws;
+    m.ru = ru; m.rv = rv; m.rw = rw;
+    m.nx = P->nx; m.ny = P->ny; m.nz = P->nz;
+    m.idx = g.idx; m.idy = g.idy; m.idzf = g.idzf; m.idzc = g.idzc;
+    m.nu = T(nu); m.dt = T(dt); m.alpha = T(al); m.beta = T(be); m.gamma = T(ga);
+    if (launch_mom_predict<T>(m, st) != cudaSuccess) return CALES_ECUDA;
+    if (launch_divergence<T>(g, us, vs, ws, nut, st) != cudaSuccess) return CALES_ECUDA;
+    const int rc = cales_internal_solve(P, false, 0.0, false, nut, phi, st);
+    if (rc != CALES_OK) return rc;
+    if (launch_gradient<T>(g, phi, us, vs, ws, u, v, w, 1, st) != cudaSuccess) return CALES_ECUDA;
+    if (launch_pressure_update<T>(p, phi, T(1.0 / (ga * dt)), (long)n, st) != cudaSuccess) return CALES_ECUDA;
+    if (launch_eddy_viscosity<T>(sgs_args<T>(P, cs, nu, utau, u, v, w, nut), st) != cudaSuccess) return CALES_ECUDA;
+    return CALES_OK;
+}
+
 #define CALES_DISPATCH(P, CALL_D, CALL_F) \
     ((P)->precision == CALES_FP32 ? (CALL_F) : (CALL_D))
 
@@ -57,6 +93,21 @@ int cales_eddy_viscosity(cales_plan_t P, double cs, double nu, double utau, cons
     if (P->precision == CALES_FP32) e = launch_eddy_viscosity<float>(sgs_args<float>(P, cs, nu, utau, u, v, w, nut), st);
     else e = launch_eddy_viscosity<double>(sgs_args<double>(P, cs, nu, utau, u, v, w, nut), st);
     return e == cudaSuccess ? CALES_OK : CALES_ECUDA;
+}
+
+int cales_rk3_substep(cales_plan_t P, int stage, double dt, double nu, double cs, double utau, void* u, void* v,
+                      void* w, void* p, void* nut, void* ru, void* rv, void* rw, void* work, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt) || !(nu > 0.0) || !std::isfinite(nu) ||
+        !(cs >= 0.0) || !std::isfinite(cs) || !(utau >= 0.0) || !std::isfinite(utau))
+        return CALES_EINVAL;
+    if (!u || !v || !w || !p || !nut || !ru || !rv || !rw || !work) return CALES_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->precision == CALES_FP32)
+        return rk3_substep<float>(P, stage, dt, nu, cs, utau, (float*)u, (float*)v, (float*)w, (float*)p,
+                                  (float*)nut, (float*)ru, (float*)rv, (float*)rw, (float*)work, st);
+    return rk3_substep<double>(P, stage, dt, nu, cs, utau, (double*)u, (double*)v, (double*)w, (double*)p,
+                               (double*)nut, (double*)ru, (double*)rv, (double*)rw, (double*)work, st);
 }
 
 int cales_divergence(cales_plan_t P, const void* u, const void* v, const void* w, void* d, void* stream) {

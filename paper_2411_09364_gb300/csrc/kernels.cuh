@@ -117,6 +117,26 @@ template <typename T> struct SgsArgs {
     double lz, dx, dy, cs, nu, utau;
 };
 
+// Explicit RK3 predictor of the pressure-correction substep (Eq. 7) on a channel.
+template <typename T> struct MomArgs {
+    const T* u;          // x-faces [nz][ny][nx]
+    const T* v;          // y-faces [nz][ny][nx]
+    const T* w;          // z-faces [nz+1][ny][nx], w[0] = w[nz] = 0
+    const T* nut;        // eddy viscosity, centres [nz][ny][nx]
+    const T* p;          // pressure p^{k-1/2}, centres
+    T* us;               // predicted velocity u* (same layouts as u, v, w)
+    T* vs;
+    T* ws;
+    T* ru;               // in: R^{k-1} (read only when beta != 0); out: R^k = H^k + nu L u^k
+    T* rv;
+    T* rw;
+    int nx, ny, nz;
+    T idx, idy;
+    const T* idzf;       // 1/dzf [nz]
+    const T* idzc;       // 1/dzc [nz+1]
+    T nu, dt, alpha, beta, gamma;
+};
+
 enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
 
 template <typename T, typename TIn> cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st);
@@ -172,6 +192,8 @@ cudaError_t launch_gradient(const GridArgs<T>&, const T*, const T*, const T*, co
 template <typename T>
 cudaError_t launch_divergence_T(const GridArgs<T>&, const T*, const T*, const T*, const T*, T*, T*, T*, cudaStream_t);
 template <typename T> cudaError_t launch_gradient_T(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
+template <typename T> cudaError_t launch_mom_predict(const MomArgs<T>&, cudaStream_t);
+template <typename T> cudaError_t launch_pressure_update(T* p, const T* phi, T scale, long n, cudaStream_t);
 cudaError_t launch_stencil27(const StencilArgs&, cudaStream_t);
 cudaError_t launch_stencil27_wgrad(const WGradArgs&, cudaStream_t);
 cudaError_t launch_sqerr(const SqErrArgs&, cudaStream_t);

@@ -24,37 +24,42 @@ namespace cales {
 
 __device__ __forceinline__ long wrapx(long i, long n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// One thread per (i, j) of plane blockIdx.z (blocks of 32 x 8): no index division.
 template <typename T>
-__global__ void k_divergence(GridArgs<T> g, const T* __restrict__ u, const T* __restrict__ v,
-                             const T* __restrict__ w, T* __restrict__ d, int transpose_unused) {
-    const long nx = g.nx, ny = g.ny, plane = nx * ny, N = plane * g.nz;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (long)gridDim.x * blockDim.x) {
-        const long k = idx / plane, rem = idx - k * plane, j = rem / nx, i = rem - j * nx;
-        const T du = (u[idx] - u[k * plane + j * nx + wrapx(i - 1, nx)]) * g.idx;
-        const T dv = (v[idx] - v[k * plane + wrapx(j - 1, ny) * nx + i]) * g.idy;
-        const T dw = (w[idx + plane] - w[idx]) * g.idzf[k];
-        d[idx] = du + dv + dw;
-    }
+__global__ void __launch_bounds__(256) k_divergence(GridArgs<T> g, const T* __restrict__ u,
+                                                   const T* __restrict__ v, const T* __restrict__ w,
+                                                   T* __restrict__ d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z, nx = g.nx, ny = g.ny;
+    if (i >= nx || j >= ny) return;
+    const size_t plane = (size_t)nx * ny, row = (size_t)k * plane + (size_t)j * nx;
+    const size_t idx = row + i;
+    const T du = (u[idx] - u[row + (i > 0 ? i - 1 : nx - 1)]) * g.idx;
+    const T dv = (v[idx] - v[(size_t)k * plane + (size_t)(j > 0 ? j - 1 : ny - 1) * nx + i]) * g.idy;
+    const T dw = (w[idx + plane] - w[idx]) * g.idzf[k];
+    d[idx] = du + dv + dw;
 }
 
-// gx, gy, gz = sub ? (vin - grad phi) : grad phi
+// gx, gy, gz = sub ? (vin - grad phi) : grad phi; plane blockIdx.z = 0..nz (z-faces)
 template <typename T>
-__global__ void k_gradient(GridArgs<T> g, const T* __restrict__ phi, const T* __restrict__ uin,
-                           const T* __restrict__ vin, const T* __restrict__ win, T* __restrict__ gx,
-                           T* __restrict__ gy, T* __restrict__ gz, int sub) {
-    const long nx = g.nx, ny = g.ny, nz = g.nz, plane = nx * ny, N = plane * (nz + 1);
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (long)gridDim.x * blockDim.x) {
-        const long k = idx / plane, rem = idx - k * plane, j = rem / nx, i = rem - j * nx;
-        T z = T(0);
-        if (k > 0 && k < nz) z = (phi[idx] - phi[idx - plane]) * g.idzc[k];
-        gz[idx] = sub ? win[idx] - z : z;
-        if (k < nz) {
-            const T c = phi[idx];
-            const T x = (phi[k * plane + j * nx + wrapx(i + 1, nx)] - c) * g.idx;
-            const T y = (phi[k * plane + wrapx(j + 1, ny) * nx + i] - c) * g.idy;
-            gx[idx] = sub ? uin[idx] - x : x;
-            gy[idx] = sub ? vin[idx] - y : y;
-        }
+__global__ void __launch_bounds__(256) k_gradient(GridArgs<T> g, const T* __restrict__ phi,
+                                                 const T* __restrict__ uin, const T* __restrict__ vin,
+                                                 const T* __restrict__ win, T* __restrict__ gx,
+                                                 T* __restrict__ gy, T* __restrict__ gz, int sub) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z, nx = g.nx, ny = g.ny, nz = g.nz;
+    if (i >= nx || j >= ny) return;
+    const size_t plane = (size_t)nx * ny, row = (size_t)k * plane + (size_t)j * nx;
+    const size_t idx = row + i;
+    T z = T(0);
+    if (k > 0 && k < nz) z = (phi[idx] - phi[idx - plane]) * g.idzc[k];
+    gz[idx] = sub ? win[idx] - z : z;
+    if (k < nz) {
+        const T c = phi[idx];
+        const T x = (phi[row + (i + 1 < nx ? i + 1 : 0)] - c) * g.idx;
+        const T y = (phi[(size_t)k * plane + (size_t)(j + 1 < ny ? j + 1 : 0) * nx + i] - c) * g.idy;
+        gx[idx] = sub ? uin[idx] - x : x;
+        gy[idx] = sub ? vin[idx] - y : y;
     }
 }
 
@@ -224,13 +229,17 @@ static unsigned grid_for(long n) {
 
 template <typename T>
 cudaError_t launch_divergence(const GridArgs<T>& g, const T* u, const T* v, const T* w, T* d, cudaStream_t st) {
-    k_divergence<T><<<grid_for((long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, u, v, w, d, 0);
+    if (g.nz > 65535 || g.ny > 8 * 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.nz);
+    k_divergence<T><<<grid, dim3(32, 8), 0, st>>>(g, u, v, w, d);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_gradient(const GridArgs<T>& g, const T* phi, const T* uin, const T* vin, const T* win, T* gx,
                             T* gy, T* gz, int sub, cudaStream_t st) {
-    k_gradient<T><<<grid_for((long)g.nx * g.ny * (g.nz + 1)), 256, 0, st>>>(g, phi, uin, vin, win, gx, gy, gz, sub);
+    if (g.nz + 1 > 65535 || g.ny > 8 * 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)(g.nz + 1));
+    k_gradient<T><<<grid, dim3(32, 8), 0, st>>>(g, phi, uin, vin, win, gx, gy, gz, sub);
     return cudaGetLastError();
 }
 template <typename T>

@@ -130,6 +130,25 @@ class Plan:
                                              _stream(stream)), "cales_eddy_viscosity")
         return out
 
+    def rk3_work(self, device="cuda"):
+        """Scratch for rk3_substep: 3 nx ny nz + nx ny (nz + 1) elements."""
+        return torch.empty(3 * self.numel + self.nx * self.ny * (self.nz + 1), dtype=self.dtype, device=device)
+
+    def rk3_substep(self, stage, dt, nu, cs, utau, u, v, w, p, nut, ru, rv, rw, work=None, stream=None):
+        """One explicit RK3 pressure-correction substep (Eqs. 7-10, then Eq. 4),
+        in place: (u, v, w, p, nut) advance to stage + 1 and (ru, rv, rw) hold
+        R^k for the next stage (their input is R^{k-1}, unread at stage 0)."""
+        n = self.numel
+        nw = self.nx * self.ny * (self.nz + 1)
+        if work is None:
+            work = self.rk3_work(u.device)
+        ptrs = [_ptr(t, self.dtype, m, name) for t, m, name in
+                ((u, n, "u"), (v, n, "v"), (w, nw, "w"), (p, n, "p"), (nut, n, "nut"), (ru, n, "ru"),
+                 (rv, n, "rv"), (rw, nw, "rw"), (work, 3 * n + nw, "work"))]
+        N.check(N.lib().cales_rk3_substep(self._h, int(stage), float(dt), float(nu), float(cs), float(utau), *ptrs,
+                                          _stream(stream)), "cales_rk3_substep")
+        return work
+
     def poisson_adjoint(self, w, out=None, stream=None):
         pf, po, out = self._io(w, out)
         N.check(N.lib().cales_poisson_solve_adjoint(self._h, pf, po, _stream(stream)),

@@ -291,7 +291,7 @@ def run_configs(args):
         del plan
         torch.cuda.empty_cache()
     if want("rk3_step_channel"):
-        # one explicit RK3 time step (three substeps of Eqs. 7-10, each with the
+        # one explicit RK3 time step (three substeps of Eqs. 11-14, each with the
         # eddy viscosity of Eq. 4) on the bench grid as a channel; seeded
         # Gaussian velocity and pressure drawn on the device
         w = wl

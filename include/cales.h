@@ -197,13 +197,13 @@ int cales_eddy_viscosity(cales_plan_t plan, double cs, double nu, double utau, c
 
 /*
  * One substep (stage 0, 1, 2) of the low-storage RK3 pressure-correction
- * scheme with explicit viscous terms, Sec. 2.2 Eqs. 7-10 and Algorithm 1:
- *   R^k       = H^k + nu L u^k,  H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j (Eq. 11;
+ * scheme with explicit viscous terms, Sec. 2.2 Eqs. 11-14 and Algorithm 1:
+ *   R^k       = H^k + nu L u^k,  H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j (Eq. 15;
  *               signs from Eqs. 2-3)
- *   u*        = u^k + dt (alpha_k R^k + beta_k R^{k-1} - gamma_k grad p^{k-1/2})   (Eq. 7)
- *   L phi     = div u* / (gamma_k dt)                                          (Eq. 8)
- *   u^{k+1}   = u* - gamma_k dt grad phi                                       (Eq. 9)
- *   p^{k+1/2} = p^{k-1/2} + phi                                                (Eq. 10)
+ *   u*        = u^k + dt (alpha_k R^k + beta_k R^{k-1} - gamma_k grad p^{k-1/2})   (Eq. 11)
+ *   L phi     = div u* / (gamma_k dt)                                          (Eq. 12)
+ *   u^{k+1}   = u* - gamma_k dt grad phi                                       (Eq. 13)
+ *   p^{k+1/2} = p^{k-1/2} + phi                                                (Eq. 14)
  *   nu_t^{k+1} from u^{k+1} as cales_eddy_viscosity (Eq. 4)
  * with Wray's alpha = (8/15, 5/12, 3/4), beta = (0, -17/60, -5/12),
  * gamma = alpha + beta.  Channel plans only (periodic x and y, Neumann z for

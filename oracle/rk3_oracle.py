@@ -2,15 +2,15 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Sec. 2.2, Eqs. 7-10 with the explicit viscous term (Algorithm 1):
+Sec. 2.2, Eqs. 11-14 with the explicit viscous term (Algorithm 1):
     u*        = u^k + dt [alpha (H^k + nu L u^k) + beta (H^{k-1} + nu L u^{k-1}) - gamma grad p^{k-1/2}]
     L phi     = div u* / (gamma dt)
     u^{k+1}   = u* - gamma dt grad phi
     p^{k+1/2} = p^{k-1/2} + phi
 followed by nu_t^{k+1} from u^{k+1} (Eq. 4).  alpha, beta, gamma are the
-Wray coefficients printed below Eq. 10.  The paper leaves open, read here as:
+Wray coefficients printed below Eq. 14.  The paper leaves open, read here as:
 
-T1  signs of H_i (Eq. 11) from the momentum equation (Eq. 2) and the
+T1  signs of H_i (Eq. 15) from the momentum equation (Eq. 2) and the
     Boussinesq closure (Eq. 3): H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j;
     the right-hand side carried between substeps is R = H + nu L u;
 T2  advection in divergence form on the staggered grid, every interpolated
@@ -124,7 +124,7 @@ def momentum_rhs(u, v, w, nut, g: Grid, nu: float):
 
 
 def rk3_substep(u, v, w, p, nut, r_prev, g: Grid, stage: int, dt: float, nu: float, cs: float, utau: float):
-    """One substep (stage 0, 1, 2) of Eqs. 7-10 and the nu_t update.
+    """One substep (stage 0, 1, 2) of Eqs. 11-14 and the nu_t update.
 
     r_prev is R^{k-1} (ignored at stage 0, where beta = 0).  Returns
     (u, v, w, p, nut, R^k) of the next substep."""

@@ -41,12 +41,12 @@ static SgsArgs<T> sgs_args(cales_plan_t P, double cs, double nu, double utau, co
     return a;
 }
 
-// Wray's low-storage RK3 coefficients (Sec. 2.2, below Eq. 10): alpha_k,
+// Wray's low-storage RK3 coefficients (Sec. 2.2, below Eq. 14): alpha_k,
 // beta_k, gamma_k = alpha_k + beta_k; the three gammas sum to one.
 static const double kRk3Alpha[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 static const double kRk3Beta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
-// One explicit substep (Eqs. 7-10, then Eq. 4): predictor, divergence of u*,
+// One explicit substep (Eqs. 11-14, then Eq. 4): predictor, divergence of u*,
 // Poisson solve for phi' = gamma dt phi, correction u = u* - grad phi',
 // p += phi' / (gamma dt), nu_t from the new velocity.  d = div u* is staged
 // in the nut array, whose old values the predictor has consumed.

@@ -1,5 +1,5 @@
 // Explicit predictor of the low-storage RK3 pressure-correction substep
-// (Sec. 2.2, Eq. 7 with H_i of Eq. 11) on a channel (x, y periodic, no-slip
+// (Sec. 2.2, Eq. 11 with H_i of Eq. 15) on a channel (x, y periodic, no-slip
 // walls in z):
 //   R^k = H^k + nu L u^k,  H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j,
 //   u*  = u^k + dt (alpha R^k + beta R^{k-1} - gamma grad p^{k-1/2}).
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(Mom
     }
 }
 
-// p^{k+1/2} = p^{k-1/2} + scale * phi'  (Eq. 10 with phi = phi' / (gamma dt))
+// p^{k+1/2} = p^{k-1/2} + scale * phi'  (Eq. 14 with phi = phi' / (gamma dt))
 template <typename T>
 __global__ void k_pressure_update(T* __restrict__ p, const T* __restrict__ phi, T scale, long n) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)

@@ -135,7 +135,7 @@ class Plan:
         return torch.empty(3 * self.numel + self.nx * self.ny * (self.nz + 1), dtype=self.dtype, device=device)
 
     def rk3_substep(self, stage, dt, nu, cs, utau, u, v, w, p, nut, ru, rv, rw, work=None, stream=None):
-        """One explicit RK3 pressure-correction substep (Eqs. 7-10, then Eq. 4),
+        """One explicit RK3 pressure-correction substep (Eqs. 11-14, then Eq. 4),
         in place: (u, v, w, p, nut) advance to stage + 1 and (ru, rv, rw) hold
         R^k for the next stage (their input is R^{k-1}, unread at stage 0)."""
         n = self.numel

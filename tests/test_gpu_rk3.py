@@ -1,4 +1,4 @@
-"""Explicit RK3 pressure-correction substeps (Eqs. 7-10, then Eq. 4) through
+"""Explicit RK3 pressure-correction substeps (Eqs. 11-14, then Eq. 4) through
 cales_rk3_substep against the oracle: three chained stages on stretched
 channels, every output (u, v, w, p, nu_t, R) compared after each stage."""
 import math

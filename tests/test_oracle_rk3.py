@@ -1,4 +1,4 @@
-"""Pins of the RK3 pressure-correction substep oracle (Sec. 2.2, Eqs. 7-11)
+"""Pins of the RK3 pressure-correction substep oracle (Sec. 2.2, Eqs. 11-15)
 against what the mathematics fixes: conservation of the divergence-form
 advection, closed-form eigenfunctions of the viscous operator, the identity
 d(2 c S_ij)/dx_j = c L u_i for divergence-free fields, the 1-D conservative
@@ -176,7 +176,7 @@ def test_substep_result_is_divergence_free_and_pressure_consistent():
         scale = np.max(np.abs(O.divergence(u, v, w, g))) + 1.0
         assert np.max(np.abs(O.divergence(un, vn, wn, g))) <= 1e-10 * scale
         assert np.max(np.abs(wn[0])) == 0.0 and np.max(np.abs(wn[-1])) == 0.0
-        # the velocity correction is -grad of gamma dt (p^{k+1/2} - p^{k-1/2}) (Eqs. 9-10)
+        # the velocity correction is -grad of gamma dt (p^{k+1/2} - p^{k-1/2}) (Eqs. 13-14)
         gm = O.RK3_GAMMA[s]
         a = O.momentum_rhs(u, v, w, nut, g, 1e-3)
         gp = O.gradient(p, g)

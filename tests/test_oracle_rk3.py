@@ -210,3 +210,110 @@ def test_mutation_west_neighbour_fails_the_energy_pin(monkeypatch):
     monkeypatch.setattr(R, "_x", lambda a, s: real(a, abs(s)))       # i+1 where i-1 is meant
     with pytest.raises(AssertionError):
         test_advection_conserves_energy_for_divergence_free_fields()
+
+
+# ---------------------------------------------------------------------------
+# Crank-Nicolson variants (Eqs. 17-19: implicit = 1; Eqs. 20-22: implicit = 2)
+# ---------------------------------------------------------------------------
+def test_velocity_grids_reproduce_the_viscous_operator():
+    """The implicit solves' grids carry the same Laplacian as the explicit
+    viscous term: u on the Dirichlet cell grid, w on the interior-face grid."""
+    g = _grid(10, 8, 11, 1.9)
+    u, v, w = _velocity(91, g, divfree=False)
+    guv, gw = O.velocity_grids(g)
+    lu, _, lw = O.viscous(u, v, w, g)
+    assert O.rel_l2(lu, O.apply_L(u, guv)) < 1e-13
+    assert O.rel_l2(lw[1:-1], O.apply_L(w[1:-1], gw)) < 1e-13
+
+
+def _eigen_step(g, field, mx, mz, nu, dt, implicit):
+    nx, nz = g.nx, g.nz
+    kc = np.arange(nz) + 0.5
+    x = np.cos(2 * np.pi * mx * np.arange(nx) / nx)
+    mode = np.broadcast_to(np.sin(np.pi * mz * kc / nz)[:, None, None] * x[None, None, :], (nz, g.ny, nx)).copy()
+    zero = np.zeros_like(mode)
+    u, v = (mode, zero) if field == "u" else (zero, mode)
+    w = np.zeros((nz + 1, g.ny, nx))
+    p, nut, r = zero.copy(), zero.copy(), None
+    for s in range(3):
+        u, v, w, p, nut, r = O.rk3_substep(u, v, w, p, nut, r, g, s, dt, nu, 0.0, 1.0, implicit)
+    return mode, (u if field == "u" else v), p
+
+
+@pytest.mark.parametrize("implicit", [1, 2])
+def test_cn_amplification_of_a_wall_normal_shear_mode(implicit):
+    """u = u(z) eigenmode, no advection or pressure: each substep multiplies it
+    by (1 + gamma z/2) / (1 - gamma z/2), z = nu lambda dt."""
+    g = _grid(8, 6, 12, 0.0)
+    nu, dt, m = 0.05, 0.2, 2
+    mode, out, p = _eigen_step(g, "u", 0, m, nu, dt, implicit)
+    lam = -4 / g.dzf[0] ** 2 * np.sin(np.pi * m / (2 * g.nz)) ** 2
+    amp = np.prod([(1 + gm * nu * lam * dt / 2) / (1 - gm * nu * lam * dt / 2) for gm in O.RK3_GAMMA])
+    assert np.max(np.abs(out - amp * mode)) <= 1e-13
+    assert np.max(np.abs(p)) <= 1e-12
+
+
+@pytest.mark.parametrize("implicit", [1, 2])
+def test_cn_split_of_an_x_z_mode(implicit):
+    """v = X(x) Z(z) (divergence-free, no advection): implicit = 1 treats the
+    whole eigenvalue by Crank-Nicolson; implicit = 2 carries the x part with
+    the explicit RK3 terms and only the z part implicitly."""
+    g = _grid(12, 6, 10, 0.0)
+    nu, dt, mx, mz = 0.03, 0.08, 2, 3
+    mode, out, _ = _eigen_step(g, "v", mx, mz, nu, dt, implicit)
+    lx = -4 / g.dx ** 2 * np.sin(np.pi * mx / g.nx) ** 2
+    lz = -4 / g.dzf[0] ** 2 * np.sin(np.pi * mz / (2 * g.nz)) ** 2
+    amp, prev = 1.0, 0.0          # amplitude and the carried explicit term of the previous stage
+    for a, b, gm in zip(O.RK3_ALPHA, O.RK3_BETA, O.RK3_GAMMA):
+        if implicit == 1:
+            new = amp * (1 + gm * nu * (lx + lz) * dt / 2) / (1 - gm * nu * (lx + lz) * dt / 2)
+        else:
+            carry = nu * lx * amp
+            new = (amp + dt * (a * carry + b * prev) + gm * nu * lz * dt / 2 * amp) / (1 - gm * nu * lz * dt / 2)
+            prev = carry
+        amp = new
+    assert np.max(np.abs(out - amp * mode)) <= 1e-12
+
+
+@pytest.mark.parametrize("implicit", [1, 2])
+def test_cn_pressure_update_closes_the_momentum_equation(implicit):
+    """Eqs. 18-19 (21-22): with p^{k+1/2} - p^{k-1/2} = (I - a L) phi the new
+    velocity satisfies (I - a L) u^{k+1} + gamma dt grad(p^{k+1/2} - p^{k-1/2})
+    = right-hand side, away from the wall rows where the velocity and the
+    pressure take different ghosts."""
+    g = _grid(12, 10, 9, 1.7)
+    u, v, w = _velocity(101, g)
+    p = S.gaussian(104, (g.nz, g.ny, g.nx))
+    nut = O.eddy_viscosity(u, v, w, g, 0.1, 1e-3, 0.05)
+    nu, dt, stage = 2e-2, 5e-3, 1
+    r_prev = O.momentum_rhs(u, v, w, nut, g, nu)
+    rhs, _ = O.rk3_rhs(u, v, w, p, nut, r_prev, g, stage, dt, nu, implicit)
+    un, vn, wn, pn, _, _ = O.rk3_substep(u, v, w, p, nut, r_prev, g, stage, dt, nu, 0.1, 0.05, implicit)
+    gm = O.RK3_GAMMA[stage]
+    ah = gm * nu * dt / 2
+    parts = O.viscous_parts(un, vn, wn, g)
+    gpd = O.gradient(pn - p, g)
+    for c, (lxy, lz), gc, rc, rows in zip((un, vn, wn), parts, gpd, rhs,
+                                          (slice(1, -1), slice(1, -1), slice(2, -2))):
+        lap = lxy + lz if implicit == 1 else lz
+        lhs = c - ah * lap + gm * dt * gc
+        assert np.max(np.abs((lhs - rc)[rows])) <= 1e-11 * (np.max(np.abs(rc)) + 1.0)
+
+
+@pytest.mark.parametrize("implicit", [1, 2])
+def test_cn_substep_is_divergence_free(implicit):
+    g = _grid(12, 8, 10, 1.8)
+    u, v, w = _velocity(111, g, divfree=False)
+    p = S.gaussian(114, (g.nz, g.ny, g.nx))
+    nut = O.eddy_viscosity(u, v, w, g, 0.1, 1e-3, 0.05)
+    r = None
+    for s in range(3):
+        u, v, w, p, nut, r = O.rk3_substep(u, v, w, p, nut, r, g, s, 1e-3, 1e-2, 0.1, 0.05, implicit)
+        assert np.max(np.abs(O.divergence(u, v, w, g))) <= 1e-10
+        assert np.max(np.abs(w[0])) == 0.0 and np.max(np.abs(w[-1])) == 0.0
+
+
+def test_mutation_plain_pressure_update_fails_the_coupling_pin(monkeypatch):
+    monkeypatch.setattr(R, "laplacian_cell", lambda phi, g, z_only=False: np.zeros_like(phi))
+    with pytest.raises(AssertionError):
+        test_cn_pressure_update_closes_the_momentum_equation(1)

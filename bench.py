@@ -300,8 +300,13 @@ def run_configs(args):
         plan = cs.Plan(w["nx"], w["ny"], w["nz"], (0, 0, 0, 0, 1, 1), w["lx"] / w["nx"], w["ly"] / w["ny"], dzc,
                        dzf, cs.FP32)
         shp, shw = (w["nz"], w["ny"], w["nx"]), (w["nz"] + 1, w["ny"], w["nx"])
-        for mode, name in ((cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
+        vel = {}
+        for mode, implicit, name in ((cs.FP32, 0, "fp32"), (cs.FP32_REFINE, 0, "fp32_refine"),
+                                     (cs.FP32, 1, "fp32 cn-3d (Eqs. 17-19)"), (cs.FP32, 2, "fp32 cn-z (Eqs. 20-22)")):
             plan.set_precision(mode, 2)
+            if implicit and not vel:
+                vel["uv"], vel["w"] = cs.channel_velocity_plans(w["nx"], w["ny"], zf, w["lx"] / w["nx"],
+                                                                w["ly"] / w["ny"], cs.FP32)
             dt = torch.float32 if mode == cs.FP32 else torch.float64
             gen = torch.Generator(device=dev)
             gen.manual_seed(7000)
@@ -315,13 +320,17 @@ def run_configs(args):
 
             def rk3_step():
                 for s in range(3):
-                    plan.rk3_substep(s, 2e-4, 1e-4, 0.1, 0.05, uu, vv, ww, pp, nut, ru, rv, rw, work)
+                    if implicit:
+                        plan.rk3_substep_cn(vel["uv"], vel["w"], implicit, s, 2e-4, 1e-4, 0.1, 0.05, uu, vv, ww, pp,
+                                            nut, ru, rv, rw, work)
+                    else:
+                        plan.rk3_substep(s, 2e-4, 1e-4, 0.1, 0.05, uu, vv, ww, pp, nut, ru, rv, rw, work)
             ms = timed(rk3_step, 3)
             emit({"workload": f"rk3_step_channel_{w['nx']}x{w['ny']}x{w['nz']}", "mode": name, "ms": ms,
                   "ms_per_substep": ms / 3, "gpoints_per_s": uu.numel() / ms / 1e6,
                   "finite": bool(torch.isfinite(uu).all().item())})
             del uu, vv, ww, pp, nut, ru, rv, rw, work
-        del plan
+        del plan, vel
         torch.cuda.empty_cache()
     if want("differentiable_poisson"):
         # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel

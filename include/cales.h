@@ -228,6 +228,32 @@ int cales_rk3_substep(cales_plan_t plan, int stage, double dt, double nu, double
                       void* stream);
 
 /*
+ * The same substep with Crank-Nicolson viscous terms, Sec. 2.2:
+ *   implicit = 1 (Eqs. 17-19):
+ *     u**  = u^k + dt (alpha_k H^k + beta_k H^{k-1} + gamma_k (nu L u^k - grad p^{k-1/2}))
+ *     (I - a L) u* = u** - a L u^k,   a = gamma_k nu dt / 2   (modified Helmholtz, Eq. 18)
+ *     Poisson and correction as above (Eqs. 12-13)
+ *     p^{k+1/2} = p^{k-1/2} + phi - a L phi
+ *     R^k = H^k
+ *   implicit = 2 (Eqs. 20-22): L replaced by its wall-normal part L_z in the
+ *     implicit terms (line solves, as cales_helmholtz_z_solve); nu (L_x + L_y) u
+ *     joins H in the explicit RK3 terms, R^k = H^k + nu (L_x + L_y) u^k.
+ * plan: the pressure plan (as cales_rk3_substep).  uv_plan: the u and v
+ * solves, bc (P, P, P, P, D, D) on the same nx, ny, nz, dx, dy and z spacings.
+ * w_plan: the w solve on the nz - 1 interior z-faces, bc (P, P, P, P, DF, DF),
+ * node spacings dzc_w = dzf, control volumes dzf_w = dzc[1..nz-1] of the
+ * pressure grid.  All three plans of the same precision mode; the z spacings
+ * are the caller's to keep consistent (nx, ny, nz, dx, dy, kinds and precision
+ * are checked: CALES_EINVAL otherwise).  Arrays, work size, ownership and the
+ * other errors as cales_rk3_substep; implicit outside 1..2 is CALES_EINVAL.
+ * The velocity solves use the plans' own workspaces, so the three plans serve
+ * one call at a time.
+ */
+int cales_rk3_substep_cn(cales_plan_t plan, cales_plan_t uv_plan, cales_plan_t w_plan, int implicit, int stage,
+                         double dt, double nu, double cs, double utau, void* u, void* v, void* w, void* p,
+                         void* nut, void* ru, void* rv, void* rw, void* work, void* stream);
+
+/*
  * Learned closure trained through the projection (the paper motivates
  * machine-learned closures built on the solver, Sec. 1).  FP32, plan layout
  * as above.  theta: device [3][27] taps, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1).

@@ -27,6 +27,8 @@ SIGNATURES = {
     "cales_eddy_viscosity": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, vp]),
     "cales_rk3_substep": (C.c_int, [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, vp,
                                     vp, vp, vp, vp, vp]),
+    "cales_rk3_substep_cn": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cales_poisson_solve_adjoint": (C.c_int, [vp, vp, vp, vp]),
     "cales_poisson_solve_noalloc": (C.c_int, [vp, vp, vp, vp]),
     "cales_helmholtz_solve_adjoint": (C.c_int, [vp, C.c_double, vp, vp, vp]),

@@ -67,6 +67,7 @@ static int rk3_substep(cales_plan_t P, int stage, double dt, double nu, double c
     m.nx = P->nx; m.ny = P->ny; m.nz = P->nz;
     m.idx = g.idx; m.idy = g.idy; m.idzf = g.idzf; m.idzc = g.idzc;
     m.nu = T(nu); m.dt = T(dt); m.alpha = T(al); m.beta = T(be); m.gamma = T(ga);
+    m.implicit = 0;
     if (launch_mom_predict<T>(m, st) != cudaSuccess) return CALES_ECUDA;
     if (launch_divergence<T>(g, us, vs, ws, nut, st) != cudaSuccess) return CALES_ECUDA;
     const int rc = cales_internal_solve(P, false, 0.0, false, nut, phi, st);
@@ -75,6 +76,63 @@ static int rk3_substep(cales_plan_t P, int stage, double dt, double nu, double c
     if (launch_pressure_update<T>(p, phi, T(1.0 / (ga * dt)), (long)n, st) != cudaSuccess) return CALES_ECUDA;
     if (launch_eddy_viscosity<T>(sgs_args<T>(P, cs, nu, utau, u, v, w, nut), st) != cudaSuccess) return CALES_ECUDA;
     return CALES_OK;
+}
+
+// Crank-Nicolson substep (Eqs. 17-19 for implicit = 1, Eqs. 20-22 for
+// implicit = 2): the predictor writes the right-hand sides of the velocity
+// solves into the work buffers, the solves write u* over u^k (consumed by
+// then), and one kernel applies the correction and the pressure update.
+template <typename T>
+static int rk3_substep_cn(cales_plan_t P, cales_plan_t Puv, cales_plan_t Pw, int implicit, int stage, double dt,
+                          double nu, double cs, double utau, T* u, T* v, T* w, T* p, T* nut, T* ru, T* rv, T* rw,
+                          T* work, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t plane = (size_t)P->nx * P->ny, n = plane * P->nz, nw = plane * (P->nz + 1);
+    T* us = work;
+    T* vs = us + n;
+    T* ws = vs + n;
+    T* phi = ws + nw;
+    const double al = kRk3Alpha[stage], be = kRk3Beta[stage], ga = al + be, ah = 0.5 * ga * nu * dt;
+    const GridArgs<T> g = gargs<T>(P);
+    MomArgs<T> m;
+    m.u = u; m.v = v; m.w = w; m.nut = nut; m.p = p;
+    m.us = us; m.vs = vs; m.ws = ws;
+    m.ru = ru; m.rv = rv; m.rw = rw;
+    m.nx = P->nx; m.ny = P->ny; m.nz = P->nz;
+    m.idx = g.idx; m.idy = g.idy; m.idzf = g.idzf; m.idzc = g.idzc;
+    m.nu = T(nu); m.dt = T(dt); m.alpha = T(al); m.beta = T(be); m.gamma = T(ga);
+    m.implicit = implicit;
+    if (launch_mom_predict<T>(m, st) != cudaSuccess) return CALES_ECUDA;
+    int rc;
+    if (implicit == 1) {
+        if ((rc = cales_internal_solve(Puv, true, ah, false, us, u, stream)) != CALES_OK) return rc;
+        if ((rc = cales_internal_solve(Puv, true, ah, false, vs, v, stream)) != CALES_OK) return rc;
+        if ((rc = cales_internal_solve(Pw, true, ah, false, ws + plane, w + plane, stream)) != CALES_OK) return rc;
+    } else {
+        if ((rc = cales_helmholtz_z_solve(Puv, ah, us, u, stream)) != CALES_OK) return rc;
+        if ((rc = cales_helmholtz_z_solve(Puv, ah, vs, v, stream)) != CALES_OK) return rc;
+        if ((rc = cales_helmholtz_z_solve(Pw, ah, ws + plane, w + plane, stream)) != CALES_OK) return rc;
+    }
+    if (launch_divergence<T>(g, u, v, w, nut, st) != cudaSuccess) return CALES_ECUDA;
+    if ((rc = cales_internal_solve(P, false, 0.0, false, nut, phi, stream)) != CALES_OK) return rc;
+    if (launch_correct_cn<T>(g, u, v, w, p, phi, T(ah), T(1.0 / (ga * dt)), implicit, st) != cudaSuccess)
+        return CALES_ECUDA;
+    if (launch_eddy_viscosity<T>(sgs_args<T>(P, cs, nu, utau, u, v, w, nut), st) != cudaSuccess) return CALES_ECUDA;
+    return CALES_OK;
+}
+
+// the velocity plans of a Crank-Nicolson substep match the pressure plan:
+// same nx, ny, dx, dy and precision; u, v plan Dirichlet in z on nz cells, w
+// plan wall nodes in z on the nz - 1 interior faces; x and y periodic
+static bool cn_plans_match(cales_plan_t P, cales_plan_t Puv, cales_plan_t Pw) {
+    if (!Puv || !Pw) return false;
+    for (cales_plan_t Q : {Puv, Pw}) {
+        if (Q->nx != P->nx || Q->ny != P->ny || Q->dx != P->dx || Q->dy != P->dy || Q->precision != P->precision ||
+            Q->bc[0] != CALES_BC_P || Q->bc[2] != CALES_BC_P)
+            return false;
+    }
+    return Puv->nz == P->nz && Puv->bc[4] == CALES_BC_D && Puv->bc[5] == CALES_BC_D && Pw->nz == P->nz - 1 &&
+           Pw->bc[4] == CALES_BC_DF && Pw->bc[5] == CALES_BC_DF;
 }
 
 #define CALES_DISPATCH(P, CALL_D, CALL_F) \
@@ -108,6 +166,24 @@ int cales_rk3_substep(cales_plan_t P, int stage, double dt, double nu, double cs
                                   (float*)nut, (float*)ru, (float*)rv, (float*)rw, (float*)work, st);
     return rk3_substep<double>(P, stage, dt, nu, cs, utau, (double*)u, (double*)v, (double*)w, (double*)p,
                                (double*)nut, (double*)ru, (double*)rv, (double*)rw, (double*)work, st);
+}
+
+int cales_rk3_substep_cn(cales_plan_t P, cales_plan_t Puv, cales_plan_t Pw, int implicit, int stage, double dt,
+                         double nu, double cs, double utau, void* u, void* v, void* w, void* p, void* nut, void* ru,
+                         void* rv, void* rw, void* work, void* stream) {
+    if (!channel_layout(P)) return P ? CALES_EUNSUPPORTED : CALES_EINVAL;
+    if (implicit < 1 || implicit > 2 || stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt) ||
+        !(nu > 0.0) || !std::isfinite(nu) || !(cs >= 0.0) || !std::isfinite(cs) || !(utau >= 0.0) ||
+        !std::isfinite(utau) || P->nz < 2)
+        return CALES_EINVAL;
+    if (!u || !v || !w || !p || !nut || !ru || !rv || !rw || !work) return CALES_EINVAL;
+    if (!cn_plans_match(P, Puv, Pw)) return CALES_EINVAL;
+    if (P->precision == CALES_FP32)
+        return rk3_substep_cn<float>(P, Puv, Pw, implicit, stage, dt, nu, cs, utau, (float*)u, (float*)v, (float*)w,
+                                     (float*)p, (float*)nut, (float*)ru, (float*)rv, (float*)rw, (float*)work, stream);
+    return rk3_substep_cn<double>(P, Puv, Pw, implicit, stage, dt, nu, cs, utau, (double*)u, (double*)v, (double*)w,
+                                  (double*)p, (double*)nut, (double*)ru, (double*)rv, (double*)rw, (double*)work,
+                                  stream);
 }
 
 int cales_divergence(cales_plan_t P, const void* u, const void* v, const void* w, void* d, void* stream) {

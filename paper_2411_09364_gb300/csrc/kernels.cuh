@@ -135,6 +135,8 @@ template <typename T> struct MomArgs {
     const T* idzf;       // 1/dzf [nz]
     const T* idzc;       // 1/dzc [nz+1]
     T nu, dt, alpha, beta, gamma;
+    int implicit;        // 0: explicit viscous terms (Eq. 11); 1: Crank-Nicolson in all directions
+                         // (Eqs. 17-18); 2: Crank-Nicolson in z only (Eqs. 20-21)
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
@@ -194,6 +196,11 @@ cudaError_t launch_divergence_T(const GridArgs<T>&, const T*, const T*, const T*
 template <typename T> cudaError_t launch_gradient_T(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
 template <typename T> cudaError_t launch_mom_predict(const MomArgs<T>&, cudaStream_t);
 template <typename T> cudaError_t launch_pressure_update(T* p, const T* phi, T scale, long n, cudaStream_t);
+// u, v, w -= grad phi' in place; p += (phi' - a L phi') * scale with L the full
+// (implicit 1) or z-only (implicit 2) Laplacian, Neumann z walls (Eqs. 13, 19, 22)
+template <typename T>
+cudaError_t launch_correct_cn(const GridArgs<T>& g, T* u, T* v, T* w, T* p, const T* phi, T a, T scale, int implicit,
+                              cudaStream_t);
 cudaError_t launch_stencil27(const StencilArgs&, cudaStream_t);
 cudaError_t launch_stencil27_wgrad(const WGradArgs&, cudaStream_t);
 cudaError_t launch_sqerr(const SqErrArgs&, cudaStream_t);

@@ -98,7 +98,7 @@ __device__ __forceinline__ void mom_fill(MomRing<T>& r, const MomArgs<T>& a, int
     mom_put(r, f, m, tid);
 }
 
-template <typename T>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(MomArgs<T> a) {
     __shared__ MomRing<T> ring;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MOM_TX + tx;
@@ -111,7 +111,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(Mom
     const T idx = a.idx, idy = a.idy, idx2 = idx * idx, idy2 = idy * idy;
     const T h = T(0.5), q = T(0.25), two = T(2);
     const T nu = a.nu, dt = a.dt, al = a.alpha, be = a.beta, ga = a.gamma;
+    const T hcn = ga * nu * dt * h;                        // gamma nu dt / 2 of the Crank-Nicolson modes
     const int cx = tx + 1, cy = ty + 1;
+    // R (carried to the next stage) and the velocity update from the advection +
+    // SGS part hs, the Laplacian parts lxy, lz and the pressure gradient gp:
+    //   MODE 0: R = hs + nu (lxy + lz),  out = c + dt (alpha R + beta R' - gamma gp)
+    //   MODE 1: R = hs,                  out = c + dt (alpha R + beta R' + gamma (nu L - gp)) - hcn L
+    //   MODE 2: R = hs + nu lxy,         out = c + dt (alpha R + beta R' + gamma (nu lz - gp)) - hcn lz
+    auto update = [&](T c, T hs, T lxy, T lz, T gp, T rp, T& r) -> T {
+        T inc;
+        if constexpr (MODE == 0) {
+            r = hs + nu * (lxy + lz);
+            inc = al * r - ga * gp;
+        } else if constexpr (MODE == 1) {
+            r = hs;
+            inc = al * r - ga * gp + ga * nu * (lxy + lz);
+        } else {
+            r = hs + nu * lxy;
+            inc = al * r - ga * gp + ga * nu * lz;
+        }
+        if (be != T(0)) inc += be * rp;
+        T out = c + dt * inc;
+        if constexpr (MODE == 1) out -= hcn * (lxy + lz);
+        if constexpr (MODE == 2) out -= hcn * lz;
+        return out;
+    };
 
     mom_fill(ring, a, k0 - 1, x0, y0, tid);
     mom_fill(ring, a, k0, x0, y0, tid);
@@ -155,20 +179,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(Mom
                 const T adv = (sq(h * (uc + ue)) - sq(h * (uw + uc))) * idx +
                               (h * (uc + un) * (h * (v0 + v0e)) - h * (us + uc) * (h * (vs0 + vse))) * idy +
                               (h * (uc + uu) * (h * (wa + wae)) - h * (ud + uc) * (h * (wb + wbe))) * izf;
-                const T lap = (ue - two * uc + uw) * idx2 + (un - two * uc + us) * idy2 +
-                              ((uu - uc) * izhi - (uc - ud) * izlo) * izf;
+                const T lxy = (ue - two * uc + uw) * idx2 + (un - two * uc + us) * idy2;
+                const T lz = ((uu - uc) * izhi - (uc - ud) * izlo) * izf;
                 const T t11e = two * n_e * (ue - uc) * idx, t11w = two * n_c * (uc - uw) * idx;
                 const T t12n = two * (q * (n_c + n_e + n_n + n_ne)) * (h * ((un - uc) * idy + (v0e - v0) * idx));
                 const T t12s = two * (q * (n_s + n_se + n_c + n_e)) * (h * ((uc - us) * idy + (vse - vs0) * idx));
                 const T t13u = two * (q * (n_c + n_e + n_u + n_ue)) * (h * ((uu - uc) * izhi + (wae - wa) * idx));
                 const T t13d = two * (q * (n_d + n_de + n_c + n_e)) * (h * ((uc - ud) * izlo + (wbe - wb) * idx));
                 const T sgs = (t11e - t11w) * idx + (t12n - t12s) * idy + (t13u - t13d) * izf;
-                const T r = -adv + nu * lap + sgs;
                 const T gp = (P(s0, 0, 1) - p_c) * idx;
-                T inc = al * r - ga * gp;
-                if (be != T(0)) inc += be * rpu;
+                T r;
+                a.us[c] = update(uc, -adv + sgs, lxy, lz, gp, rpu, r);
                 a.ru[c] = r;
-                a.us[c] = uc + dt * inc;
             }
             // ---- y-momentum at (i, j+1/2, k) ----
             {
@@ -179,20 +201,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(Mom
                 const T adv = (h * (uc + un) * (h * (vc + ve)) - h * (uw + unw) * (h * (vw + vc))) * idx +
                               (sq(h * (vc + vn)) - sq(h * (vs + vc))) * idy +
                               (h * (vc + vu) * (h * (wa + wan)) - h * (vd + vc) * (h * (wb + wbn))) * izf;
-                const T lap = (ve - two * vc + vw) * idx2 + (vn - two * vc + vs) * idy2 +
-                              ((vu - vc) * izhi - (vc - vd) * izlo) * izf;
+                const T lxy = (ve - two * vc + vw) * idx2 + (vn - two * vc + vs) * idy2;
+                const T lz = ((vu - vc) * izhi - (vc - vd) * izlo) * izf;
                 const T t22n = two * n_n * (vn - vc) * idy, t22c = two * n_c * (vc - vs) * idy;
                 const T t12e = two * (q * (n_c + n_e + n_n + n_ne)) * (h * ((un - uc) * idy + (ve - vc) * idx));
                 const T t12w = two * (q * (n_w + n_c + n_nw + n_n)) * (h * ((unw - uw) * idy + (vc - vw) * idx));
                 const T t23u = two * (q * (n_c + n_n + n_u + n_un)) * (h * ((vu - vc) * izhi + (wan - wa) * idy));
                 const T t23d = two * (q * (n_d + n_dn + n_c + n_n)) * (h * ((vc - vd) * izlo + (wbn - wb) * idy));
                 const T sgs = (t12e - t12w) * idx + (t22n - t22c) * idy + (t23u - t23d) * izf;
-                const T r = -adv + nu * lap + sgs;
                 const T gp = (P(s0, 1, 0) - p_c) * idy;
-                T inc = al * r - ga * gp;
-                if (be != T(0)) inc += be * rpv;
+                T r;
+                a.vs[c] = update(vc, -adv + sgs, lxy, lz, gp, rpv, r);
                 a.rv[c] = r;
-                a.vs[c] = vc + dt * inc;
             }
             // ---- z-momentum at the face (i, j, k), k >= 1; the wall faces stay 0 ----
             if (k == 0) {
@@ -208,20 +228,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mom_predict(Mom
                 const T adv = (h * (udc + ukc) * (h * (wc + we)) - h * (udw + ukw) * (h * (ww + wc))) * idx +
                               (h * (vdc + vkc) * (h * (wc + wn)) - h * (vds + vks) * (h * (ws + wc))) * idy +
                               (sq(h * (wc + wu)) - sq(h * (wd + wc))) * izlo;
-                const T lap = (we - two * wc + ww) * idx2 + (wn - two * wc + ws) * idy2 +
-                              ((wu - wc) * izf - (wc - wd) * izfd) * izlo;
+                const T lxy = (we - two * wc + ww) * idx2 + (wn - two * wc + ws) * idy2;
+                const T lz = ((wu - wc) * izf - (wc - wd) * izfd) * izlo;
                 const T t33c = two * n_c * (wu - wc) * izf, t33d = two * n_d * (wc - wd) * izfd;
                 const T t13e = two * (q * (n_d + n_c + n_de + n_e)) * (h * ((ukc - udc) * izlo + (we - wc) * idx));
                 const T t13w = two * (q * (n_dw + n_w + n_d + n_c)) * (h * ((ukw - udw) * izlo + (wc - ww) * idx));
                 const T t23n = two * (q * (n_d + n_c + n_dn + n_n)) * (h * ((vkc - vdc) * izlo + (wn - wc) * idy));
                 const T t23s = two * (q * (n_ds + n_s + n_d + n_c)) * (h * ((vks - vds) * izlo + (wc - ws) * idy));
                 const T sgs = (t13e - t13w) * idx + (t23n - t23s) * idy + (t33c - t33d) * izlo;
-                const T r = -adv + nu * lap + sgs;
                 const T gp = (p_c - P(sd, 0, 0)) * izlo;
-                T inc = al * r - ga * gp;
-                if (be != T(0)) inc += be * rpw;
+                T r;
+                a.ws[c] = update(wc, -adv + sgs, lxy, lz, gp, rpw, r);
                 a.rw[c] = r;
-                a.ws[c] = wc + dt * inc;
             }
             if (k == nz - 1) {                              // top wall face
                 a.ws[c + plane] = T(0);
@@ -243,13 +261,61 @@ __global__ void k_pressure_update(T* __restrict__ p, const T* __restrict__ phi, 
         p[e] += scale * phi[e];
 }
 
+// Crank-Nicolson correction (Eqs. 13 and 19 / 22) in place, one thread per
+// cell (i, j, k): u, v at the faces i+1/2, j+1/2 and w at the face k (k >= 1)
+// lose the gradient of phi'; p gains scale (phi' - a L phi') with L the full
+// (MODE 1) or z-only (MODE 2) Laplacian of the pressure (Neumann z walls).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_correct_cn(GridArgs<T> g, T* __restrict__ u, T* __restrict__ v,
+                                                   T* __restrict__ w, T* __restrict__ p,
+                                                   const T* __restrict__ phi, T a, T scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z, nx = g.nx, ny = g.ny, nz = g.nz;
+    if (i >= nx || j >= ny) return;
+    const size_t plane = (size_t)nx * ny, row = (size_t)k * plane + (size_t)j * nx;
+    const size_t c = row + i;
+    const int ip = i + 1 < nx ? i + 1 : 0, im = i > 0 ? i - 1 : nx - 1;
+    const int jp = j + 1 < ny ? j + 1 : 0, jm = j > 0 ? j - 1 : ny - 1;
+    const T pc = phi[c];
+    const T pe = phi[row + ip];
+    const T pn = phi[(size_t)k * plane + (size_t)jp * nx + i];
+    const T pd = k > 0 ? phi[c - plane] : pc;               // Neumann: the ghost repeats the wall cell
+    const T pu = k < nz - 1 ? phi[c + plane] : pc;
+    u[c] -= (pe - pc) * g.idx;
+    v[c] -= (pn - pc) * g.idy;
+    if (k > 0) w[c] -= (pc - pd) * g.idzc[k];
+    T lap = ((pu - pc) * g.idzc[k + 1] - (pc - pd) * g.idzc[k]) * g.idzf[k];
+    if constexpr (MODE == 1) {
+        const T pw = phi[row + im];
+        const T ps = phi[(size_t)k * plane + (size_t)jm * nx + i];
+        lap = (pe - T(2) * pc + pw) * (g.idx * g.idx) + (pn - T(2) * pc + ps) * (g.idy * g.idy) + lap;
+    }
+    p[c] += scale * (pc - a * lap);
+}
+
+template <typename T>
+cudaError_t launch_correct_cn(const GridArgs<T>& g, T* u, T* v, T* w, T* p, const T* phi, T a, T scale,
+                              int implicit, cudaStream_t st) {
+    if (g.nz < 1 || g.nz > 65535 || g.ny > 8 * 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.nz);
+    if (implicit == 1) k_correct_cn<T, 1><<<grid, dim3(32, 8), 0, st>>>(g, u, v, w, p, phi, a, scale);
+    else if (implicit == 2) k_correct_cn<T, 2><<<grid, dim3(32, 8), 0, st>>>(g, u, v, w, p, phi, a, scale);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mom_predict(const MomArgs<T>& a, cudaStream_t st) {
     if (a.nz < 1 || a.ny > MOM_TY * 65535) return cudaErrorInvalidValue;
     const dim3 block(MOM_TX, MOM_TY);
     const dim3 grid((unsigned)((a.nx + MOM_TX - 1) / MOM_TX), (unsigned)((a.ny + MOM_TY - 1) / MOM_TY),
                     (unsigned)((a.nz + MOM_KC - 1) / MOM_KC));
-    k_mom_predict<T><<<grid, block, 0, st>>>(a);
+    switch (a.implicit) {
+        case 0: k_mom_predict<T, 0><<<grid, block, 0, st>>>(a); break;
+        case 1: k_mom_predict<T, 1><<<grid, block, 0, st>>>(a); break;
+        case 2: k_mom_predict<T, 2><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -266,5 +332,9 @@ template cudaError_t launch_mom_predict<float>(const MomArgs<float>&, cudaStream
 template cudaError_t launch_mom_predict<double>(const MomArgs<double>&, cudaStream_t);
 template cudaError_t launch_pressure_update<float>(float*, const float*, float, long, cudaStream_t);
 template cudaError_t launch_pressure_update<double>(double*, const double*, double, long, cudaStream_t);
+template cudaError_t launch_correct_cn<float>(const GridArgs<float>&, float*, float*, float*, float*, const float*, float,
+                                             float, int, cudaStream_t);
+template cudaError_t launch_correct_cn<double>(const GridArgs<double>&, double*, double*, double*, double*,
+                                              const double*, double, double, int, cudaStream_t);
 
 }  // namespace cales

@@ -36,6 +36,18 @@ def face_spacings(zf):
     return np.diff(zf), np.diff(zc)
 
 
+def channel_velocity_plans(nx, ny, zf, dx, dy, precision=None, sweeps=2):
+    """(uv_plan, w_plan) of a channel with faces zf[0..nz]: u and v cell-centred
+    with Dirichlet z walls, w on the interior faces with wall nodes."""
+    dzc, dzf = cell_spacings(zf)
+    wdzc, wdzf = face_spacings(zf)
+    nz = len(zf) - 1
+    prec = FP64 if precision is None else precision
+    uv = Plan(nx, ny, nz, (0, 0, 0, 0, 2, 2), dx, dy, dzc, dzf, prec, sweeps)
+    w = Plan(nx, ny, nz - 1, (0, 0, 0, 0, 3, 3), dx, dy, wdzc, wdzf, prec, sweeps)
+    return uv, w
+
+
 def _stream(stream) -> int:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
@@ -147,6 +159,23 @@ class Plan:
                  (rv, n, "rv"), (rw, nw, "rw"), (work, 3 * n + nw, "work"))]
         N.check(N.lib().cales_rk3_substep(self._h, int(stage), float(dt), float(nu), float(cs), float(utau), *ptrs,
                                           _stream(stream)), "cales_rk3_substep")
+        return work
+
+    def rk3_substep_cn(self, uv_plan, w_plan, implicit, stage, dt, nu, cs, utau, u, v, w, p, nut, ru, rv, rw,
+                       work=None, stream=None):
+        """One Crank-Nicolson RK3 substep in place: implicit = 1 (Eqs. 17-19,
+        Helmholtz solves on uv_plan / w_plan) or 2 (Eqs. 20-22, line solves);
+        see channel_velocity_plans for the two velocity plans."""
+        n = self.numel
+        nw = self.nx * self.ny * (self.nz + 1)
+        if work is None:
+            work = self.rk3_work(u.device)
+        ptrs = [_ptr(t, self.dtype, m, name) for t, m, name in
+                ((u, n, "u"), (v, n, "v"), (w, nw, "w"), (p, n, "p"), (nut, n, "nut"), (ru, n, "ru"),
+                 (rv, n, "rv"), (rw, nw, "rw"), (work, 3 * n + nw, "work"))]
+        N.check(N.lib().cales_rk3_substep_cn(self._h, uv_plan._h, w_plan._h, int(implicit), int(stage), float(dt),
+                                             float(nu), float(cs), float(utau), *ptrs, _stream(stream)),
+                "cales_rk3_substep_cn")
         return work
 
     def poisson_adjoint(self, w, out=None, stream=None):

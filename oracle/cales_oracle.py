@@ -230,6 +230,9 @@ def z_operator(g: Grid):
     c = 1.0 / (g.dzc[1:] * g.dzf)      # coupling of row k to k+1
     diag = -(a + c)
     lo, hi = g.bc[4], g.bc[5]
+    if lo == BC_P:
+        # periodic: sub[0] couples row 0 to row nz-1, sup[nz-1] row nz-1 to row 0
+        return a.copy(), diag, c.copy()
     diag[0] += {BC_N: a[0], BC_D: -a[0], BC_DF: 0.0}[lo]
     diag[nz - 1] += {BC_N: c[nz - 1], BC_D: -c[nz - 1], BC_DF: 0.0}[hi]
     sub = a.copy()
@@ -262,10 +265,26 @@ def thomas(sub, diag, sup, rhs):
     return x
 
 
+def cyclic_solve(sub, diag, sup, rhs):
+    """Periodic z: the cyclic tridiagonal of each column (corners sub[0] at
+    (0, n-1) and sup[n-1] at (n-1, 0)) assembled densely and solved by LAPACK
+    (batched gesv).  diag: (n, M) or (n,); rhs: (n, M)."""
+    n, m = rhs.shape
+    diag = np.broadcast_to(diag if np.ndim(diag) == 2 else np.asarray(diag)[:, None], rhs.shape)
+    mat = np.zeros((m, n, n))
+    k = np.arange(n)
+    mat[:, k, k] = diag.T
+    mat[:, k[1:], k[:-1]] = sub[1:]
+    mat[:, k[:-1], k[1:]] = sup[:-1]
+    mat[:, 0, n - 1] += sub[0]
+    mat[:, n - 1, 0] += sup[n - 1]
+    return np.linalg.solve(mat, rhs.T[:, :, None])[:, :, 0].T
+
+
 def is_singular(g: Grid, alpha=None) -> bool:
     """Poisson with only periodic/Neumann sides: constants are in the null space."""
     return (alpha is None and g.bc[0] in (BC_P, BC_N) and g.bc[2] in (BC_P, BC_N)
-            and g.bc[4] == BC_N and g.bc[5] == BC_N)
+            and g.bc[4] in (BC_P, BC_N) and g.bc[5] in (BC_P, BC_N))
 
 
 def weighted_mean(f: np.ndarray, g: Grid) -> float:
@@ -282,8 +301,12 @@ def _check_supported(g: Grid):
     for lo, hi in ((g.bc[0], g.bc[1]), (g.bc[2], g.bc[3])):
         if lo != hi or lo not in (BC_P, BC_N, BC_D):
             raise ValueError("uniform directions take P, N or D on both sides")
-    if g.bc[4] not in (BC_N, BC_D, BC_DF) or g.bc[5] not in (BC_N, BC_D, BC_DF):
-        raise ValueError("z takes N, D or DF at each side")
+    if (g.bc[4] == BC_P) != (g.bc[5] == BC_P):
+        raise ValueError("a periodic z is periodic on both sides")
+    if g.bc[4] == BC_P and g.nz < 3:
+        raise ValueError("a periodic z needs at least three cells")
+    if g.bc[4] not in (BC_P, BC_N, BC_D, BC_DF) or g.bc[5] not in (BC_P, BC_N, BC_D, BC_DF):
+        raise ValueError("z takes P (both sides), N, D or DF at each side")
 
 
 def _apply_along(mat: np.ndarray, a: np.ndarray, axis: int) -> np.ndarray:
@@ -325,14 +348,17 @@ def solve(f: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     fh = _apply_along(fwd_matrix(g.bc[2], ny), fh, 1)
     sub, diag, sup = _mode_tridiag(g, alpha)
     rhs = fh.reshape(nz, -1)
+    per = g.bc[4] == BC_P
+    line = (lambda a, d, c, r: cyclic_solve(a, d, c, r)) if per else thomas
     if sing:
         ph = np.empty_like(rhs)
-        ph[:, 1:] = thomas(sub, diag[:, 1:], sup, rhs[:, 1:])
+        ph[:, 1:] = line(sub, diag[:, 1:], sup, rhs[:, 1:])
         ph[nz - 1, 0] = 0.0
         if nz > 1:
+            # pinned last unknown: the wrap couplings of rows 0 and nz-2 to it drop out
             ph[:nz - 1, :1] = thomas(sub[:nz - 1], diag[:nz - 1, :1], sup[:nz - 1], rhs[:nz - 1, :1])
     else:
-        ph = thomas(sub, diag, sup, rhs)
+        ph = line(sub, diag, sup, rhs)
     ph = ph.reshape(nz, ny, nx)
     p = _apply_along(inv_matrix(g.bc[2], ny), ph, 1)
     p = _apply_along(inv_matrix(g.bc[0], nx), p, 2)
@@ -359,6 +385,8 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     transposed and applied in reverse order (an independent route to S^T w).
     """
     _check_supported(g)
+    if g.bc[4] == BC_P:
+        raise ValueError("the transposed solve takes non-periodic z")
     w = np.asarray(w, dtype=np.float64)
     nx, ny, nz = g.nx, g.ny, g.nz
     sing = is_singular(g, alpha)

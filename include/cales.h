@@ -56,7 +56,9 @@ enum cales_status {
     CALES_OK = 0,
     CALES_EINVAL = -1,       /* bad size, spacing, boundary pairing or argument  */
     CALES_EUNSUPPORTED = -2, /* odd length > 1 or a radix outside {2,3,5} in x/y,
-                                DF in x/y, periodic z                           */
+                                DF in x/y, periodic z with nz < 3 or on a path
+                                that needs z walls (refinement, adjoint, line
+                                solves, residual, allocation-free solve)        */
     CALES_ENOMEM = -3,       /* device allocation failed                        */
     CALES_ECUDA = -4,        /* a CUDA runtime call failed                      */
     CALES_ETOOBIG = -5       /* grid larger than the static scratch of
@@ -72,7 +74,15 @@ enum cales_device_status_bits {
  * Create a plan for an nx x ny x nz grid (paper Sec. 2.2: uniform x, y;
  * stretched z).  bc[6] = {xlo, xhi, ylo, yhi, zlo, zhi}; x and y take P, N or
  * D with the same kind on both sides and an even length (or 1) whose half
- * factors into 2, 3 and 5; z takes N, D or DF independently per side.
+ * factors into 2, 3 and 5; z takes N, D or DF independently per side, or P
+ * on both sides (nz >= 3; periodic on one side only is CALES_EINVAL).
+ * Periodic z: each mode's z system is cyclic (row 0 couples to row nz-1
+ * through dzc[0], row nz-1 to row 0 through dzc[nz]; give both the distance
+ * between the last and the first cell centre through the period) and is
+ * solved by the Sherman-Morrison form of the Thomas algorithm, one thread
+ * per mode, with 16 bytes per grid point of plan-owned scratch.  It serves
+ * the FP64 and FP32 Poisson and Helmholtz solves; all-periodic/Neumann
+ * Poisson problems are made consistent and gauged as below.
  * dx, dy: uniform spacings.  dzc[0..nz]: distance between unknowns k-1 and k
  * (dzc[0], dzc[nz]: to the ghost/boundary node; mirror value dzf[0] resp.
  * dzf[nz-1] for cell-centred unknowns).  dzf[0..nz-1]: control-volume width

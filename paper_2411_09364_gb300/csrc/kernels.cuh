@@ -194,6 +194,8 @@ cudaError_t launch_gradient(const GridArgs<T>&, const T*, const T*, const T*, co
 template <typename T>
 cudaError_t launch_divergence_T(const GridArgs<T>&, const T*, const T*, const T*, const T*, T*, T*, T*, cudaStream_t);
 template <typename T> cudaError_t launch_gradient_T(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
+// periodic z: cyclic tridiagonal per mode (Sherman-Morrison), two scratch fields [nz][nmodes]
+template <typename T> cudaError_t launch_zsolve_cyclic(const ZArgs<T>&, T* ework, T* zwork, cudaStream_t);
 template <typename T> cudaError_t launch_mom_predict(const MomArgs<T>&, cudaStream_t);
 template <typename T> cudaError_t launch_pressure_update(T* p, const T* phi, T scale, long n, cudaStream_t);
 // u, v, w -= grad phi' in place; p += (phi' - a L phi') * scale with L the full

@@ -340,7 +340,15 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     }
     za.ecache_stride = (long)P->nx * P->ny;
     P->prof_begin(st, "z_solve");
-    if (launch_zsolve<T>(za, st) != cudaSuccess) return CALES_ECUDA;
+    if (P->bc[4] == CALES_BC_P) {
+        if (o.adjoint || o.cacc) return CALES_EUNSUPPORTED;
+        T* ework = reinterpret_cast<T*>(P->zcyc);
+        if (launch_zsolve_cyclic<T>(za, ework, ework + (size_t)P->nx * P->ny * P->nz, st) != cudaSuccess)
+            return CALES_ECUDA;
+        za.ecache_mode = 0;
+    } else if (launch_zsolve<T>(za, st) != cudaSuccess) {
+        return CALES_ECUDA;
+    }
     if (za.ecache_mode == 1) {
         zk.valid = 1; zk.P = za.P; zk.maxm = za.maxm; zk.sigma = o.sigma; zk.alpha = o.alpha;
     }
@@ -441,6 +449,7 @@ int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint,
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {
     if (!P || !f || !p) return CALES_EINVAL;
     if (helm && !(alpha > 0.0)) return CALES_EINVAL;
+    if (P->bc[4] == CALES_BC_P && (adjoint || P->precision == CALES_FP32_REFINE)) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double nxy = (double)P->nx * (double)P->ny;
     PassOpt o;
@@ -557,7 +566,8 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         if (bc[i] < 0 || bc[i] > 3) return CALES_EINVAL;
     if (bc[0] != bc[1] || bc[2] != bc[3]) return (bc[0] == 0 || bc[1] == 0 || bc[2] == 0 || bc[3] == 0) ? CALES_EINVAL : CALES_EUNSUPPORTED;
     if (bc[0] == CALES_BC_DF || bc[2] == CALES_BC_DF) return CALES_EUNSUPPORTED;
-    if (bc[4] == CALES_BC_P || bc[5] == CALES_BC_P) return CALES_EUNSUPPORTED;
+    if ((bc[4] == CALES_BC_P) != (bc[5] == CALES_BC_P)) return CALES_EINVAL;
+    if (bc[4] == CALES_BC_P && nz < 3) return CALES_EUNSUPPORTED;
     for (int k = 0; k <= nz; ++k)
         if (!(dzc[k] > 0) || !std::isfinite(dzc[k])) return CALES_EINVAL;
     for (int k = 0; k < nz; ++k)
@@ -568,7 +578,8 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     P->nx = nx; P->ny = ny; P->nz = nz;
     for (int i = 0; i < 6; ++i) P->bc[i] = bc[i];
     P->dx = dx; P->dy = dy;
-    P->singular_poisson = (bc[0] != CALES_BC_D && bc[2] != CALES_BC_D && bc[4] == CALES_BC_N && bc[5] == CALES_BC_N) ? 1 : 0;
+    P->singular_poisson = (bc[0] != CALES_BC_D && bc[2] != CALES_BC_D && (bc[4] == CALES_BC_N || bc[4] == CALES_BC_P) &&
+                           (bc[5] == CALES_BC_N || bc[5] == CALES_BC_P)) ? 1 : 0;
     int rc = build_dir(P->X, nx, bc[0], dx, P->owned);
     if (rc == CALES_OK) rc = build_dir(P->Y, ny, bc[2], dy, P->owned);
     if (rc == CALES_OK) {
@@ -608,6 +619,11 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         for (int k = 0; k < nz; ++k) { zcen[k] = zacc + 0.5 * dzf[k]; zacc += dzf[k]; }
         P->zcen_d = dev_upload(zcen, P->owned);
         P->sgs_coef = dev_upload(std::vector<double>(nz, 0.0), P->owned);
+        if (bc[4] == CALES_BC_P) {
+            if (cudaMalloc(&P->zcyc, 2 * (size_t)nx * ny * nz * sizeof(double)) == cudaSuccess) P->owned.push_back(P->zcyc);
+            else P->zcyc = nullptr;
+            if (!P->zcyc) rc = CALES_ENOMEM;
+        }
         const int nzero = nx > ny ? nx : ny;
         P->zero_d = dev_upload(std::vector<double>(nzero, 0.0), P->owned);
         P->zero_f = dev_upload(std::vector<float>(nzero, 0.0f), P->owned);
@@ -636,6 +652,7 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
 
 int cales_set_precision(cales_plan_t P, int mode, int sweeps) {
     if (!P || mode < 0 || mode > 2 || sweeps < 0 || sweeps > 8) return CALES_EINVAL;
+    if (mode == CALES_FP32_REFINE && P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     if (mode == CALES_FP32_REFINE && !P->work) {
         void* w = nullptr;
         const size_t bytes = (size_t)P->nx * P->ny * P->nz * sizeof(float);
@@ -658,6 +675,7 @@ int cales_helmholtz_solve(cales_plan_t P, double alpha, const void* f, void* u, 
 
 int cales_helmholtz_z_solve(cales_plan_t P, double alpha, const void* f, void* u, void* stream) {
     if (!P || !f || !u || !(alpha >= 0.0) || !std::isfinite(alpha)) return CALES_EINVAL;
+    if (P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (P->precision == CALES_FP32) return z_lines<float>(P, alpha, (const float*)f, (float*)u, st);
     return z_lines<double>(P, alpha, (const double*)f, (double*)u, st);
@@ -673,6 +691,7 @@ int cales_helmholtz_solve_adjoint(cales_plan_t P, double alpha, const void* w, v
 
 int cales_residual(cales_plan_t P, double alpha, const double* u, const double* f, double* r, void* stream) {
     if (!P || !u || !f || !r) return CALES_EINVAL;
+    if (P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     ResidArgs ra;
     const bool helm = alpha >= 0.0;
     P->fill_resid(ra, u, f, r, true, helm ? 1.0 : 0.0, helm ? -alpha : 1.0);
@@ -775,6 +794,7 @@ int static_scratch(void** out) {
 
 extern "C" int cales_poisson_solve_noalloc(cales_plan_t P, const void* f, void* p, void* stream) {
     if (!P || !f || !p || f == p) return CALES_EINVAL;
+    if (P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     if ((long)P->nx * P->ny * P->nz > CALES_STATIC_SCRATCH_POINTS) return CALES_ETOOBIG;
     void* base = nullptr;
     int rc = static_scratch(&base);

@@ -44,6 +44,7 @@ struct cales_plan_s {
     float* za_f = nullptr;
     double* zcen_d = nullptr;    // cell-centre heights [nz], bottom face at 0
     double* sgs_coef = nullptr;  // [nz] eddy-viscosity plane coefficients (C_s Delta D)^2
+    void* zcyc = nullptr;        // periodic z: two [nz][nx*ny] scratch fields (FP64 size)
     double* zero_d = nullptr;    // max(nx, ny) zeros: the eigenvalues of the line solves
     float* zero_f = nullptr;
     float* zc_f = nullptr;

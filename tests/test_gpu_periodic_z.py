@@ -1,0 +1,74 @@
+"""Periodic z (cyclic tridiagonal per mode) through the C ABI against the
+oracle: FP64 and FP32 Poisson and Helmholtz solves on stretched periodic
+grids, every x/y kind, ragged sizes, the singular all-periodic case, and the
+paths that refuse a periodic z."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth_inputs as S
+from paper_2411_09364_gb300 import solver as cs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {cs.FP64: 1e-11, cs.FP32: 1e-5}
+
+
+def _periodic(dzc_dzf):
+    dzc, dzf = dzc_dzf
+    dzc = np.array(dzc, dtype=np.float64)
+    dzc[0] = dzc[-1] = 0.5 * (dzf[0] + dzf[-1])            # last centre to first through the period
+    return dzc, dzf
+
+
+def pair(nx, ny, nz, bcx, bcy, beta=1.5, precision=cs.FP64):
+    zf = S.tanh_faces(nz, beta, 2.0)
+    bc = (bcx, bcx, bcy, bcy, O.BC_P, O.BC_P)
+    odzc, odzf = _periodic(O.cell_spacings(zf))
+    gdzc, gdzf = _periodic(cs.cell_spacings(zf))
+    g = O.Grid(nx, ny, nz, 2 * math.pi / nx, 1.3 / ny, odzc, odzf, bc)
+    return g, cs.Plan(nx, ny, nz, bc, 2 * math.pi / nx, 1.3 / ny, gdzc, gdzf, precision)
+
+
+@pytest.mark.parametrize("shape", [(48, 20, 33), (64, 32, 64), (16, 1, 3)])
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_P, O.BC_P), (O.BC_P, O.BC_N), (O.BC_N, O.BC_D), (O.BC_D, O.BC_P)])
+@pytest.mark.parametrize("alpha", [None, 2e-3])
+@pytest.mark.parametrize("precision", [cs.FP64, cs.FP32])
+def test_periodic_z_against_oracle(cuda_device, shape, bcx, bcy, alpha, precision):
+    nx, ny, nz = shape
+    g, plan = pair(nx, ny, nz, bcx, bcy, precision=precision)
+    f = S.gaussian(700 + nx + nz + bcx * 3 + bcy, (nz, ny, nx))
+    x = torch.from_numpy(f).to("cuda", plan.dtype)
+    out = plan.poisson(x) if alpha is None else plan.helmholtz(alpha, x)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    ref = O.solve(f, g, alpha)
+    assert O.rel_l2(got, ref) <= TOL[precision]
+    if O.is_singular(g, alpha):
+        assert abs(O.weighted_mean(got, g)) <= (1e-10 if precision == cs.FP64 else 1e-6) * np.max(np.abs(ref))
+
+
+def test_periodic_z_in_place_and_repeatable(cuda_device):
+    g, plan = pair(32, 16, 24, O.BC_P, O.BC_P)
+    f = S.gaussian(760, (24, 16, 32))
+    x = torch.from_numpy(f).cuda()
+    y = plan.poisson(x.clone())
+    x2 = x.clone()
+    plan.poisson(x2, x2)
+    torch.cuda.synchronize()
+    assert torch.equal(x2, y)
+    assert O.rel_l2(y.cpu().numpy(), O.solve(f, g)) <= TOL[cs.FP64]
+
+
+def test_periodic_z_refuses_wall_only_paths(cuda_device):
+    g, plan = pair(16, 8, 8, O.BC_P, O.BC_P)
+    f = torch.zeros((8, 8, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(Exception):
+        plan.set_precision(cs.FP32_REFINE)
+    with pytest.raises(Exception):
+        plan.helmholtz_z(1e-3, f)
+    with pytest.raises(Exception):
+        plan.poisson_adjoint(f)

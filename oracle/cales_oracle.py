@@ -41,7 +41,7 @@ BC_P, BC_N, BC_D, BC_DF = 0, 1, 2, 3
 BC_NAMES = {"P": BC_P, "N": BC_N, "D": BC_D, "DF": BC_DF}
 
 __all__ = [
-    "BC_P", "BC_N", "BC_D", "BC_DF", "BC_NAMES", "Grid", "cell_spacings",
+    "BC_P", "BC_N", "BC_D", "BC_DF", "BC_NAMES", "KIND_ND", "KIND_DN", "dir_kind", "Grid", "cell_spacings",
     "face_spacings", "apply_L", "apply_M", "fwd_matrix", "inv_matrix",
     "eigenvalues", "z_operator", "thomas", "is_singular", "weighted_mean",
     "project", "solve", "solve_z_lines", "solve_T", "dense_matrix", "dense_solve", "residual",
@@ -151,14 +151,39 @@ def _cos_sin_frac(num: np.ndarray, den: int):
     return np.cos(2.0 * math.pi * r), np.sin(2.0 * math.pi * r)
 
 
+# Transform kinds of a uniform direction with different sides: Neumann below
+# and Dirichlet above (KIND_ND), or the reverse (KIND_DN).
+KIND_ND, KIND_DN = 4, 5
+
+
+def dir_kind(lo: int, hi: int) -> int:
+    """Transform kind of a uniform direction from its two sides."""
+    if lo == hi:
+        return lo
+    if (lo, hi) == (BC_N, BC_D):
+        return KIND_ND
+    if (lo, hi) == (BC_D, BC_N):
+        return KIND_DN
+    raise ValueError(f"no transform for the sides ({lo}, {hi})")
+
+
 def fwd_matrix(kind: int, n: int) -> np.ndarray:
     """Forward transform matrix of one uniform direction.
 
     P : F[m, i] = exp(-2 pi i m i / n)                  (complex DFT)
     N : C[m, i] = cos(pi m (i + 1/2) / n), m = 0..n-1    (DCT-II)
     D : S[m, i] = sin(pi m (i + 1/2) / n), m = 1..n      (DST-II), row m-1
+    DF: S[m, i] = sin(pi (m+1) (i+1) / (n+1))            (DST-I; n interior nodes)
+    ND: C[m, i] = cos(pi (m + 1/2) (i + 1/2) / n)        (DCT-IV)
+    DN: S[m, i] = sin(pi (m + 1/2) (i + 1/2) / n)        (DST-IV)
     """
     i = np.arange(n, dtype=np.int64)
+    if kind == BC_DF:
+        _, s = _cos_sin_frac(np.outer(i + 1, i + 1), 2 * (n + 1))
+        return s
+    if kind in (KIND_ND, KIND_DN):
+        c, s = _cos_sin_frac(np.outer(2 * i + 1, 2 * i + 1), 8 * n)
+        return c if kind == KIND_ND else s
     if kind == BC_P:
         c, s = _cos_sin_frac(np.outer(i, i), n)
         return c - 1j * s
@@ -178,8 +203,14 @@ def inv_matrix(kind: int, n: int) -> np.ndarray:
 
     P : conj(F)^T / n.   N : DCT-III with weights 1/n (m=0) and 2/n.
     D : DST-III with weights 2/n (m<n) and 1/n (m=n).
+    DF, ND, DN: the matrices are symmetric and orthogonal up to the factor
+    (n+1)/2 resp. n/2, so the inverse is 2/(n+1) resp. 2/n times the matrix.
     """
     i = np.arange(n, dtype=np.int64)
+    if kind == BC_DF:
+        return fwd_matrix(BC_DF, n) * (2.0 / (n + 1))
+    if kind in (KIND_ND, KIND_DN):
+        return fwd_matrix(kind, n) * (2.0 / n)
     if kind == BC_P:
         return np.conj(fwd_matrix(BC_P, n)).T / n
     if kind == BC_N:
@@ -203,7 +234,15 @@ def eigenvalues(kind: int, n: int, h: float) -> np.ndarray:
     P : -(4/h^2) sin^2(pi m / n),      m = 0..n-1
     N : -(4/h^2) sin^2(pi m / (2n)),   m = 0..n-1
     D : -(4/h^2) sin^2(pi m / (2n)),   m = 1..n
+    DF: -(4/h^2) sin^2(pi m / (2(n+1))), m = 1..n      (h: node spacing)
+    ND, DN: -(4/h^2) sin^2(pi (2m+1) / (4n)), m = 0..n-1
     """
+    if kind == BC_DF:
+        m = np.arange(1, n + 1)
+        return -(4.0 / h ** 2) * np.sin(math.pi * m / (2.0 * (n + 1))) ** 2
+    if kind in (KIND_ND, KIND_DN):
+        m = np.arange(n)
+        return -(4.0 / h ** 2) * np.sin(math.pi * (2 * m + 1) / (4.0 * n)) ** 2
     if kind == BC_P:
         m = np.arange(n)
         return -(4.0 / h ** 2) * np.sin(math.pi * m / n) ** 2
@@ -283,8 +322,7 @@ def cyclic_solve(sub, diag, sup, rhs):
 
 def is_singular(g: Grid, alpha=None) -> bool:
     """Poisson with only periodic/Neumann sides: constants are in the null space."""
-    return (alpha is None and g.bc[0] in (BC_P, BC_N) and g.bc[2] in (BC_P, BC_N)
-            and g.bc[4] in (BC_P, BC_N) and g.bc[5] in (BC_P, BC_N))
+    return alpha is None and all(b in (BC_P, BC_N) for b in g.bc)
 
 
 def weighted_mean(f: np.ndarray, g: Grid) -> float:
@@ -299,8 +337,8 @@ def project(f: np.ndarray, g: Grid) -> np.ndarray:
 
 def _check_supported(g: Grid):
     for lo, hi in ((g.bc[0], g.bc[1]), (g.bc[2], g.bc[3])):
-        if lo != hi or lo not in (BC_P, BC_N, BC_D):
-            raise ValueError("uniform directions take P, N or D on both sides")
+        if (lo == BC_P) != (hi == BC_P) or (lo == BC_DF) != (hi == BC_DF):
+            raise ValueError("uniform directions take P or DF on both sides, or N / D per side")
     if (g.bc[4] == BC_P) != (g.bc[5] == BC_P):
         raise ValueError("a periodic z is periodic on both sides")
     if g.bc[4] == BC_P and g.nz < 3:
@@ -325,8 +363,8 @@ def _apply_along(mat: np.ndarray, a: np.ndarray, axis: int) -> np.ndarray:
 def _mode_tridiag(g: Grid, alpha):
     """Per-mode tridiagonal of Poisson (L_z + lambda) or Helmholtz (I - alpha(L_z + lambda))."""
     sub, diag, sup = z_operator(g)
-    lam = (eigenvalues(g.bc[2], g.ny, g.dy)[:, None]
-           + eigenvalues(g.bc[0], g.nx, g.dx)[None, :]).reshape(-1)
+    lam = (eigenvalues(dir_kind(g.bc[2], g.bc[3]), g.ny, g.dy)[:, None]
+           + eigenvalues(dir_kind(g.bc[0], g.bc[1]), g.nx, g.dx)[None, :]).reshape(-1)
     if alpha is None:
         return sub, diag[:, None] + lam[None, :], sup
     return -alpha * sub, 1.0 - alpha * (diag[:, None] + lam[None, :]), -alpha * sup
@@ -344,8 +382,8 @@ def solve(f: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     sing = is_singular(g, alpha)
     if sing:
         f = project(f, g)
-    fh = _apply_along(fwd_matrix(g.bc[0], nx), f, 2)
-    fh = _apply_along(fwd_matrix(g.bc[2], ny), fh, 1)
+    fh = _apply_along(fwd_matrix(dir_kind(g.bc[0], g.bc[1]), nx), f, 2)
+    fh = _apply_along(fwd_matrix(dir_kind(g.bc[2], g.bc[3]), ny), fh, 1)
     sub, diag, sup = _mode_tridiag(g, alpha)
     rhs = fh.reshape(nz, -1)
     per = g.bc[4] == BC_P
@@ -360,8 +398,8 @@ def solve(f: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     else:
         ph = line(sub, diag, sup, rhs)
     ph = ph.reshape(nz, ny, nx)
-    p = _apply_along(inv_matrix(g.bc[2], ny), ph, 1)
-    p = _apply_along(inv_matrix(g.bc[0], nx), p, 2)
+    p = _apply_along(inv_matrix(dir_kind(g.bc[2], g.bc[3]), ny), ph, 1)
+    p = _apply_along(inv_matrix(dir_kind(g.bc[0], g.bc[1]), nx), p, 2)
     p = np.real(p) if np.iscomplexobj(p) else p
     if sing:
         p = p - weighted_mean(p, g)
@@ -393,8 +431,8 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     mvec = (g.dzf / (g.dzf.sum() * nx * ny)).reshape(-1, 1, 1)
     if sing:   # gauge Z = I - 1 m^T  ->  Z^T w = w - m * sum(w)
         w = w - mvec * w.sum()
-    a = _apply_along(inv_matrix(g.bc[0], nx).T, w, 2)
-    a = _apply_along(inv_matrix(g.bc[2], ny).T, a, 1)
+    a = _apply_along(inv_matrix(dir_kind(g.bc[0], g.bc[1]), nx).T, w, 2)
+    a = _apply_along(inv_matrix(dir_kind(g.bc[2], g.bc[3]), ny).T, a, 1)
     sub, diag, sup = _mode_tridiag(g, alpha)
     rhs = a.reshape(nz, -1)
     # transposed tridiagonal: sub'[k] = sup[k-1], sup'[k] = sub[k+1]
@@ -420,8 +458,8 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     else:
         out = thomas(subT, diag, supT, rhs)
     out = out.reshape(nz, ny, nx)
-    out = _apply_along(fwd_matrix(g.bc[2], ny).T, out, 1)
-    out = _apply_along(fwd_matrix(g.bc[0], nx).T, out, 2)
+    out = _apply_along(fwd_matrix(dir_kind(g.bc[2], g.bc[3]), ny).T, out, 1)
+    out = _apply_along(fwd_matrix(dir_kind(g.bc[0], g.bc[1]), nx).T, out, 2)
     out = np.real(out) if np.iscomplexobj(out) else out
     if sing:   # projection Pi = I - 1 m^T  ->  Pi^T v = v - m * sum(v)
         out = out - mvec * out.sum()

@@ -56,3 +56,13 @@ def test_invalid_plans_are_rejected_on_host(lib):
     assert lib.cales_poisson_solve(None, None, None, None) == -1
     assert lib.cales_set_precision(None, 0, 2) == -1
     assert lib.cales_strerror(-2) == b"unsupported size or boundary combination"
+
+
+def test_next_row_entries_reject_null_plans_on_host(lib):
+    """The closure and substep entries check their plan before any device work."""
+    d = C.c_double
+    assert lib.cales_eddy_viscosity(None, d(0.1), d(1e-3), d(0.05), None, None, None, None, None) == -1
+    assert lib.cales_rk3_substep(None, 0, d(1e-3), d(1e-3), d(0.1), d(0.05), *([None] * 10)) == -1
+    assert lib.cales_rk3_substep_cn(None, None, None, 1, 0, d(1e-3), d(1e-3), d(0.1), d(0.05),
+                                    *([None] * 10)) == -1
+    assert lib.cales_helmholtz_z_solve(None, d(1e-3), None, None, None) == -1

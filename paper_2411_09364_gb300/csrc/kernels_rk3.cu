@@ -1,8 +1,15 @@
-// Explicit predictor of the low-storage RK3 pressure-correction substep
-// (Sec. 2.2, Eq. 11 with H_i of Eq. 15) on a channel (x, y periodic, no-slip
-// walls in z):
-//   R^k = H^k + nu L u^k,  H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j,
-//   u*  = u^k + dt (alpha R^k + beta R^{k-1} - gamma grad p^{k-1/2}).
+// Predictor of the low-storage RK3 pressure-correction substep (Sec. 2.2) on
+// a channel (x, y periodic, no-slip walls in z), H_i of Eq. 15:
+//   H_i = -d(u_i u_j)/dx_j + d(2 nu_t S_ij)/dx_j,
+//   explicit (Eq. 11):   R^k = H^k + nu L u^k,
+//                        u*  = u^k + dt (alpha R^k + beta R^{k-1} - gamma grad p^{k-1/2});
+//   Crank-Nicolson, all directions (Eqs. 17-18): R^k = H^k and the kernel writes
+//                        u** - a L u^k,  a = gamma nu dt / 2, the right-hand side of the
+//                        Helmholtz solve;
+//   Crank-Nicolson in z (Eqs. 20-21): R^k = H^k + nu (L_x + L_y) u^k and the
+//                        right-hand side u** - a L_z u^k of the line solves.
+// The last two are followed by the in-place correction and pressure update of
+// k_correct_cn (Eqs. 13, 19, 22).
 // The signs of H follow the momentum equation (Eq. 2) with the Boussinesq
 // closure (Eq. 3).  Advection is in divergence form with every interpolated
 // velocity the mean of its two neighbours; the off-diagonal strain rates sit

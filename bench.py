@@ -332,6 +332,25 @@ def run_configs(args):
             del uu, vv, ww, pp, nut, ru, rv, rw, work
         del plan, vel
         torch.cuda.empty_cache()
+    if want("periodic_z_poisson"):
+        # fully periodic box (x, y, z periodic; cyclic tridiagonal per mode), 512x256x256,
+        # stretched z with the wrap distance joining the last and the first cell centre
+        nx_, ny_, nz_ = 512, 256, 256
+        zf = S.tanh_faces(nz_, 1.5, 2.0)
+        dzc, dzf = cs.cell_spacings(zf)
+        dzc = np.array(dzc)
+        dzc[0] = dzc[-1] = 0.5 * (dzf[0] + dzf[-1])
+        plan = cs.Plan(nx_, ny_, nz_, (0, 0, 0, 0, 0, 0), 2 * math.pi / nx_, math.pi / ny_, dzc, dzf, cs.FP64)
+        fp = torch.from_numpy(S.gaussian(8000, (nz_, ny_, nx_))).to(dev)
+        for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32")):
+            plan.set_precision(mode)
+            fi = fp if mode == cs.FP64 else fp.float()
+            po = torch.empty_like(fi)
+            ms = timed(lambda: plan.poisson(fi, po), 10)
+            emit({"workload": f"periodic_z_poisson_{nx_}x{ny_}x{nz_}", "mode": name, "ms": ms,
+                  "gpoints_per_s": fi.numel() / ms / 1e6})
+        del plan, fp
+        torch.cuda.empty_cache()
     if want("differentiable_poisson"):
         # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
         plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)

@@ -7,8 +7,13 @@ mean removed.  One step = one Poisson solve in FP32 with double-float
 refinement (the default 2 sweeps) of a resident 3.2 GB FP64 right-hand side
 into a resident FP64 solution; the plain FP64 GPU solve is timed beside it.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  Besides the headline it carries the FP64 CPU
+oracle timed on a bounded sample of the workload (the 1536 x 512 cross-section
+on 16 z cells) with the GPU's error against the oracle's solution of that
+sample (``rel_err_vs_oracle``), and the timings of the other workloads
+(``configs``: the 64x32x32 and 512x256x192 channels, the 16-domain RK3
+substep graph, the differentiable 256x128x128 solve).  ``--impl reference``
+times the FP64 CPU oracle on the same sample instead.
 """
 from __future__ import annotations
 
@@ -30,8 +35,10 @@ import synth_inputs as S  # noqa: E402
 
 WORKLOAD = dict(name="duct_poisson_1536x512x512", nx=1536, ny=512, nz=512, bc=(0, 0, 1, 1, 1, 1),
                 lx=6.0, ly=2.0, lz=2.0, beta=1.5, seed=3000)
-# oracle sample of the same family for the CPU baseline / reference arm
-SAMPLE = dict(nx=384, ny=128, nz=128)
+# oracle sample of the same workload for the CPU baseline / reference arm: the
+# full 1536 x 512 cross-section (the benchmark's own x and y transform
+# kernels) on a thin stretched z; its oracle solution also pins the GPU error
+SAMPLE = dict(nx=1536, ny=512, nz=16)
 METRIC = "Gpoints/s per Poisson solve (FP32 + double-float refinement, rel err <= 1e-10 vs FP64)"
 UNIT = "Gpoints/s"
 # algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
@@ -52,13 +59,6 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
-
-
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", str(rank)))
-    return rank, world, local
 
 
 def grid_arrays(w=WORKLOAD, nx=None, ny=None, nz=None):
@@ -117,8 +117,7 @@ class Clocks:
 
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
-    rank, world, _ = dist_env()
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle as O
     nx, ny, nz = SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"]
@@ -147,7 +146,9 @@ def run_reference(args):
 
 
 def cpu_baseline_leg():
-    """The oracle as it stands, timed on a bounded sample (about 10-30 s of CPU work)."""
+    """The oracle as it stands, timed on a bounded sample (about 10-30 s of CPU
+    work).  Returns the timing record, the sample's right-hand side and the
+    oracle's solution of it."""
     import oracle as O
     nx, ny, nz = SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"]
     w = WORKLOAD
@@ -155,7 +156,7 @@ def cpu_baseline_leg():
     dzc, dzf = O.cell_spacings(zf)
     g = O.Grid(nx, ny, nz, w["lx"] / nx, w["ly"] / ny, dzc, dzf, w["bc"])
     f = make_rhs(nx, ny, nz, zf, w["seed"])
-    O.solve(f, g)
+    p = O.solve(f, g)
     reps, t0 = 0, time.perf_counter()
     while True:
         O.solve(f, g)
@@ -163,9 +164,141 @@ def cpu_baseline_leg():
         if time.perf_counter() - t0 > 12.0 or reps >= 200:
             break
     dt = (time.perf_counter() - t0) / reps
-    return {"value": nx * ny * nz / dt / 1e9, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": f"FP64 oracle solve of the same duct family at {nx}x{ny}x{nz}, "
-                                        f"{reps} repetitions ({dt:.2f} s each)"}
+    rec = {"value": nx * ny * nz / dt / 1e9, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+           "kind": "oracle", "sample": f"FP64 oracle solve of the benchmark workload's {nx}x{ny} cross-section "
+                                       f"on {nz} stretched z cells, {reps} repetitions ({dt:.2f} s each)"}
+    return rec, f, p
+
+
+def oracle_error(cs, dev, f_s, p_s):
+    """Error of the GPU solves of the oracle's sample (the benchmark workload's
+    1536 x 512 cross-section on a thin z: the benchmark's x and y kernels)
+    against the oracle's solution, relative L2 over all points and the largest
+    point error relative to max |p|."""
+    import torch
+    nx, ny, nz = SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"]
+    w = WORKLOAD
+    zf = S.tanh_faces(nz, w["beta"], w["lz"])
+    dzc, dzf = cs.cell_spacings(zf)
+    plan = cs.Plan(nx, ny, nz, w["bc"], w["lx"] / nx, w["ly"] / ny, dzc, dzf, cs.FP32_REFINE, 2)
+    ref = torch.from_numpy(p_s).to(dev)
+    fd = torch.from_numpy(f_s).to(dev)
+    out = {"sample": f"{nx}x{ny}x{nz} of the benchmark workload (oracle solution of the cpu_baseline leg)"}
+    for mode, name in ((cs.FP32_REFINE, "fp32_refine"), (cs.FP64, "fp64"), (cs.FP32, "fp32")):
+        plan.set_precision(mode, 2)
+        x = fd if mode != cs.FP32 else fd.float()
+        p = plan.poisson(x).double()
+        d = p - ref
+        out[name] = {"rel_l2": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(ref)),
+                     "max_abs_rel": float(d.abs().max() / ref.abs().max())}
+    out["device_status"] = plan.status()
+    return out
+
+
+def _event_ms(fn, reps, flush=None):
+    """Mean device time of fn over reps calls (CUDA events on the current
+    stream, 3 warm-up calls first); with flush, an L2-sized buffer is
+    rewritten before every timed call, outside the timed interval."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    if flush is None:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        flush.add_(1.0)
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+
+def other_configs(dev):
+    """The other workloads of the solver, timed inside the default run (about
+    20 s): the 64x32x32 channel (FP64; warm L2 and L2 flushed), the
+    512x256x192 channel (FP64, FP32, FP32 + refinement; right-hand side = the
+    discrete divergence of a seeded Gaussian velocity), the RK3 substep of 16
+    uneven channel domains in one CUDA graph (FP32 + refinement; warm and
+    flushed) and the differentiable 256x128x128 solve (FP32 forward +
+    backward)."""
+    import torch
+    from paper_2411_09364_gb300 import autograd as AG
+    from paper_2411_09364_gb300 import batch as B
+    from paper_2411_09364_gb300 import solver as cs
+    hbm = peaks()[0]
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)      # 256 MB > L2 (129 MB)
+    res = {}
+    # channel 64x32x32, P,P,N, uniform z, FP64 (fits L2: latency-bound)
+    plan = cs.channel_plan(64, 32, 32, beta=0.0)
+    f = torch.from_numpy(S.remove_mean(S.uniform(1000, (32, 32, 64)))).to(dev)
+    p = torch.empty_like(f)
+    warm = _event_ms(lambda: plan.poisson(f, p), 200)
+    cold = _event_ms(lambda: plan.poisson(f, p), 50, flush)
+    res["channel_poisson_64x32x32"] = {"mode": "fp64", "ms_warm_l2": warm, "ms_l2_flushed": cold,
+                                       "solves_per_s_warm_l2": 1e3 / warm,
+                                       "gpoints_per_s_warm_l2": f.numel() / warm / 1e6,
+                                       "gpoints_per_s_l2_flushed": f.numel() / cold / 1e6}
+    del plan
+    # channel 512x256x192, P,P,N, tanh 1.8, f = div of a Gaussian staggered velocity (walls w = 0)
+    nx, ny, nz = 512, 256, 192
+    plan = cs.channel_plan(nx, ny, nz, beta=1.8)
+    u, v, w = (torch.from_numpy(a).to(dev) for a in S.velocity_field(2000, nx, ny, nz))
+    f64 = AG.divergence(plan, u, v, w)
+    del u, v, w
+    ch = {"rhs": "discrete divergence of a seeded Gaussian staggered velocity (sigma 1, w = 0 on the walls)",
+          "l2": "f and p 201 MB (FP64) each, larger than L2"}
+    p64 = None
+    for mode, name in ((cs.FP64, "fp64"), (cs.FP32, "fp32"), (cs.FP32_REFINE, "fp32_refine")):
+        plan.set_precision(mode, 2)
+        fi = f64 if mode != cs.FP32 else f64.float()
+        po = torch.empty_like(fi)
+        ms = _event_ms(lambda: plan.poisson(fi, po), 20)
+        if mode == cs.FP64:
+            p64 = po.clone()
+        rel = float(torch.linalg.vector_norm(po.double() - p64) / torch.linalg.vector_norm(p64))
+        ch[name] = {"ms": ms, "gpoints_per_s": fi.numel() / ms / 1e6, "solves_per_s": 1e3 / ms,
+                    "rel_err_vs_fp64_gpu": rel,
+                    "min_traffic_roofline_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / hbm}
+    res["channel_poisson_512x256x192"] = ch
+    del plan, f64, p64, fi, po
+    # 16 channel domains x {u, v, w Helmholtz, p Poisson}, FP32 + refinement, one CUDA graph
+    alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
+    batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
+    fs = [torch.from_numpy(S.gaussian(4000 + i, pl.shape)).to(dev) for i, pl in enumerate(plans)]
+    us = [torch.empty_like(x) for x in fs]
+    st = batch.capture(fs, us)
+    with torch.cuda.stream(st):
+        warm = _event_ms(lambda: batch.launch(st), 10)
+        cold = _event_ms(lambda: batch.launch(st), 10, flush)
+    pts = sum(pl.numel for pl in plans)
+    res["rk3_substep_16_channel_domains"] = {
+        "mode": "fp32_refine", "solves": len(plans), "graph_nodes": batch.graph_nodes(),
+        "ms_warm_l2": warm, "ms_l2_flushed": cold, "gpoint_solves_per_s_warm_l2": pts / warm / 1e6,
+        "gpoint_solves_per_s_l2_flushed": pts / cold / 1e6,
+        "l2": "inputs 1.76 GB in total (the small domains fit L2)"}
+    del batch, plans, fs, us
+    # differentiable 256x128x128 solve, FP32, forward + backward through the adjoint kernel
+    plan = cs.channel_plan(256, 128, 128, beta=1.8, precision=cs.FP32)
+    fd = torch.from_numpy(S.gaussian(5000, (128, 128, 256))).to(dev, torch.float32).requires_grad_(True)
+    wd = torch.from_numpy(S.gaussian(5001, (128, 128, 256))).to(dev, torch.float32)
+
+    def fwd_bwd():
+        fd.grad = None
+        (wd * AG.poisson_solve(fd, plan)).sum().backward()
+    ms = _event_ms(fwd_bwd, 20)
+    res["differentiable_poisson_256x128x128"] = {"mode": "fp32 forward+backward", "ms": ms,
+                                                 "gpoints_per_s": fd.numel() / ms / 1e6}
+    del plan, fd, wd, flush
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_configs(args):
@@ -374,6 +507,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the timings of the other workloads")
     ap.add_argument("--small", action="store_true", help="512x256x192 channel variant (profiling)")
     ap.add_argument("--shape", default=None, help="NX,NY,NZ: the duct at another size (profiling case)")
     ap.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each)")
@@ -387,6 +521,7 @@ def main():
     import torch
     import torch.distributed as dist
 
+    from paper_2411_09364_gb300.replicas import dist_env
     rank, world, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
@@ -559,7 +694,11 @@ def main():
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_leg()
+        rec, f_s, p_s = cpu_baseline_leg()
+        line["cpu_baseline"] = rec
+        line["rel_err_vs_oracle"] = oracle_error(cs, dev, f_s, p_s)
+    if not args.no_configs:
+        line["configs"] = other_configs(dev)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -67,7 +67,9 @@ enum cales_status {
 
 enum cales_device_status_bits {
     CALES_DEV_NONFINITE = 1, /* a non-finite value was produced               */
-    CALES_DEV_BADPIVOT = 2   /* a non-positive pivot met outside the pinned mode */
+    CALES_DEV_BADPIVOT = 2,  /* a non-positive pivot met outside the pinned mode */
+    CALES_DEV_TIMEOUT = 4    /* a bounded wait for an asynchronous copy gave up;
+                                the kernel skipped its tile and returned      */
 };
 
 /*
@@ -77,12 +79,16 @@ enum cales_device_status_bits {
  * factors into 2, 3 and 5; z takes N, D or DF independently per side, or P
  * on both sides (nz >= 3; periodic on one side only is CALES_EINVAL).
  * Periodic z: each mode's z system is cyclic (row 0 couples to row nz-1
- * through dzc[0], row nz-1 to row 0 through dzc[nz]; give both the distance
- * between the last and the first cell centre through the period) and is
- * solved by the Sherman-Morrison form of the Thomas algorithm, one thread
- * per mode, with 16 bytes per grid point of plan-owned scratch.  It serves
- * the FP64 and FP32 Poisson and Helmholtz solves; all-periodic/Neumann
- * Poisson problems are made consistent and gauged as below.
+ * through dzc[0], row nz-1 to row 0 through dzc[nz]; both must hold the same
+ * distance, the one between the last and the first cell centre through the
+ * period, else CALES_EINVAL).  Row 0 is eliminated last: rows 1..nz-1 are a
+ * tridiagonal T solved by Thomas with excess-form pivots for two right-hand
+ * sides (the data, and the couplings to u[0]), u = p + u[0] (1 - q), and
+ * u[0] follows from row 0 through a denominator that is a sum of positive
+ * terms.  One thread per mode, 16 bytes per grid point of plan-owned
+ * scratch.  It serves the FP64 and FP32 Poisson and Helmholtz solves;
+ * all-periodic/Neumann Poisson problems are made consistent, their zero
+ * mode pinned and the result gauged as below.
  * dx, dy: uniform spacings.  dzc[0..nz]: distance between unknowns k-1 and k
  * (dzc[0], dzc[nz]: to the ghost/boundary node; mirror value dzf[0] resp.
  * dzf[nz-1] for cell-centred unknowns).  dzf[0..nz-1]: control-volume width
@@ -138,10 +144,11 @@ int cales_helmholtz_z_solve(cales_plan_t plan, double alpha, const void* f, void
 /*
  * Poisson solve like cales_poisson_solve with FP32 solves and double-float
  * refinement (the plan's refine_sweeps), for callers that cannot allocate
- * device memory when they solve: code running inside CUDA stream capture,
- * hosts that give the library a fixed memory budget, loops that must not
- * stall in the allocator.  No counterpart in the paper (an interface
- * addition).  It allocates nothing: its scratch (4 bytes per grid point plus
+ * device memory when they solve: hosts that hand the library a fixed
+ * device-memory budget and fail any further allocation (another framework's
+ * memory pool owns the rest of the GPU), and time-stepping loops that must
+ * not block in cudaMalloc, which may synchronise the device.  No counterpart
+ * in the paper (an interface addition).  It allocates nothing: its scratch (4 bytes per grid point plus
  * 256 bytes) is one file-scope device array of the library, sized for at most
  * 8,388,608 grid points (8 * 2^20); larger grids return CALES_ETOOBIG.  The
  * plan needs no cales_set_precision call; f, p: double device arrays, f != p.

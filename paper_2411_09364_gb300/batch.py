@@ -16,14 +16,7 @@ import numpy as np
 import torch
 
 from . import _native as N
-from .solver import FP32_REFINE, Plan, _stream, cell_spacings, face_spacings
-
-
-def tanh_faces(nz: int, beta: float, lz: float = 2.0) -> np.ndarray:
-    k = np.arange(nz + 1, dtype=np.float64)
-    if beta <= 0:
-        return lz * k / nz
-    return 0.5 * lz * (1.0 + np.tanh(beta * (2.0 * k / nz - 1.0)) / math.tanh(beta))
+from .solver import FP32_REFINE, Plan, _stream, cell_spacings, face_spacings, tanh_faces
 
 
 class Batch:

@@ -399,21 +399,23 @@ void cales_plan_s::prof_end(cudaStream_t st) {
 // consistency constant of f is estimated from the first mode-space solve and
 // refined by every sweep (acc[0]); the dzf-weighted mean of the solution is
 // measured by each residual pass (acc[1]) and removed by the same sweep.
-static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, void* p, PassOpt o, cudaStream_t st) {
+// work: one FP32 field (mode space and residual); acc: two FP64 accumulators.
+static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, void* p, PassOpt o, float* work,
+                        double* acc, cudaStream_t st) {
     const int ns = P->sweeps;
     const bool sing = o.singular;
-    if (cudaMemsetAsync(P->acc, 0, 2 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
-    o.cacc = sing ? P->acc : nullptr;
-    int rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, P->work, o, st)
-                     : pipeline<float, double, OUT_FF_INIT>(P, f, p, P->work, o, st);
+    if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+    o.cacc = sing ? acc : nullptr;
+    int rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, work, o, st)
+                     : pipeline<float, double, OUT_FF_INIT>(P, f, p, work, o, st);
     if (rc) return rc;
     const double c1 = helm ? -alpha : 1.0;
     for (int s = 0; s < ns; ++s) {
-        if (sing && cudaMemsetAsync(P->acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+        if (sing && cudaMemsetAsync(acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
         ResidFFArgs ra;
         ra.f = (const double*)f;
         ra.u = (const float2*)p;
-        ra.r = P->work;
+        ra.r = work;
         ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
         ra.bcx = P->bc[0]; ra.bcy = P->bc[2]; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
         split_double(c1 / (P->dx * P->dx), ra.cxh, ra.cxl);
@@ -422,18 +424,18 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
         ra.za = P->za_d;
         ra.zc = P->zc_d;
         ra.c1 = c1;
-        ra.cshift = sing ? P->acc : nullptr;
+        ra.cshift = sing ? acc : nullptr;
         // the gauge of p is measured by the last sweep only: the operator
         // annihilates constants, so earlier iterates may carry any mean
-        ra.gacc = (sing && s == ns - 1) ? P->acc + 1 : nullptr;
+        ra.gacc = (sing && s == ns - 1) ? acc + 1 : nullptr;
         ra.dzf = P->dzf_d;
         P->prof_begin(st, "residual");
         if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
         P->prof_end(st);
-        o.shift_acc = (sing && s == ns - 1) ? P->acc + 1 : nullptr;
+        o.shift_acc = (sing && s == ns - 1) ? acc + 1 : nullptr;
         o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
-        rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, P->work, p, P->work, o, st)
-                           : pipeline<float, float, OUT_FF_ACC>(P, P->work, p, P->work, o, st);
+        rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, work, p, work, o, st)
+                           : pipeline<float, float, OUT_FF_ACC>(P, work, p, work, o, st);
         if (rc) return rc;
     }
     return CALES_OK;
@@ -469,7 +471,7 @@ static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, c
         case CALES_FP32_REFINE:
             if (adjoint) return CALES_EUNSUPPORTED;
             if (f == p || !P->work) return CALES_EINVAL;
-            return refine_solve(P, helm, alpha, f, p, o, st);
+            return refine_solve(P, helm, alpha, f, p, o, P->work, P->acc, st);
         default:
             return CALES_EINVAL;
     }
@@ -572,6 +574,9 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
         if (!(dzc[k] > 0) || !std::isfinite(dzc[k])) return CALES_EINVAL;
     for (int k = 0; k < nz; ++k)
         if (!(dzf[k] > 0) || !std::isfinite(dzf[k])) return CALES_EINVAL;
+    // periodic z: dzc[0] and dzc[nz] are the same wrap-around distance; the
+    // operator only telescopes under dzf weighting when they agree
+    if (bc[4] == CALES_BC_P && std::fabs(dzc[0] - dzc[nz]) > 1e-12 * dzc[0]) return CALES_EINVAL;
 
     cales_plan_s* P = new (std::nothrow) cales_plan_s();
     if (!P) return CALES_ENOMEM;
@@ -808,39 +813,11 @@ extern "C" int cales_poisson_solve_noalloc(cales_plan_t P, const void* f, void* 
     o.scale = -1.0 / ((double)P->nx * (double)P->ny);
     o.singular = P->singular_poisson != 0;
     o.adjoint = false;
-    o.cacc = o.singular ? acc : nullptr;
+    o.cacc = nullptr;
     o.shift_acc = nullptr;
     o.shift_scale = 0.0;
-    const int ns = P->sweeps;
-    const bool sing = o.singular;
-    // the array keeps the previous call's contents: clear the accumulators
-    if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
-    rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, work, o, st)
-                 : pipeline<float, double, OUT_FF_INIT>(P, f, p, work, o, st);
-    if (rc) return rc;
-    for (int s = 0; s < ns; ++s) {
-        if (sing && cudaMemsetAsync(acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
-        ResidFFArgs ra;
-        ra.f = (const double*)f;
-        ra.u = (const float2*)p;
-        ra.r = work;
-        ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
-        ra.bcx = P->bc[0]; ra.bcy = P->bc[2]; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
-        split_double(1.0 / (P->dx * P->dx), ra.cxh, ra.cxl);
-        split_double(1.0 / (P->dy * P->dy), ra.cyh, ra.cyl);
-        ra.c0h = 0.0f;
-        ra.za = P->za_d;
-        ra.zc = P->zc_d;
-        ra.c1 = 1.0;
-        ra.cshift = sing ? acc : nullptr;
-        ra.gacc = (sing && s == ns - 1) ? acc + 1 : nullptr;
-        ra.dzf = P->dzf_d;
-        if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
-        o.shift_acc = (sing && s == ns - 1) ? acc + 1 : nullptr;
-        o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
-        rc = (s == ns - 1) ? pipeline<float, float, OUT_FF_FINAL>(P, work, p, work, o, st)
-                           : pipeline<float, float, OUT_FF_ACC>(P, work, p, work, o, st);
-        if (rc) return rc;
-    }
-    return CALES_OK;
+    // the same refinement as cales_poisson_solve on an FP32_REFINE plan, with
+    // the scratch taken from the static array (it keeps the previous call's
+    // contents: refine_solve clears the accumulators itself)
+    return refine_solve(P, false, 0.0, f, p, o, work, acc, st);
 }

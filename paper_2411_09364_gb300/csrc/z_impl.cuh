@@ -36,8 +36,13 @@ namespace cales {
 template <typename T> __device__ __forceinline__ T rcp_(T d);
 template <> __device__ __forceinline__ float rcp_<float>(float d) { return __frcp_rn(d); }
 // FP64: FP32 reciprocal refined by two Newton steps (24 -> 48 -> ~53 bits);
-// IEEE FP64 division is far slower on GB300's narrow FP64 pipe.
+// IEEE FP64 division is far slower on GB300's narrow FP64 pipe.  The FP32
+// seed needs 1/d to be a normal float: |d| in [2^-125, 2^125), tested on the
+// exponent bits with integer operations; anything else (zero, tiny, huge,
+// non-finite) takes the division.
 template <> __device__ __forceinline__ double rcp_<double>(double d) {
+    const unsigned e = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+    if (e - 898u > 249u) return 1.0 / d;
     double r = (double)__frcp_rn((float)d);
     r = r * fma(-d, r, 2.0);
     r = r * fma(-d, r, 2.0);

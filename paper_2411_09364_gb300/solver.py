@@ -282,12 +282,19 @@ def cales_destroy(plan: Plan) -> None:
     plan.close()
 
 
+def tanh_faces(nz: int, beta: float, lz: float = 2.0) -> np.ndarray:
+    """Wall-normal faces z_k = lz/2 (1 + tanh(beta (2k/nz - 1)) / tanh(beta)), k = 0..nz,
+    of a channel or duct clustered at both walls; beta <= 0 gives a uniform grid."""
+    k = np.arange(nz + 1, dtype=np.float64)
+    if beta <= 0:
+        return lz * k / nz
+    return 0.5 * lz * (1.0 + np.tanh(beta * (2.0 * k / nz - 1.0)) / math.tanh(beta))
+
+
 def channel_plan(nx, ny, nz, beta=1.8, lx=2 * math.pi, ly=math.pi, lz=2.0, bc=(0, 0, 0, 0, 1, 1),
                  precision=FP64, sweeps=2, faces=None):
     """Plan on a tanh-stretched channel grid (cell-centred unknowns in z)."""
     if faces is None:
-        k = np.arange(nz + 1, dtype=np.float64)
-        faces = (lz * k / nz if beta <= 0 else
-                 0.5 * lz * (1.0 + np.tanh(beta * (2.0 * k / nz - 1.0)) / math.tanh(beta)))
+        faces = tanh_faces(nz, beta, lz)
     dzc, dzf = cell_spacings(faces)
     return Plan(nx, ny, nz, bc, lx / nx, ly / ny, dzc, dzf, precision, sweeps)

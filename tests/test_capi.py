@@ -50,6 +50,10 @@ def test_invalid_plans_are_rejected_on_host(lib):
     assert args(4, 4, 8, (C.c_int * 6)(3, 3, 0, 0, 1, 1)) == -2    # node unknowns in x
     assert args(4, 4, 2, (C.c_int * 6)(0, 0, 0, 0, 0, 0)) == -2    # periodic z needs three cells
     assert args(4, 4, 8, (C.c_int * 6)(0, 0, 0, 0, 0, 1)) == -1    # periodic z on one side only
+    wrap = np.ones(9)
+    wrap[8] = 1.5                                  # periodic z: dzc[0] and dzc[nz] disagree
+    assert lib.cales_plan(C.byref(h), 4, 4, 8, (C.c_int * 6)(0, 0, 0, 0, 0, 0), 1.0, 1.0,
+                          wrap.ctypes.data_as(dp), dzf.ctypes.data_as(dp)) == -1
     bad = np.ones(9)
     bad[3] = 0.0
     assert lib.cales_plan(C.byref(h), 4, 4, 8, bc, 1.0, 1.0, bad.ctypes.data_as(dp), dzf.ctypes.data_as(dp)) == -1

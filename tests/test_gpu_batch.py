@@ -95,7 +95,7 @@ def test_autotune_sets_and_caches_a_schedule(cuda_device, tmp_path):
 def test_rk3_substep_16_domains_graph(cuda_device):
     """The 16 uneven channel domains (64^3 ... 384x192x160): u, v, w Helmholtz
     (alpha 1e-4 / 1e-3 alternating) and p Poisson per domain, FP32 + refinement,
-    one CUDA graph; checked on sampled domains against the oracle."""
+    one CUDA graph; every one of the 64 solves checked against the oracle."""
     alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
     batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
     fs = [torch.from_numpy(S.gaussian(4000 + 10 * d + i, p.shape)).cuda()
@@ -104,10 +104,13 @@ def test_rk3_substep_16_domains_graph(cuda_device):
     st = batch.capture(fs, us)
     batch.launch(st)
     st.synchronize()
-    for k in (0, 5, 10, 13):           # u of domain 0, v of 1, w of 2, v of 3
-        d, name = tags[k]
+    worst = {}
+    for k, (d, name) in enumerate(tags):
         o = O.solve(fs[k].cpu().numpy(), _oracle_grid(plans[k]), None if name == "p" else alphas[d])
-        assert O.rel_l2(us[k].cpu().numpy(), o) <= 1e-10, (d, name)
+        rel = O.rel_l2(us[k].cpu().numpy(), o)
+        worst[name] = max(worst.get(name, 0.0), rel)
+        assert rel <= 1e-10, (d, name, rel)
+    print("worst rel err per field over the 16 domains:", worst)
     for _ in range(2):
         batch.launch(st)
     st.synchronize()

@@ -14,7 +14,7 @@ from paper_2411_09364_gb300 import solver as cs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {cs.FP64: 1e-11, cs.FP32: 1e-5}
+TOL = {cs.FP64: 1e-12, cs.FP32: 1e-5}
 
 
 def _periodic(dzc_dzf):
@@ -46,7 +46,9 @@ def test_periodic_z_against_oracle(cuda_device, shape, bcx, bcy, alpha, precisio
     torch.cuda.synchronize()
     got = out.double().cpu().numpy()
     ref = O.solve(f, g, alpha)
-    assert O.rel_l2(got, ref) <= TOL[precision]
+    rel = O.rel_l2(got, ref)
+    print(f"periodic z {shape} bc {bcx},{bcy} alpha {alpha} prec {precision}: rel {rel:.3e}")
+    assert rel <= TOL[precision]
     if O.is_singular(g, alpha):
         assert abs(O.weighted_mean(got, g)) <= (1e-10 if precision == cs.FP64 else 1e-6) * np.max(np.abs(ref))
 

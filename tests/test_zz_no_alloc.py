@@ -1,9 +1,12 @@
 """cales_poisson_solve_noalloc: the Poisson solve for callers that cannot
-allocate device memory at solve time (inside stream capture, under a fixed
-memory budget).  It takes its scratch from a static device array of the
-library instead of the plan's workspace; its result must match the regular
-FP32 + refinement entry point within the refinement tolerance, call after call
-(the shared array keeps the previous call's contents).
+allocate device memory at solve time (a host that gives the library a fixed
+memory budget, a time-stepping loop that must not block in the allocator).
+It takes its scratch from a static device array of the library instead of
+the plan's workspace; its result must match the regular FP32 + refinement
+entry point within the refinement tolerance, call after call (the shared
+array keeps the previous call's contents).  It runs on plans of any
+precision; on an FP32 or FP32 + refinement plan it shares the plan's cache of
+FP32 z pivots with the regular solves.
 
 Collected last on purpose (file name), so a failure here stops a ``-x`` run
 only after every other test has run.
@@ -34,12 +37,13 @@ def _noalloc(plan, f, p):
 
 
 @pytest.mark.parametrize("bc,beta", [((0, 0, 0, 0, 1, 1), 1.8), ((0, 0, 1, 1, 1, 1), 1.5), ((1, 1, 2, 2, 2, 3), 1.2)])
-def test_noalloc_matches_refine_entry_point_twice(cuda_device, bc, beta):
+@pytest.mark.parametrize("noalloc_precision", [cs.FP64, cs.FP32_REFINE])
+def test_noalloc_matches_refine_entry_point_twice(cuda_device, bc, beta, noalloc_precision):
     nx, ny, nz = 96, 48, 40
     zf = S.tanh_faces(nz + 1 if bc[5] == 3 else nz, beta)
     dzc, dzf = (cs.face_spacings if bc[5] == 3 else cs.cell_spacings)(zf)
     plan = cs.Plan(nx, ny, nz, bc, 2 * math.pi / nx, math.pi / ny, dzc, dzf, cs.FP32_REFINE, 2)
-    noalloc_plan = cs.Plan(nx, ny, nz, bc, 2 * math.pi / nx, math.pi / ny, dzc, dzf, cs.FP64, 2)
+    noalloc_plan = cs.Plan(nx, ny, nz, bc, 2 * math.pi / nx, math.pi / ny, dzc, dzf, noalloc_precision, 2)
     for seed in (41, 42):
         f = torch.from_numpy(S.gaussian(seed, (nz, ny, nx))).to(cuda_device)
         ref = plan.poisson(f)

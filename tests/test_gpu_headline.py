@@ -88,11 +88,15 @@ def test_bench_xy_kernels_vs_oracle(cuda_device, nz):
 
 def test_bench_z_depth_vs_oracle(cuda_device):
     """64 x 32 x 512 duct: the benchmark's 512-row stretched z lines (16
-    segments of 32 rows, cached segment-entry pivots on the second solve)."""
+    segments of 32 rows, cached segment-entry pivots on the second solve).
+    The reference is the oracle's solve with one FP64 refinement step: the
+    plain expansion's scalar Thomas sweeps are themselves off by about 1e-12
+    on the near-singular modes of this grid (condition numbers near 3e6),
+    which is the FP64 tolerance."""
     nx, ny, nz = 64, 32, 512
     g, plan, zf = duct_pair(nx, ny, nz)
     f = S.remove_mean(S.gaussian(3001, (nz, ny, nx)), np.diff(zf))
-    ref = O.solve(f, g)
+    ref = O.solve_refined(f, g)
     for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE):
         plan.set_precision(prec, 2)
         for rep in range(2):                 # first solve fills the pivot cache, second reads it

@@ -198,6 +198,24 @@ def test_residual_machine_precision_stretched_duct(alpha):
     assert O.rel_l2(O.apply_M(p, g, alpha), rhs) < 1e-13
 
 
+@pytest.mark.parametrize("alpha", [None, 1e-4])
+def test_refined_solve_reaches_the_exact_discrete_solution(alpha):
+    """Deep stretched z (the benchmark's 512 cells, tanh 1.5): a smooth p*
+    (the solution of a Gaussian right-hand side) and f = M p* by the stencil;
+    the refined solve returns p* at the stencil's rounding floor, where the
+    plain expansion is off by cond * eps (about 1e-12).  On a grid small
+    enough for dense LU the two agree with LAPACK."""
+    g = make_grid(64, 32, 512, (O.BC_P, O.BC_P, O.BC_N, O.BC_N, O.BC_N, O.BC_N), beta=1.5, lx=6.0, ly=2.0)
+    p_star = O.solve(S.gaussian(3001, (512, 32, 64)), g, alpha)
+    f = O.apply_M(p_star, g, alpha)
+    plain, refined = O.solve(f, g, alpha), O.solve_refined(f, g, alpha)
+    assert O.rel_l2(refined, p_star) < 1e-14, O.rel_l2(refined, p_star)
+    assert O.rel_l2(refined, p_star) < O.rel_l2(plain, p_star)
+    gs = make_grid(6, 4, 8, (O.BC_P, O.BC_P, O.BC_N, O.BC_N, O.BC_N, O.BC_D), beta=1.5)
+    fs = S.gaussian(3002, (8, 4, 6))
+    assert O.rel_l2(O.solve_refined(fs, gs, alpha), O.dense_solve(fs, gs, alpha)) < 1e-13
+
+
 def test_weighted_symmetry():
     g = make_grid(6, 5, 7, (O.BC_N, O.BC_N, O.BC_D, O.BC_D, O.BC_D, O.BC_N), beta=1.7)
     p, q = RNG.standard_normal((2, 7, 5, 6))

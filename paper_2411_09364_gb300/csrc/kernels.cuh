@@ -66,6 +66,8 @@ template <typename T> struct ZArgs {
     T* ecache;
     int ecache_mode;
     long ecache_stride;  // nmodes; 0 when every line has the same pivots (line solves)
+    int persist;         // warp-per-segment kernel: 0 = one tile per CTA; else the persistent
+                         // double-buffered variant where it applies
 };
 
 // FP64 residual r = f - (c0 u + c1 L u) of the 7-point staggered Laplacian.
@@ -98,6 +100,7 @@ struct ResidFFArgs {
     const double* cshift;
     double* gacc;
     const double* dzf;
+    int lo_zero;         // every lo part of u is zero (first sweep after an FP32 solve)
     int rows_per_cta;    // set by the launcher
 };
 

@@ -177,22 +177,39 @@ __device__ __forceinline__ ff split_double_fast(double d) {
     return ff{hi, lo};
 }
 
-// One point of the double-float residual (the arithmetic of k_residual_ff)
-// with its x differences given: de = e - c and dw = w - c of the hi parts as
-// exact pairs, lxe / lxw the differences of the lo parts; c the point,
-// s n d up its y and z neighbours, fv = f.  SING: singular Poisson
-// (consistency shift subtracted); GAUGE: the gauge sum of u is kept as an
-// unnormalised (hi, lo) pair; HELM: the c0 u term of Eq. 18.
-template <bool SING, bool HELM, bool GAUGE>
-__device__ __forceinline__ float resid_point(float2 c, ff de, ff dw, float lxe, float lxw, float2 s, float2 n,
-                                             float2 d, float2 up, double fv, ff cx, ff cy, ff zc, ff za, ff csh,
-                                             float& ghi, float& glo) {
-    const ff dn = two_sum(n.x, -c.x), ds = two_sum(s.x, -c.x);
+// Second difference a + b - 2c of three hi parts as an exact pair: TwoSum of
+// the neighbours, then TwoSum with -2c (exact scaling); the two rounding
+// errors are gathered in one float.  About half the operations of two
+// one-sided differences and their TwoSum.
+__device__ __forceinline__ ff second_diff(float a, float b, float c) {
+    const ff t = two_sum(a, b);
+    const ff v = two_sum(t.hi, -2.f * c);
+    return ff{v.hi, t.lo + v.lo};
+}
+
+// One point of the double-float residual
+//   r = (f - cshift) - (c0 u + cx Sx + cy Sy + zc (u_up - u) + za (u_dn - u)),
+// Sx = u_e + u_w - 2u, Sy = u_n + u_s - 2u, with u = (hi, lo) pairs: second
+// differences and one-sided z differences of the hi parts exact (TwoSum),
+// leading products exact (TwoProd by FMA), every rounding error and the
+// first-order terms of the lo parts and of the coefficients' low halves
+// gathered in one FP32 compensation, the accumulation a TwoSum chain.  LO =
+// false: every lo part is zero (the first sweep after an FP32 solve).
+// SING: singular Poisson (consistency shift subtracted); HELM: the c0 u term
+// of Eq. 18; GAUGE: the gauge sum of u as an unnormalised (hi, lo) pair.
+template <bool SING, bool HELM, bool GAUGE, bool LO>
+__device__ __forceinline__ float resid_point(float2 c, float2 w, float2 e, float2 s, float2 n, float2 d, float2 up,
+                                             double fv, ff cx, ff cy, ff zc, ff za, ff csh, float& ghi,
+                                             float& glo) {
+    const ff sx = second_diff(e.x, w.x, c.x), sy = second_diff(n.x, s.x, c.x);
     const ff du = two_sum(up.x, -c.x), dd = two_sum(d.x, -c.x);
-    const ff sx = two_sum(de.hi, dw.hi), sy = two_sum(dn.hi, ds.hi);
-    const float sxl = sx.lo + de.lo + dw.lo + (lxe + lxw);
-    const float syl = sy.lo + dn.lo + ds.lo + __fmaf_rn(-2.f, c.y, n.y + s.y);
-    const float dul = du.lo + (up.y - c.y), ddl = dd.lo + (d.y - c.y);
+    float sxl = sx.lo, syl = sy.lo, dul = du.lo, ddl = dd.lo;
+    if (LO) {
+        sxl += __fmaf_rn(-2.f, c.y, e.y + w.y);
+        syl += __fmaf_rn(-2.f, c.y, n.y + s.y);
+        dul += up.y - c.y;
+        ddl += d.y - c.y;
+    }
     const ff px = two_prod(cx.hi, sx.hi);
     float comp = __fmaf_rn(cx.hi, sxl, __fmaf_rn(cx.lo, sx.hi, px.lo));
     const ff py = two_prod(cy.hi, sy.hi);
@@ -213,7 +230,8 @@ __device__ __forceinline__ float resid_point(float2 c, ff de, ff dw, float lxe, 
     }
     if (HELM) {
         acc = two_sum(acc.hi, -c.x);
-        err += acc.lo - c.y;
+        err += acc.lo;
+        if (LO) err -= c.y;
     }
     acc = two_sum(acc.hi, -px.hi); err += acc.lo;
     acc = two_sum(acc.hi, -py.hi); err += acc.lo;
@@ -222,7 +240,7 @@ __device__ __forceinline__ float resid_point(float2 c, ff de, ff dw, float lxe, 
     if (GAUGE) {
         const ff g = two_sum(ghi, c.x);
         ghi = g.hi;
-        glo += g.lo + c.y;
+        glo += LO ? g.lo + c.y : g.lo;
     }
     return __fadd_rn(acc.hi, err);
 }
@@ -236,8 +254,8 @@ __device__ __forceinline__ float4 sc4(float g, float4 v) { return make_float4(g 
 // aligned u and f): the centre pair, both y and both z neighbour pairs and
 // f come in one vector load each, the x neighbours of the pair in two 8-byte
 // loads.  A CTA covers whole rows of one z-plane.
-template <bool SING, bool HELM, bool GAUGE>
-__global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
+template <bool SING, bool HELM, bool GAUGE, bool LO>
+__global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
     const int nx = a.nx, ny = a.ny;
     const long plane = (long)nx * ny;
     const int k = blockIdx.y;
@@ -282,15 +300,10 @@ __global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
                 if (i == 0) w = make_float2(gx * w.x, gx * w.y);
                 if (i + 2 == nx) e = make_float2(gx * e.x, gx * e.y);
             }
-            // x differences of the pair: the centre-to-centre one serves both
-            // points (negated for the second: TwoSum is odd under negation)
-            const ff d01 = two_sum(c.z, -c.x);
-            const float l01 = c.w - c.y;
-            const ff dw0 = two_sum(w.x, -c.x), de1 = two_sum(e.x, -c.z);
-            const float r0 = resid_point<SING, HELM, GAUGE>(lo2(c), d01, dw0, l01, w.y - c.y, lo2(s), lo2(n), lo2(d),
-                                                            lo2(up), fv.x, cx, cy, zc, za, csh, ghi, glo);
-            const float r1 = resid_point<SING, HELM, GAUGE>(hi2(c), de1, ff_neg(d01), e.y - c.w, -l01, hi2(s), hi2(n),
-                                                            hi2(d), hi2(up), fv.y, cx, cy, zc, za, csh, ghi, glo);
+            const float r0 = resid_point<SING, HELM, GAUGE, LO>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up),
+                                                                fv.x, cx, cy, zc, za, csh, ghi, glo);
+            const float r1 = resid_point<SING, HELM, GAUGE, LO>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up),
+                                                                fv.y, cx, cy, zc, za, csh, ghi, glo);
             *reinterpret_cast<float2*>(a.r + rb + i) = make_float2(r0, r1);
         }
     }
@@ -310,6 +323,16 @@ __global__ void __launch_bounds__(256) k_residual_ff2(ResidFFArgs a) {
     }
 }
 
+template <bool LO>
+static void launch_df(const ResidFFArgs& a, dim3 grid, bool sing, bool helm, cudaStream_t st) {
+    if (a.gacc && !helm) k_residual_df<true, false, true, LO><<<grid, 256, 0, st>>>(a);
+    else if (a.gacc) k_residual_df<true, true, true, LO><<<grid, 256, 0, st>>>(a);
+    else if (sing && !helm) k_residual_df<true, false, false, LO><<<grid, 256, 0, st>>>(a);
+    else if (sing) k_residual_df<true, true, false, LO><<<grid, 256, 0, st>>>(a);
+    else if (helm) k_residual_df<false, true, false, LO><<<grid, 256, 0, st>>>(a);
+    else k_residual_df<false, false, false, LO><<<grid, 256, 0, st>>>(a);
+}
+
 cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     ResidFFArgs a = a0;
     // about 4096 points per CTA, whole rows
@@ -323,12 +346,8 @@ cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     const bool sing = a.gacc != nullptr || a.cshift != nullptr;
     const bool helm = a.c0h != 0.f;
     if (!vec) k_residual_ff<<<grid, 256, 0, st>>>(a);
-    else if (a.gacc && !helm) k_residual_ff2<true, false, true><<<grid, 256, 0, st>>>(a);
-    else if (a.gacc) k_residual_ff2<true, true, true><<<grid, 256, 0, st>>>(a);
-    else if (sing && !helm) k_residual_ff2<true, false, false><<<grid, 256, 0, st>>>(a);
-    else if (sing) k_residual_ff2<true, true, false><<<grid, 256, 0, st>>>(a);
-    else if (helm) k_residual_ff2<false, true, false><<<grid, 256, 0, st>>>(a);
-    else k_residual_ff2<false, false, false><<<grid, 256, 0, st>>>(a);
+    else if (a.lo_zero) launch_df<false>(a, grid, sing, helm, st);
+    else launch_df<true>(a, grid, sing, helm, st);
     return cudaGetLastError();
 }
 

@@ -268,6 +268,16 @@ template <typename T> int choose_tx(int ny, int forced = 0) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// The persistent double-buffered z kernel is used where it applies unless
+// CALES_ZPERSIST=0 (one tile per CTA; for comparisons).
+static bool zpersist_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("CALES_ZPERSIST");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 // Per-solve options of one pass of the solver.
 struct PassOpt {
     double sigma, alpha, scale;
@@ -339,6 +349,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
                           zk.alpha == o.alpha) ? 2 : 1;
     }
     za.ecache_stride = (long)P->nx * P->ny;
+    za.persist = zpersist_enabled() ? 1 : 0;
     P->prof_begin(st, "z_solve");
     if (P->bc[4] == CALES_BC_P) {
         if (o.adjoint || o.cacc) return CALES_EUNSUPPORTED;
@@ -429,6 +440,7 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
         // annihilates constants, so earlier iterates may carry any mean
         ra.gacc = (sing && s == ns - 1) ? acc + 1 : nullptr;
         ra.dzf = P->dzf_d;
+        ra.lo_zero = s == 0 ? 1 : 0;       // the FP32 solve wrote (v, 0) pairs
         P->prof_begin(st, "residual");
         if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
         P->prof_end(st);
@@ -520,6 +532,7 @@ static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t 
     za.ecache = nullptr;
     za.ecache_mode = 0;
     za.ecache_stride = 0;
+    za.persist = zpersist_enabled() ? 1 : 0;
     const int zi = sizeof(T) == 8 ? 1 : 0;
     cales_plan_s::ZCacheKey& lk = P->lkey[zi];
     if (za.warp_mode && za.P <= 16 && P->lcache[zi]) {

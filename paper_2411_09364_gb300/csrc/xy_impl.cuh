@@ -161,6 +161,16 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     }
 }
 
+// pair + (v - shift) as a normalised pair; without a shift (every sweep but
+// the last of a singular problem) the single float v joins by one TwoSum.
+__device__ __forceinline__ ff pair_update(float2 pr, float v, ff shift, bool has_shift) {
+    if (!has_shift) {
+        const ff sm = two_sum(pr.x, v);
+        return fast_two_sum(sm.hi, sm.lo + pr.y);
+    }
+    return ff_add(ff{pr.x, pr.y}, ff_sub(ff{v, 0.f}, shift));
+}
+
 // One inverse-x result into an 8-byte slot according to the output mode.
 template <typename T, int MODE>
 __device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
@@ -170,7 +180,7 @@ __device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
         *reinterpret_cast<float2*>(slot) = make_float2(float(v), 0.f);
     } else {
         const float2 pr = *reinterpret_cast<const float2*>(slot);
-        const ff x = ff_add(ff{pr.x, pr.y}, ff_sub(ff{float(v), 0.f}, shift));
+        const ff x = pair_update(pr, float(v), shift, shift.hi != 0.f || shift.lo != 0.f);
         if (MODE == OUT_FF_ACC) *reinterpret_cast<float2*>(slot) = make_float2(x.hi, x.lo);
         else *reinterpret_cast<double*>(slot) = ff_to_double_bits(x);
     }
@@ -183,6 +193,7 @@ __device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, 
     if (MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL) {
         constexpr int U = 4;
         const int bd = blockDim.x;
+        const bool has_shift = shift.hi != 0.f || shift.lo != 0.f;     // uniform per CTA
         float2* po = reinterpret_cast<float2*>(outp);
         for (int e0 = threadIdx.x; e0 < tot; e0 += U * bd) {
             float2 pr[U];
@@ -195,7 +206,7 @@ __device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, 
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * bd;
                 if (e < tot) {
-                    const ff x = ff_add(ff{pr[u].x, pr[u].y}, ff_sub(ff{float(vals[e]), 0.f}, shift));
+                    const ff x = pair_update(pr[u], float(vals[e]), shift, has_shift);
                     if (MODE == OUT_FF_ACC) po[e] = make_float2(x.hi, x.lo);
                     else reinterpret_cast<double*>(outp)[e] = ff_to_double_bits(x);
                 }

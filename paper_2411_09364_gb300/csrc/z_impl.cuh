@@ -609,65 +609,79 @@ static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <typename T> struct alignas(2 * sizeof(T)) ZPair { T a, c; };
 
+// Coefficient tables of the warp-per-segment kernels in shared memory:
+// sA, sC (alpha-scaled couplings), sG, sO (adjoint weights), the (A_k, C_k)
+// pairs sAC with A_0 = 0 and C_{nz-1} = 0 (one 8-byte (FP32) or 16-byte
+// (FP64) load per row and no first/last-row tests), and two nz-long scratch
+// lines of the singular mode (save0, r0).
+template <typename T> struct ZwTables {
+    T *sA, *sC, *sG, *sO, *save0, *r0;
+    ZPair<T>* sAC;
+    __device__ ZwTables(T* base, int nz) {
+        sA = base; sC = sA + nz; sG = sC + nz; sO = sG + nz; save0 = sO + nz; r0 = save0 + nz;
+        sAC = reinterpret_cast<ZPair<T>*>(r0 + nz);
+    }
+    __device__ void fill(const ZArgs<T>& a) {
+        const int nz = a.nz;
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            sA[k] = a.alpha * a.za[k];
+            sC[k] = a.alpha * a.zc[k];
+            ZPair<T> pr;
+            pr.a = k > 0 ? sA[k] : T(0);
+            pr.c = k < nz - 1 ? sC[k] : T(0);
+            sAC[k] = pr;
+            double gs = double(a.scale), os = 1.0;
+            if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
+            sG[k] = T(gs);
+            sO[k] = T(os);
+        }
+    }
+};
+
+// Rows [0, nz) of the 32 modes q0 .. q0+31 of `in` into the tile [nz][32] with
+// 16-byte cp.async copies (zero-filled past the w live modes); completion by
+// the caller's commit / wait.
+template <typename T>
+__device__ __forceinline__ void zw_load_async(T* tile, const T* __restrict__ in, long nmodes, long q0, int w, int nz) {
+    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+        cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, long nmodes, long q0, int w, int nz) {
+    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+        if (c0 < w)
+            *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) = *reinterpret_cast<const float4*>(tile + k * TM + c0);
+    }
+}
+
+// The solve of one tile of 32 modes (q0 .. q0 + w - 1) already in shared
+// memory, in place; every thread of the CTA takes part (P warps, warp s owns
+// rows [s m, s m + m)).  Phases as in the header of this file; the segment
+// states are chained by warp 0 through `ch` (6 x [P][32]).
 // FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
 // predicates and the first/last-row conditions reduce to compile-time tests
 // on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
 // transposed) instead of the uniform forward scale.
 template <typename T, int MAXM, bool FULL, bool ADJ>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch, const ZwTables<T>& tb, long q0,
+                                              int w) {
     constexpr int TM = 32;
-    constexpr int EPC = 16 / (int)sizeof(T);          // elements per 16-byte chunk
-    constexpr int CPR = TM / EPC;                      // chunks per row
     const int nz = a.nz;
     const int P = blockDim.x / 32;
     const int m = (nz + P - 1) / P;
-    const long nmodes = (long)a.nx * a.ny;
-    const int nthr = blockDim.x;
-    T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
-    T* ch = tile + (long)P * m * TM;                   // 6 x [P][32] chain states
-    T* sA = ch + 6 * P * TM;
-    T* sC = sA + nz;
-    T* sG = sC + nz;
-    T* sO = sG + nz;
-    T* save0 = sO + nz;
-    T* r0 = save0 + nz;
-    // (A_k, C_k) pairs with A_0 = 0 and C_{nz-1} = 0: one 8-byte (FP32) or
-    // 16-byte (FP64) load per row and no first/last-row tests
-    ZPair<T>* sAC = reinterpret_cast<ZPair<T>*>(r0 + nz);
-    const long q0 = (long)blockIdx.x * TM;
-    const int w = (int)min((long)TM, nmodes - q0);
-    const T* __restrict__ in = a.src ? a.src : a.data;
     const int tid = threadIdx.x;
-
-    for (int k = tid; k < nz; k += nthr) {
-        sA[k] = a.alpha * a.za[k];
-        sC[k] = a.alpha * a.zc[k];
-        ZPair<T> pr;
-        pr.a = k > 0 ? sA[k] : T(0);
-        pr.c = k < nz - 1 ? sC[k] : T(0);
-        sAC[k] = pr;
-        double gs = double(a.scale), os = 1.0;
-        if (a.adjoint) { gs /= a.dzf[k]; os = a.dzf[k]; }
-        sG[k] = T(gs);
-        sO[k] = T(os);
-    }
-    if (a.bulk) {
-        for (int e = tid; e < nz * CPR; e += nthr) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
-        }
-        cp_async_wait_all();
-    } else {
-        for (int e = tid; e < nz * TM; e += nthr) {
-            const int k = e / TM, c = e - k * TM;
-            tile[e] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
-        }
-    }
-    __syncthreads();
+    const T* sA = tb.sA;
+    const T* sC = tb.sC;
+    const ZPair<T>* sAC = tb.sAC;
     const bool sing_tile = a.singular && q0 == 0;
     if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) save0[k] = tile[k * TM];
+        for (int k = 0; k < nz; ++k) tb.save0[k] = tile[k * TM];
 
     const int s = tid >> 5, c = tid & 31;
     const long q = q0 + (c < w ? c : 0);
@@ -679,8 +693,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
     const int k0 = s * m;
     const int mseg = max(0, min(m, nz - k0));
     const ZPair<T>* AC = sAC + k0;
-    const T* G = sG + k0;
-    const T* O = sO + k0;
+    const T* G = tb.sG + k0;
+    const T* O = tb.sO + k0;
     const T gsc = T(a.scale);
     const bool lastseg = s == P - 1, firstseg = s == 0;
     (void)lastseg; (void)firstseg;
@@ -821,7 +835,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
     __syncthreads();
     if (sing_tile && tid == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, nz, 0, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0);
+        serial_line<T>(tile, TM, nz, 0, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf, nz, base0, true, a.cacc,
+                       a.cacc_scale, 0);
         for (int k = 0; k < nz; ++k)
             if (!isfinite(tile[k * TM])) {
                 if (a.status) atomicOr(a.status, ST_NONFINITE);
@@ -829,19 +844,83 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
             }
     }
     __syncthreads();
+}
+
+// One tile of 32 consecutive modes per CTA: load (16-byte cp.async, all in
+// flight), solve, store.
+template <typename T, int MAXM, bool FULL, bool ADJ>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TM = 32;
+    const int nz = a.nz;
+    const int P = blockDim.x / 32;
+    const int m = (nz + P - 1) / P;
+    const long nmodes = (long)a.nx * a.ny;
+    T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
+    T* ch = tile + (long)P * m * TM;                   // 6 x [P][32] chain states
+    ZwTables<T> tb(ch + 6 * P * TM, nz);
+    const long q0 = (long)blockIdx.x * TM;
+    const int w = (int)min((long)TM, nmodes - q0);
+    const T* __restrict__ in = a.src ? a.src : a.data;
+    tb.fill(a);
     if (a.bulk) {
-        for (int e = tid; e < nz * CPR; e += nthr) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            if (c0 < w)
-                *reinterpret_cast<float4*>(a.data + (long)k * nmodes + q0 + c0) =
-                    *reinterpret_cast<const float4*>(tile + k * TM + c0);
-        }
+        zw_load_async<T>(tile, in, nmodes, q0, w, nz);
+        cp_async_wait_all();
     } else {
-        for (int e = tid; e < nz * TM; e += nthr) {
+        for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
+            const int k = e / TM, c = e - k * TM;
+            tile[e] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
+        }
+    }
+    __syncthreads();
+    zw_solve_tile<T, MAXM, FULL, ADJ>(a, tile, ch, tb, q0, w);
+    if (a.bulk) {
+        zw_store<T>(a.data, tile, nmodes, q0, w, nz);
+    } else {
+        for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
             const int k = e / TM, cc = e - k * TM;
             if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[e];
         }
     }
+}
+
+// Persistent variant (16-byte aligned rows only): each CTA walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... with two tile buffers, so the
+// cp.async load of the next tile is in flight while the current one is
+// solved and stored.  One CTA per SM.
+template <typename T, int MAXM, bool FULL, bool ADJ>
+__global__ void __launch_bounds__(512, 1) k_zsolve_wp(ZArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TM = 32;
+    const int nz = a.nz;
+    const int P = blockDim.x / 32;
+    const int m = (nz + P - 1) / P;
+    const long nmodes = (long)a.nx * a.ny;
+    const long tsz = (long)P * m * TM;                 // elements of one tile buffer
+    T* tiles = reinterpret_cast<T*>(smem_raw);         // 2 x [P*m][32]
+    T* ch = tiles + 2 * tsz;
+    ZwTables<T> tb(ch + 6 * P * TM, nz);
+    const T* __restrict__ in = a.src ? a.src : a.data;
+    const long ntiles = (nmodes + TM - 1) / TM;
+    tb.fill(a);
+    long t = blockIdx.x;
+    if (t < ntiles) zw_load_async<T>(tiles, in, nmodes, t * TM, (int)min((long)TM, nmodes - t * TM), nz);
+    cp_async_commit();
+    for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+        T* cur = tiles + (it & 1) * tsz;
+        const long tn = t + gridDim.x;
+        if (tn < ntiles)
+            zw_load_async<T>(tiles + ((it + 1) & 1) * tsz, in, nmodes, tn * TM, (int)min((long)TM, nmodes - tn * TM), nz);
+        cp_async_commit();
+        cp_async_wait_prev();                          // the current tile's group has landed
+        __syncthreads();
+        const long q0 = t * TM;
+        const int w = (int)min((long)TM, nmodes - q0);
+        zw_solve_tile<T, MAXM, FULL, ADJ>(a, cur, ch, tb, q0, w);
+        zw_store<T>(a.data, cur, nmodes, q0, w, nz);
+        __syncthreads();                               // the buffer is free for the load after next
+    }
+    cp_async_wait_none();
 }
 
 template <typename T>
@@ -850,16 +929,51 @@ size_t zsolve_w_smem(int nz, int P) {
     return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 8 * (size_t)nz) * sizeof(T);
 }
 
+// Shared memory of the persistent variant: two tile buffers.
+template <typename T>
+size_t zsolve_wp_smem(int nz, int P) {
+    const int m = (nz + P - 1) / P;
+    return zsolve_w_smem<T>(nz, P) + (size_t)P * m * 32 * sizeof(T);
+}
+
+// Streaming-multiprocessor count of the current device (cached).
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+        if (n <= 0) { cudaGetLastError(); return 1; }
+    }
+    return n;
+}
+
 template <typename T, int MAXM>
 static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
-    const size_t sm = zsolve_w_smem<T>(a.nz, a.P);
     const bool full = a.nz == a.P * MAXM;
+    const long nmodes = (long)a.nx * a.ny;
+    const long ntiles = (nmodes + 31) / 32;
+    const int nsm = sm_count();
+    // persistent double-buffered kernel when every SM gets several tiles and
+    // two tile buffers fit
+    const size_t smp = zsolve_wp_smem<T>(a.nz, a.P);
+    if (a.bulk && a.persist != 0 && ntiles >= 8L * nsm && smp <= 227 * 1024) {
+        auto kern = full ? (a.adjoint ? k_zsolve_wp<T, MAXM, true, true> : k_zsolve_wp<T, MAXM, true, false>)
+                         : (a.adjoint ? k_zsolve_wp<T, MAXM, false, true> : k_zsolve_wp<T, MAXM, false, false>);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * a.P, smp) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const long slots = (long)nsm * per_sm;
+        const unsigned grid = (unsigned)(ntiles < slots ? ntiles : slots);
+        kern<<<grid, 32 * a.P, smp, st>>>(a);
+        return cudaGetLastError();
+    }
+    const size_t sm = zsolve_w_smem<T>(a.nz, a.P);
     auto kern = full ? (a.adjoint ? k_zsolve_w<T, MAXM, true, true> : k_zsolve_w<T, MAXM, true, false>)
                      : (a.adjoint ? k_zsolve_w<T, MAXM, false, true> : k_zsolve_w<T, MAXM, false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const long nmodes = (long)a.nx * a.ny;
-    const unsigned grid = (unsigned)((nmodes + 31) / 32);
-    kern<<<grid, 32 * a.P, sm, st>>>(a);
+    kern<<<(unsigned)ntiles, 32 * a.P, sm, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -42,8 +42,9 @@ enum cales_bc {
     CALES_BC_N = 1,  /* homogeneous Neumann at the boundary face, cell-centred unknown */
     CALES_BC_D = 2,  /* homogeneous Dirichlet at the boundary face, cell-centred
                         unknown: ghost = -interior at the mirror distance            */
-    CALES_BC_DF = 3  /* homogeneous Dirichlet at a boundary node, node-centred unknown
-                        (z only): the boundary value is exactly zero               */
+    CALES_BC_DF = 3  /* homogeneous Dirichlet at a boundary node, node-centred unknown:
+                        the boundary value is exactly zero (in x or y on both
+                        sides of the direction, DST-I)                           */
 };
 
 enum cales_precision {
@@ -55,10 +56,11 @@ enum cales_precision {
 enum cales_status {
     CALES_OK = 0,
     CALES_EINVAL = -1,       /* bad size, spacing, boundary pairing or argument  */
-    CALES_EUNSUPPORTED = -2, /* odd length > 1 or a radix outside {2,3,5} in x/y,
-                                DF in x/y, periodic z with nz < 3 or on a path
-                                that needs z walls (refinement, adjoint, line
-                                solves, residual, allocation-free solve)        */
+    CALES_EUNSUPPORTED = -2, /* x/y: a length the transforms do not take (see
+                                cales_plan) or a side pairing other than P-P,
+                                N-N, D-D, DF-DF, N-D, D-N; periodic z with
+                                nz < 3 or on a path that needs z walls
+                                (adjoint, line solves, allocation-free solve) */
     CALES_ENOMEM = -3,       /* device allocation failed                        */
     CALES_ECUDA = -4,        /* a CUDA runtime call failed                      */
     CALES_ETOOBIG = -5       /* grid larger than the static scratch of
@@ -74,10 +76,14 @@ enum cales_device_status_bits {
 
 /*
  * Create a plan for an nx x ny x nz grid (paper Sec. 2.2: uniform x, y;
- * stretched z).  bc[6] = {xlo, xhi, ylo, yhi, zlo, zhi}; x and y take P, N or
- * D with the same kind on both sides and an even length (or 1) whose half
- * factors into 2, 3 and 5; z takes N, D or DF independently per side, or P
- * on both sides (nz >= 3; periodic on one side only is CALES_EINVAL).
+ * stretched z).  bc[6] = {xlo, xhi, ylo, yhi, zlo, zhi}.  Each of x and y
+ * takes, with its transform: P on both sides (real DFT), N-N (DCT-II), D-D
+ * (DST-II), N-D (DCT-IV), D-N (DST-IV) for cell-centred unknowns, with an
+ * even length (or 1) whose half factors into 2, 3 and 5; or DF-DF (DST-I)
+ * for node-centred unknowns between two wall nodes (n = interior nodes,
+ * spacing = node distance), with n + 1 factoring into 2, 3 and 5.  Periodic
+ * on one side only is CALES_EINVAL, other pairings CALES_EUNSUPPORTED.
+ * z takes N, D or DF independently per side, or P on both sides (nz >= 3).
  * Periodic z: each mode's z system is cyclic (row 0 couples to row nz-1
  * through dzc[0], row nz-1 to row 0 through dzc[nz]; both must hold the same
  * distance, the one between the last and the first cell centre through the
@@ -86,9 +92,9 @@ enum cales_device_status_bits {
  * sides (the data, and the couplings to u[0]), u = p + u[0] (1 - q), and
  * u[0] follows from row 0 through a denominator that is a sum of positive
  * terms.  One thread per mode, 16 bytes per grid point of plan-owned
- * scratch.  It serves the FP64 and FP32 Poisson and Helmholtz solves;
- * all-periodic/Neumann Poisson problems are made consistent, their zero
- * mode pinned and the result gauged as below.
+ * scratch.  It serves the Poisson and Helmholtz solves in every precision
+ * mode and the residual; all-periodic/Neumann Poisson problems are made
+ * consistent, their zero mode pinned and the result gauged as below.
  * dx, dy: uniform spacings.  dzc[0..nz]: distance between unknowns k-1 and k
  * (dzc[0], dzc[nz]: to the ghost/boundary node; mirror value dzf[0] resp.
  * dzf[nz-1] for cell-centred unknowns).  dzf[0..nz-1]: control-volume width

@@ -70,7 +70,7 @@ std::string device_name() {
 
 std::string tune_key(cales_plan_t P) {
     char buf[256];
-    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%d,%d,%d,%d,%s", P->nx, P->ny, P->nz, P->bc[0], P->bc[2], P->bc[4],
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%d,%d,%d,%d,%s", P->nx, P->ny, P->nz, P->X.kind, P->Y.kind, P->bc[4],
              P->bc[5], P->precision, device_name().c_str());
     return buf;
 }

@@ -15,7 +15,10 @@
 
 namespace cales {
 
-enum { KIND_P = 0, KIND_N = 1, KIND_D = 2 };
+// Transform kinds of a uniform direction: the kind of both sides (P, N, D;
+// DF = node-centred unknowns between two zero boundary nodes), or mixed cell
+// sides: ND = Neumann below, Dirichlet above; DN the reverse.
+enum { KIND_P = 0, KIND_N = 1, KIND_D = 2, KIND_DF = 3, KIND_ND = 4, KIND_DN = 5 };
 enum { ZBC_N = 1, ZBC_D = 2, ZBC_DF = 3 };
 constexpr int MAX_RADICES = 16;
 
@@ -181,6 +184,66 @@ template <typename T, bool INV> struct Bfly<T, 8, INV> {
         v[1] = b[0]; v[3] = b[1]; v[5] = b[2]; v[7] = b[3];
     }
 };
+
+// Ghost multipliers of the low and high side of a direction (R2): the value
+// beyond the boundary is mult * (the first / last unknown); periodic
+// directions wrap instead (not used).
+__host__ __device__ __forceinline__ float ghost_lo(int kind) {
+    return (kind == KIND_N || kind == KIND_ND) ? 1.f : (kind == KIND_DF ? 0.f : -1.f);
+}
+__host__ __device__ __forceinline__ float ghost_hi(int kind) {
+    return (kind == KIND_N || kind == KIND_DN) ? 1.f : (kind == KIND_DF ? 0.f : -1.f);
+}
+
+// ---------------------------------------------------------------------------
+// Transforms of the kinds DF, ND and DN (explicit packing and post-processing
+// around a forward complex FFT of length L; the same steps with a scale give
+// the inverse, since each of these transforms is its own inverse up to a
+// constant):
+//   ND (DCT-IV, n even, L = n/2):
+//     z_j = (x_{2j} + i x_{n-1-2j}) exp(-i pi (4j+1)/(4n)),  V = FFT_L(z),
+//     w_k = V_k exp(-i pi k/n),  X_{2k} = Re w_k,  X_{n-1-2k} = -Im w_k.
+//   DN (DST-IV): the same on the reversed input, output signs alternating:
+//     X_{2k} = Re w_k, X_{n-1-2k} = Im w_k.
+//   DF (DST-I, L = n+1): the real DFT of length 2(n+1) of the odd extension
+//     y = (0, x_0 .. x_{n-1}, 0, -x_{n-1} .. -x_0), Y_k = -2i X_{k-1},
+//     computed from the FFT of the pairs z_j = y_{2j} + i y_{2j+1}.
+// Tables: `mak` holds the ND/DN pre-twiddles exp(-i pi (4j+1)/(4n)), `post`
+// the post-twiddles exp(-i pi k/n) (ND/DN) or exp(-i pi k/(n+1)) (DF).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T df_ext(const T* x, int xes, int n, int t) {
+    if (t == 0 || t == n + 1) return T(0);
+    return t <= n ? x[(t - 1) * xes] : -x[(2 * n + 1 - t) * xes];
+}
+
+// Packed element j (of L) of one line x (element s at x[s * xes]), times sc.
+template <typename T>
+__device__ __forceinline__ cpx<T> pack_new(int kind, int n, const T* x, int xes, const cpx<T>* pre, int j, T sc) {
+    if (kind == KIND_DF) return mk(df_ext(x, xes, n, 2 * j) * sc, df_ext(x, xes, n, 2 * j + 1) * sc);
+    const T a = x[2 * j * xes], b = x[(n - 1 - 2 * j) * xes];
+    const cpx<T> z = kind == KIND_ND ? mk(a, b) : mk(b, a);
+    return scale(cmul(z, pre[j]), sc);
+}
+
+// Outputs of post-processing step k of one line: k in [0, L) for ND / DN
+// (two outputs), k in [1, n] for DF (one output X_{k-1}).
+template <typename T>
+__device__ __forceinline__ void post_new(int kind, int n, int L, const cpx<T>* Z, int zes, T* out, int oes,
+                                         const cpx<T>* pst, int k) {
+    if (kind == KIND_DF) {
+        const cpx<T> A = Z[k * zes], B = conj_(Z[(L - k) * zes]);
+        const cpx<T> d = A - B;
+        const cpx<T> W = pst[k];
+        // Im Y_k = Im E + Im(W O), E = (A + B)/2, O = (A - B)/(2i)
+        const T imy = T(0.5) * (A.y + B.y) + T(0.5) * (fma_(W.x, -d.x, mul_(W.y, d.y)));
+        out[(k - 1) * oes] = T(-0.5) * imy;
+        return;
+    }
+    const cpx<T> w = cmul(Z[k * zes], pst[k]);
+    out[2 * k * oes] = w.x;
+    out[(n - 1 - 2 * k) * oes] = kind == KIND_ND ? -w.y : w.y;
+}
 
 // Position of input sample s in the packed sequence v (Makhoul reordering for
 // N and D; identity for P) and its sign (-1)^s for D.

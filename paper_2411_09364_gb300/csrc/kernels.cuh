@@ -197,7 +197,7 @@ cudaError_t launch_gradient(const GridArgs<T>&, const T*, const T*, const T*, co
 template <typename T>
 cudaError_t launch_divergence_T(const GridArgs<T>&, const T*, const T*, const T*, const T*, T*, T*, T*, cudaStream_t);
 template <typename T> cudaError_t launch_gradient_T(const GridArgs<T>&, const T*, const T*, const T*, T*, cudaStream_t);
-// periodic z: cyclic tridiagonal per mode (Sherman-Morrison), two scratch fields [nz][nmodes]
+// periodic z: cyclic tridiagonal per mode (row 0 eliminated last), two scratch fields [nz][nmodes]
 template <typename T> cudaError_t launch_zsolve_cyclic(const ZArgs<T>&, T* ework, T* zwork, cudaStream_t);
 template <typename T> cudaError_t launch_mom_predict(const MomArgs<T>&, cudaStream_t);
 template <typename T> cudaError_t launch_pressure_update(T* p, const T* phi, T scale, long n, cudaStream_t);

@@ -15,7 +15,7 @@ static cudaError_t cols_l(const ColArgs<float>& a, bool inverse, cudaStream_t st
 }
 
 bool launch_cols_static(const ColArgs<float>& a, bool inverse, cudaStream_t st, cudaError_t* err) {
-    if (!static_fft_enabled() || !radices_match(a.t, a.t.L)) return false;
+    if (!static_fft_enabled() || a.t.kind > KIND_D || !radices_match(a.t, a.t.L)) return false;
     if (a.t.L == 64 && a.tx == 32) { *err = cols_l<64, 32>(a, inverse, st); return true; }
     if (a.t.L == 128 && a.tx == 32) { *err = cols_l<128, 32>(a, inverse, st); return true; }
     if (a.t.L == 256 && a.tx == 16) {

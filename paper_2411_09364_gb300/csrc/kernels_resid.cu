@@ -8,9 +8,6 @@
 
 namespace cales {
 
-__device__ __forceinline__ double ghost(int kind, double v0) {
-    return kind == KIND_N ? v0 : -v0;   // N mirror, D antisymmetric
-}
 
 __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
     const long nx = a.nx, ny = a.ny, nz = a.nz;
@@ -24,18 +21,21 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
         const double* __restrict__ u = a.u;
         const double uc = u[idx];
         double uw, ue, us, un, ud, uu;
+        // ghosts (R2): N mirror, D antisymmetric mirror, DF zero boundary node,
+        // per side for the mixed kinds
         if (i > 0) uw = u[idx - 1];
-        else uw = (a.bcx == KIND_P) ? u[idx + nx - 1] : ghost(a.bcx, uc);
+        else uw = (a.bcx == KIND_P) ? u[idx + nx - 1] : (double)ghost_lo(a.bcx) * uc;
         if (i < nx - 1) ue = u[idx + 1];
-        else ue = (a.bcx == KIND_P) ? u[idx - (nx - 1)] : ghost(a.bcx, uc);
+        else ue = (a.bcx == KIND_P) ? u[idx - (nx - 1)] : (double)ghost_hi(a.bcx) * uc;
         if (j > 0) us = u[idx - nx];
-        else us = (a.bcy == KIND_P) ? u[idx + (ny - 1) * nx] : ghost(a.bcy, uc);
+        else us = (a.bcy == KIND_P) ? u[idx + (ny - 1) * nx] : (double)ghost_lo(a.bcy) * uc;
         if (j < ny - 1) un = u[idx + nx];
-        else un = (a.bcy == KIND_P) ? u[idx - (ny - 1) * nx] : ghost(a.bcy, uc);
+        else un = (a.bcy == KIND_P) ? u[idx - (ny - 1) * nx] : (double)ghost_hi(a.bcy) * uc;
+        // z: periodic (kind 0) wraps through the period, else the R2 ghosts
         if (k > 0) ud = u[idx - plane];
-        else ud = a.zlo == ZBC_N ? uc : (a.zlo == ZBC_D ? -uc : 0.0);
+        else ud = a.zlo == 0 ? u[idx + (nz - 1) * plane] : (a.zlo == ZBC_N ? uc : (a.zlo == ZBC_D ? -uc : 0.0));
         if (k < nz - 1) uu = u[idx + plane];
-        else uu = a.zhi == ZBC_N ? uc : (a.zhi == ZBC_D ? -uc : 0.0);
+        else uu = a.zhi == 0 ? u[idx - (nz - 1) * plane] : (a.zhi == ZBC_N ? uc : (a.zhi == ZBC_D ? -uc : 0.0));
         const double lu = (ue + uw - 2.0 * uc) * a.idx2 + (un + us - 2.0 * uc) * a.idy2
                         + a.zc[k] * (uu - uc) - a.za[k] * (uc - ud);
         const double r = (a.f[idx] - a.fshift) - (a.c0 * uc + a.c1 * lu);
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
     const bool kd = k > 0, ku = k < a.nz - 1;
     const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
     const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
-    const float gx = a.bcx == KIND_N ? 1.f : -1.f, gy = a.bcy == KIND_N ? 1.f : -1.f;
+    const float gxl = ghost_lo(a.bcx), gxh = ghost_hi(a.bcx), gyl = ghost_lo(a.bcy), gyh = ghost_hi(a.bcy);
     ff gsum{0.f, 0.f};                       // gauge sum of u (double-float)
     const int rows = a.rows_per_cta;
     const int j0 = blockIdx.x * rows, j1 = min(j0 + rows, ny);
@@ -108,15 +108,17 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidFFArgs a) {
             const float2 c = u[idx];
             float2 w, e, s, n, d, up;
             if (i > 0) w = u[idx - 1];
-            else w = a.bcx == KIND_P ? u[idx + nx - 1] : make_float2(gx * c.x, gx * c.y);
+            else w = a.bcx == KIND_P ? u[idx + nx - 1] : make_float2(gxl * c.x, gxl * c.y);
             if (i < nx - 1) e = u[idx + 1];
-            else e = a.bcx == KIND_P ? u[idx - (nx - 1)] : make_float2(gx * c.x, gx * c.y);
+            else e = a.bcx == KIND_P ? u[idx - (nx - 1)] : make_float2(gxh * c.x, gxh * c.y);
             if (j > 0) s = u[idx - nx];
-            else s = a.bcy == KIND_P ? u[idx + (long)(ny - 1) * nx] : make_float2(gy * c.x, gy * c.y);
+            else s = a.bcy == KIND_P ? u[idx + (long)(ny - 1) * nx] : make_float2(gyl * c.x, gyl * c.y);
             if (j < ny - 1) n = u[idx + nx];
-            else n = a.bcy == KIND_P ? u[idx - (long)(ny - 1) * nx] : make_float2(gy * c.x, gy * c.y);
-            d = kd ? u[idx - plane] : make_float2(gd * c.x, gd * c.y);
-            up = ku ? u[idx + plane] : make_float2(gu * c.x, gu * c.y);
+            else n = a.bcy == KIND_P ? u[idx - (long)(ny - 1) * nx] : make_float2(gyh * c.x, gyh * c.y);
+            if (kd || a.zlo == 0) d = u[idx + (kd ? -plane : (long)(a.nz - 1) * plane)];
+            else d = make_float2(gd * c.x, gd * c.y);
+            if (ku || a.zhi == 0) up = u[idx + (ku ? plane : -(long)(a.nz - 1) * plane)];
+            else up = make_float2(gu * c.x, gu * c.y);
             // exact differences of the hi parts (TwoSum), lo parts in FP32:
             // errors scale with the small neighbour differences of a smooth u
             const ff de = two_sum(e.x, -c.x), dw = two_sum(w.x, -c.x);
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
     const bool kd = k > 0, ku = k < a.nz - 1;
     const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
     const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
-    const float gx = a.bcx == KIND_N ? 1.f : -1.f, gy = a.bcy == KIND_N ? 1.f : -1.f;
+    const float gxl = ghost_lo(a.bcx), gxh = ghost_hi(a.bcx), gyl = ghost_lo(a.bcy), gyh = ghost_hi(a.bcy);
     const bool px_ = a.bcx == KIND_P, py_ = a.bcy == KIND_P;
     float ghi = 0.f, glo = 0.f;
     const int npair = nx >> 1;
@@ -275,12 +277,15 @@ __global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
     // neighbour offsets and multipliers: a ghost reads the centre (offset 0)
     // and scales it (Neumann mirror 1, Dirichlet -1, node 0); the tests on
     // the multipliers are uniform per CTA (z) or per row (y)
-    const long offD = kd ? -plane : 0, offU = ku ? plane : 0;
-    const float mD = kd ? 1.f : gd, mU = ku ? 1.f : gu;
+    // periodic z (kind 0) wraps: plane nz-1 below plane 0, plane 0 above nz-1
+    const bool pz_ = a.zlo == 0;
+    const long offD = kd ? -plane : (pz_ ? (long)(a.nz - 1) * plane : 0);
+    const long offU = ku ? plane : (pz_ ? -(long)(a.nz - 1) * plane : 0);
+    const float mD = (kd || pz_) ? 1.f : gd, mU = (ku || pz_) ? 1.f : gu;
     for (int j = j0; j < j1; ++j) {
         const long offS = j > 0 ? -(long)nx : (py_ ? (long)(ny - 1) * nx : 0);
         const long offN = j < ny - 1 ? (long)nx : (py_ ? -(long)(ny - 1) * nx : 0);
-        const float mS = (j > 0 || py_) ? 1.f : gy, mN = (j < ny - 1 || py_) ? 1.f : gy;
+        const float mS = (j > 0 || py_) ? 1.f : gyl, mN = (j < ny - 1 || py_) ? 1.f : gyh;
         const long rb = kbase + (long)j * nx;
         const float2* __restrict__ ur = u + rb;
         for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
@@ -297,8 +302,8 @@ __global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
             if (mD != 1.f) d = sc4(mD, d);
             if (mU != 1.f) up = sc4(mU, up);
             if (!px_) {
-                if (i == 0) w = make_float2(gx * w.x, gx * w.y);
-                if (i + 2 == nx) e = make_float2(gx * e.x, gx * e.y);
+                if (i == 0) w = make_float2(gxl * w.x, gxl * w.y);
+                if (i + 2 == nx) e = make_float2(gxh * e.x, gxh * e.y);
             }
             const float r0 = resid_point<SING, HELM, GAUGE, LO>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up),
                                                                 fv.x, cx, cy, zc, za, csh, ghi, glo);

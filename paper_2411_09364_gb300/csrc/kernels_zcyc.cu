@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
             sw += a.dzf[k];
         }
         const T gmean = T(sum / sw);
+        if (a.cacc) a.cacc[0] += (sum / sw) * a.cacc_scale;    // consistency constant (refinement)
         // rows 0..nz-2 with u[nz-1] = 0
         T einv = T(0), d = T(0);
         for (int k = 0; k < nz - 1; ++k) {

@@ -69,11 +69,18 @@ template <typename T> T* dev_upload(const std::vector<T>& h, std::vector<void*>&
     return reinterpret_cast<T*>(p);
 }
 
+// Tables of one uniform direction of n unknowns, transform kind `kind`
+// (KIND_P .. KIND_DN) and spacing h.  FFT length L = n/2, or n + 1 for the
+// DST-I of node-centred unknowns (the real DFT of the odd extension).
 int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) {
     d.n = n;
     d.kind = kind;
-    if (n > 1 && (n % 2)) return CALES_EUNSUPPORTED;
-    d.L = n >= 2 ? n / 2 : 1;
+    if (kind == KIND_DF) {
+        d.L = n + 1;
+    } else {
+        if (n > 1 && (n % 2)) return CALES_EUNSUPPORTED;
+        d.L = n >= 2 ? n / 2 : 1;
+    }
     if (!factorize(d.L, d.radix, d.nrad)) return CALES_EUNSUPPORTED;
     const int L = d.L;
     // per-pass twiddles W_L^(r k tstep) at twoff[p] + (r - 1) Ns + k
@@ -99,10 +106,21 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
     }
     for (int m = 0; m <= L; ++m) {
         double c, s;
-        cis_frac(m, n >= 2 ? n : 1, c, s);
-        post[m] = make_double2(c, -s);
-        cis_frac(m, 4L * (n >= 1 ? n : 1), c, s);
-        mak[m] = make_double2(c, -s);
+        if (kind == KIND_ND || kind == KIND_DN) {
+            cis_frac(m, 2L * n, c, s);                 // exp(-i pi m / n)
+            post[m] = make_double2(c, -s);
+            cis_frac(4L * m + 1, 8L * n, c, s);        // exp(-i pi (4m + 1) / (4n))
+            mak[m] = make_double2(c, -s);
+        } else if (kind == KIND_DF) {
+            cis_frac(m, 2L * (n + 1), c, s);           // exp(-i pi m / (n + 1))
+            post[m] = make_double2(c, -s);
+            mak[m] = post[m];
+        } else {
+            cis_frac(m, n >= 2 ? n : 1, c, s);
+            post[m] = make_double2(c, -s);
+            cis_frac(m, 4L * (n >= 1 ? n : 1), c, s);
+            mak[m] = make_double2(c, -s);
+        }
     }
     std::vector<double> lam(n);
     std::vector<float> lamf(n);
@@ -114,8 +132,12 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
             sv = std::sin(pi * m / n);
         } else if (kind == KIND_N) {
             sv = std::sin(pi * q / (2.0 * n));
-        } else {
+        } else if (kind == KIND_D) {
             sv = std::sin(pi * (q + 1) / (2.0 * n));
+        } else if (kind == KIND_DF) {
+            sv = std::sin(pi * (q + 1) / (2.0 * (n + 1)));
+        } else {
+            sv = std::sin(pi * (2 * q + 1) / (4.0 * n));
         }
         lam[q] = -(4.0 / (h * h)) * sv * sv;
         lamf[q] = (float)lam[q];
@@ -268,12 +290,15 @@ template <typename T> int choose_tx(int ny, int forced = 0) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// The persistent double-buffered z kernel is used where it applies unless
-// CALES_ZPERSIST=0 (one tile per CTA; for comparisons).
+// The persistent double-buffered z kernel replaces the one-tile-per-CTA
+// kernel only with CALES_ZPERSIST=1: measured on GB300 at 1536 x 512 x 512
+// (FP32, 16 segments of 32 rows) it took 1.55 ms per launch against 0.87 ms,
+// since one resident CTA per SM leaves the serial segment chains and the
+// tile copies unhidden.
 static bool zpersist_enabled() {
     static const bool on = [] {
         const char* e = getenv("CALES_ZPERSIST");
-        return !(e && e[0] == '0');
+        return e && e[0] == '1';
     }();
     return on;
 }
@@ -296,7 +321,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ra.in = in;
     ra.out = work;
     ra.nrows = nrows;
-    ra.rpc = rows_per_cta<T>(P->nx, 0, P->sched[0]);
+    ra.rpc = rows_per_cta<T>(2 * P->X.L, 0, P->sched[0]);
     ra.in_scale = 1.0;
     ra.shift_acc = nullptr;
     ra.shift_scale = 0.0;
@@ -312,7 +337,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ca.data = work;
     ca.nx = P->nx;
     ca.nplanes = P->nz;
-    ca.tx = choose_tx<T>(P->ny, P->sched[1]);
+    ca.tx = choose_tx<T>(2 * P->Y.L, P->sched[1]);
     ca.bulk = (aligned16(work) && ((size_t)P->nx * sizeof(T)) % 16 == 0 && ca.tx * sizeof(T) >= 16) ? 1 : 0;
     ca.status = P->status;
     if (P->ny > 1) {
@@ -352,7 +377,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.persist = zpersist_enabled() ? 1 : 0;
     P->prof_begin(st, "z_solve");
     if (P->bc[4] == CALES_BC_P) {
-        if (o.adjoint || o.cacc) return CALES_EUNSUPPORTED;
+        if (o.adjoint) return CALES_EUNSUPPORTED;
         T* ework = reinterpret_cast<T*>(P->zcyc);
         if (launch_zsolve_cyclic<T>(za, ework, ework + (size_t)P->nx * P->ny * P->nz, st) != cudaSuccess)
             return CALES_ECUDA;
@@ -374,7 +399,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     RowArgs<T> ri = ra;
     ri.in = work;
     ri.out = out;
-    ri.rpc = rows_per_cta<T>(P->nx, 0, P->sched[0]);
+    ri.rpc = rows_per_cta<T>(2 * P->X.L, 0, P->sched[0]);
     ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
                ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
     ri.shift_acc = o.shift_acc;
@@ -428,7 +453,7 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
         ra.u = (const float2*)p;
         ra.r = work;
         ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
-        ra.bcx = P->bc[0]; ra.bcy = P->bc[2]; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
+        ra.bcx = P->X.kind; ra.bcy = P->Y.kind; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
         split_double(c1 / (P->dx * P->dx), ra.cxh, ra.cxl);
         split_double(c1 / (P->dy * P->dy), ra.cyh, ra.cyl);
         ra.c0h = helm ? 1.0f : 0.0f;
@@ -463,7 +488,7 @@ int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint,
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {
     if (!P || !f || !p) return CALES_EINVAL;
     if (helm && !(alpha > 0.0)) return CALES_EINVAL;
-    if (P->bc[4] == CALES_BC_P && (adjoint || P->precision == CALES_FP32_REFINE)) return CALES_EUNSUPPORTED;
+    if (P->bc[4] == CALES_BC_P && adjoint) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double nxy = (double)P->nx * (double)P->ny;
     PassOpt o;
@@ -496,7 +521,7 @@ void cales_plan_s::fill_resid(cales::ResidArgs& ra, const double* u, const doubl
     ra.r = r;
     ra.r_is_double = r_double ? 1 : 0;
     ra.nx = nx; ra.ny = ny; ra.nz = nz;
-    ra.bcx = bc[0]; ra.bcy = bc[2]; ra.zlo = bc[4]; ra.zhi = bc[5];
+    ra.bcx = X.kind; ra.bcy = Y.kind; ra.zlo = bc[4]; ra.zhi = bc[5];
     ra.idx2 = 1.0 / (dx * dx);
     ra.idy2 = 1.0 / (dy * dy);
     ra.za = za_d;
@@ -579,8 +604,18 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     if ((long)nx * ny * nz > (1L << 34)) return CALES_EINVAL;
     for (int i = 0; i < 6; ++i)
         if (bc[i] < 0 || bc[i] > 3) return CALES_EINVAL;
-    if (bc[0] != bc[1] || bc[2] != bc[3]) return (bc[0] == 0 || bc[1] == 0 || bc[2] == 0 || bc[3] == 0) ? CALES_EINVAL : CALES_EUNSUPPORTED;
-    if (bc[0] == CALES_BC_DF || bc[2] == CALES_BC_DF) return CALES_EUNSUPPORTED;
+    // transform kind of each uniform direction: both sides alike, or mixed
+    // Neumann / Dirichlet cell sides (DCT-IV / DST-IV); periodic pairs only
+    // with periodic
+    int dkind[2];
+    for (int d = 0; d < 2; ++d) {
+        const int lo = bc[2 * d], hi = bc[2 * d + 1];
+        if ((lo == CALES_BC_P) != (hi == CALES_BC_P)) return CALES_EINVAL;
+        if (lo == hi) dkind[d] = lo;
+        else if (lo == CALES_BC_N && hi == CALES_BC_D) dkind[d] = KIND_ND;
+        else if (lo == CALES_BC_D && hi == CALES_BC_N) dkind[d] = KIND_DN;
+        else return CALES_EUNSUPPORTED;
+    }
     if ((bc[4] == CALES_BC_P) != (bc[5] == CALES_BC_P)) return CALES_EINVAL;
     if (bc[4] == CALES_BC_P && nz < 3) return CALES_EUNSUPPORTED;
     for (int k = 0; k <= nz; ++k)
@@ -596,14 +631,17 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
     P->nx = nx; P->ny = ny; P->nz = nz;
     for (int i = 0; i < 6; ++i) P->bc[i] = bc[i];
     P->dx = dx; P->dy = dy;
-    P->singular_poisson = (bc[0] != CALES_BC_D && bc[2] != CALES_BC_D && (bc[4] == CALES_BC_N || bc[4] == CALES_BC_P) &&
-                           (bc[5] == CALES_BC_N || bc[5] == CALES_BC_P)) ? 1 : 0;
-    int rc = build_dir(P->X, nx, bc[0], dx, P->owned);
-    if (rc == CALES_OK) rc = build_dir(P->Y, ny, bc[2], dy, P->owned);
+    // singular: no Dirichlet condition anywhere (x, y sides periodic or Neumann)
+    P->singular_poisson = ((dkind[0] == KIND_P || dkind[0] == KIND_N) && (dkind[1] == KIND_P || dkind[1] == KIND_N) &&
+                           (bc[4] == CALES_BC_N || bc[4] == CALES_BC_P) && (bc[5] == CALES_BC_N || bc[5] == CALES_BC_P))
+                              ? 1 : 0;
+    int rc = build_dir(P->X, nx, dkind[0], dx, P->owned);
+    if (rc == CALES_OK) rc = build_dir(P->Y, ny, dkind[1], dy, P->owned);
     if (rc == CALES_OK) {
         int tm_, p_, mm_, wm_;
-        if (rows_per_cta<double>(nx, 0) < 1 || 2.0 * nx * sizeof(double) > 200.0 * 1024 || !choose_zt<double>(nz, tm_, p_, mm_, wm_) ||
-            choose_tx<double>(ny) == 0)
+        const int ex = 2 * P->X.L, ey = 2 * P->Y.L;       // real elements of one FFT buffer line
+        if (rows_per_cta<double>(ex, 0) < 1 || 2.0 * ex * sizeof(double) > 200.0 * 1024 ||
+            !choose_zt<double>(nz, tm_, p_, mm_, wm_) || choose_tx<double>(ey) == 0)
             rc = CALES_EUNSUPPORTED;
     }
     if (rc == CALES_OK) {
@@ -670,7 +708,6 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
 
 int cales_set_precision(cales_plan_t P, int mode, int sweeps) {
     if (!P || mode < 0 || mode > 2 || sweeps < 0 || sweeps > 8) return CALES_EINVAL;
-    if (mode == CALES_FP32_REFINE && P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     if (mode == CALES_FP32_REFINE && !P->work) {
         void* w = nullptr;
         const size_t bytes = (size_t)P->nx * P->ny * P->nz * sizeof(float);
@@ -709,7 +746,6 @@ int cales_helmholtz_solve_adjoint(cales_plan_t P, double alpha, const void* w, v
 
 int cales_residual(cales_plan_t P, double alpha, const double* u, const double* f, double* r, void* stream) {
     if (!P || !u || !f || !r) return CALES_EINVAL;
-    if (P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     ResidArgs ra;
     const bool helm = alpha >= 0.0;
     P->fill_resid(ra, u, f, r, true, helm ? 1.0 : 0.0, helm ? -alpha : 1.0);

@@ -119,6 +119,41 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
         __syncthreads();
     }
     NatIO<T> nat{reinterpret_cast<const T*>(b0), nullptr, n, 1, reinterpret_cast<const double*>(in)};
+    if (KS < 0 && kind >= KIND_DF) {
+        // DST-I / DCT-IV / DST-IV: explicit packing with the pre-twiddles,
+        // FFT, post-processing (natural-order input staged in b0)
+        T* xs = reinterpret_cast<T*>(b0);
+        if (IN64) {
+            for (int e = tid; e < tot; e += blockDim.x) xs[e] = T(trunc_double_int(double(in[e])));
+            __syncthreads();
+        }
+        for (int idx = tid; idx < nr * L; idx += blockDim.x) {
+            const int r = (int)fdivu((unsigned)idx, t.lmag), j = idx - r * L;
+            b1[r * L + j] = pack_new<T>(kind, n, xs + r * n, 1, mkt, j, sc);
+        }
+        __syncthreads();
+        cpx<T>* Zn = fft_lines<T, false, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
+        T* obn = reinterpret_cast<T*>(Zn == b0 ? b1 : b0);
+        const int kb = kind == KIND_DF ? 1 : 0, nk = kind == KIND_DF ? n : L;
+        const unsigned kmag = kind == KIND_DF ? t.nmag : t.lmag;
+        for (int idx = tid; idx < nr * nk; idx += blockDim.x) {
+            const int r = (int)fdivu((unsigned)idx, kmag), k = idx - r * nk + kb;
+            post_new<T>(kind, n, L, Zn + r * L, 1, obn + r * n, 1, pst, k);
+        }
+        if (a.bulk) {
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                bulk_s2g(out, obn, (uint32_t)(tot * sizeof(T)));
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+        } else {
+            __syncthreads();
+            for (int e = tid; e < tot; e += blockDim.x) out[e] = obn[e];
+        }
+        return;
+    }
     // (the fused FP64 read uses 16-byte loads: only with aligned rows)
     const bool fused = nrad > 0 && sc == T(1) && (!IN64 || a.bulk);
     if (!fused) {
@@ -275,6 +310,32 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     }
     const cpx<T>* pst = tw_s + t.twlen;
     const cpx<T>* mkt = tw_s + t.twlen + L + 1;
+    T* ob;
+    if (KS < 0 && kind >= KIND_DF) {
+        // DST-I / DCT-IV / DST-IV are their own inverses up to a constant:
+        // the forward steps, scaled so that inverse(forward(x)) = n x
+        const T isc = kind == KIND_DF ? T(2.0 * n / (n + 1)) : T(2);
+        for (int idx = tid; idx < nr * L; idx += blockDim.x) {
+            const int r = (int)fdivu((unsigned)idx, t.lmag), j = idx - r * L;
+            b1[r * L + j] = pack_new<T>(kind, n, x0 + r * n, 1, mkt, j, isc);
+        }
+        __syncthreads();
+        const NatIO<T> nat0{nullptr, nullptr, n, 1};
+        cpx<T>* Zn = fft_lines<T, false, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat0);
+        T* natout = reinterpret_cast<T*>(Zn == b0 ? b1 : b0);
+        const int kb = kind == KIND_DF ? 1 : 0, nk = kind == KIND_DF ? n : L;
+        const unsigned kmag = kind == KIND_DF ? t.nmag : t.lmag;
+        for (int idx = tid; idx < nr * nk; idx += blockDim.x) {
+            const int r = (int)fdivu((unsigned)idx, kmag), k = idx - r * nk + kb;
+            post_new<T>(kind, n, L, Zn + r * L, 1, natout + r * n, 1, pst, k);
+        }
+        __syncthreads();
+        if (MODE != OUT_T) {
+            store8_rows<T, MODE>(outp, natout, tot, shift);
+            return;
+        }
+        ob = natout;
+    } else {
     const int half = L / 2 + 1;
     const int npre = nr * half;
     for (int idx = tid; idx < npre; idx += blockDim.x) {
@@ -282,7 +343,6 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
         pre_inverse_pair<T, LS, KS>(x0 + r * n, 1, b1 + r * L, 1, t, pst, mkt, m);
     }
     __syncthreads();
-    T* ob;
     if (nrad > 0) {
         // the last pass unpacks straight into natural order (real rows); a
         // periodic row's packed pairs already are its natural order
@@ -305,6 +365,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
             else store8<T, MODE>(outp + (long)e * 8, v, shift);
         }
         if (MODE != OUT_T) return;
+    }
     }
     if (a.bulk) {
         fence_proxy_async();
@@ -369,7 +430,24 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     __syncthreads();
     T* ob;
     const int half = L / 2 + 1;
-    if (!INV) {
+    if (KS < 0 && kind >= KIND_DF) {
+        // DST-I / DCT-IV / DST-IV: explicit packing, forward FFT, post-processing;
+        // the inverse is the same transform scaled so that inverse(forward(x)) = n x
+        const T sc = INV ? (kind == KIND_DF ? T(2.0 * n / (n + 1)) : T(2)) : T(1);
+        for (int idx = tid; idx < TX * L; idx += blockDim.x) {
+            const int q = idx / TX, c = idx - q * TX;
+            b1[q * TX + c] = pack_new<T>(kind, n, nat + c, TX, mkt, q, sc);
+        }
+        __syncthreads();
+        const NatIO<T> nat0{nullptr, nullptr, 1, TX};
+        cpx<T>* Zn = fft_lines<T, false, TX, false, false, LS, KS>(b1, b0, t, TX, 1, TX, tw_s, nat0);
+        ob = reinterpret_cast<T*>(Zn == b0 ? b1 : b0);
+        const int kb = kind == KIND_DF ? 1 : 0, nk = kind == KIND_DF ? n : L;
+        for (int idx = tid; idx < nk * TX; idx += blockDim.x) {
+            const int k = idx / TX, c = idx - k * TX;
+            post_new<T>(kind, n, L, Zn + c, TX, ob + c, TX, pst, k + kb);
+        }
+    } else if (!INV) {
         cpx<T>* Z;
         if (nrad > 0) {
             const NatIO<T> natio{nat, nullptr, 1, TX};

@@ -47,7 +47,9 @@ def test_invalid_plans_are_rejected_on_host(lib):
     assert args(0, 4, 8) == -1                     # empty grid
     assert args(4, 4, 8, dx=-1.0) == -1            # bad spacing
     assert args(4, 4, 8, (C.c_int * 6)(0, 1, 0, 0, 1, 1)) == -1    # periodic paired with a wall
-    assert args(4, 4, 8, (C.c_int * 6)(3, 3, 0, 0, 1, 1)) == -2    # node unknowns in x
+    assert args(4, 4, 8, (C.c_int * 6)(1, 3, 0, 0, 1, 1)) == -2    # a wall node beside a Neumann face
+    assert args(6, 4, 8, (C.c_int * 6)(3, 3, 0, 0, 1, 1)) == -2    # node unknowns: n + 1 = 7 has no FFT here
+    assert args(5, 4, 8, (C.c_int * 6)(1, 2, 0, 0, 1, 1)) == -2    # mixed sides need an even n
     assert args(4, 4, 2, (C.c_int * 6)(0, 0, 0, 0, 0, 0)) == -2    # periodic z needs three cells
     assert args(4, 4, 8, (C.c_int * 6)(0, 0, 0, 0, 0, 1)) == -1    # periodic z on one side only
     wrap = np.ones(9)

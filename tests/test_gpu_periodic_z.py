@@ -65,11 +65,39 @@ def test_periodic_z_in_place_and_repeatable(cuda_device):
     assert O.rel_l2(y.cpu().numpy(), O.solve(f, g)) <= TOL[cs.FP64]
 
 
+@pytest.mark.parametrize("shape", [(48, 20, 33), (64, 32, 64)])
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_P, O.BC_P), (O.BC_P, O.BC_N), (O.BC_N, O.BC_D)])
+@pytest.mark.parametrize("alpha", [None, 2e-3])
+def test_periodic_z_refinement_against_oracle(cuda_device, shape, bcx, bcy, alpha):
+    """FP32 solves with double-float refinement over a periodic z: the
+    residual wraps through the period, the consistency constant of a
+    singular problem is accumulated by the cyclic solve."""
+    nx, ny, nz = shape
+    g, plan = pair(nx, ny, nz, bcx, bcy, precision=cs.FP32_REFINE)
+    f = S.gaussian(720 + nx + nz + bcx * 3 + bcy, (nz, ny, nx))
+    x = torch.from_numpy(f).cuda()
+    out = plan.poisson(x) if alpha is None else plan.helmholtz(alpha, x)
+    torch.cuda.synchronize()
+    ref = O.solve(f, g, alpha)
+    rel = O.rel_l2(out.cpu().numpy(), ref)
+    print(f"periodic z refine {shape} bc {bcx},{bcy} alpha {alpha}: rel {rel:.3e}")
+    assert rel <= 1e-10
+    assert plan.status() == 0
+
+
+def test_periodic_z_fp64_residual(cuda_device):
+    g, plan = pair(24, 10, 9, O.BC_P, O.BC_N)
+    u, f = S.gaussian(740, (9, 10, 24)), S.gaussian(741, (9, 10, 24))
+    for alpha in (None, 1e-3):
+        r = plan.residual(torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda(), alpha)
+        torch.cuda.synchronize()
+        ref = O.residual(u, f, g, alpha)
+        assert np.abs(r.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_periodic_z_refuses_wall_only_paths(cuda_device):
     g, plan = pair(16, 8, 8, O.BC_P, O.BC_P)
     f = torch.zeros((8, 8, 16), dtype=torch.float64, device="cuda")
-    with pytest.raises(Exception):
-        plan.set_precision(cs.FP32_REFINE)
     with pytest.raises(Exception):
         plan.helmholtz_z(1e-3, f)
     with pytest.raises(Exception):

@@ -1,8 +1,8 @@
 """The persistent double-buffered z kernel against the one-tile-per-CTA kernel.
 
 Both run the same per-tile arithmetic (the same device function), so their
-solves agree bit for bit.  The one-tile kernel runs in a child process started
-with CALES_ZPERSIST=0 (read once per process).  The grids have enough modes
+solves agree bit for bit.  The persistent kernel runs in a child process started
+with CALES_ZPERSIST=1 (read once per process).  The grids have enough modes
 (at least eight 32-mode tiles per SM) for the persistent kernel to be chosen:
 full and ragged z segments, FP32, FP64 and FP32 + refinement, Poisson,
 Helmholtz and the adjoint solve.
@@ -53,10 +53,10 @@ def _solve_all():
 
 def test_persistent_and_one_tile_z_kernels_agree_bitwise(cuda_device, tmp_path):
     mine = _solve_all()
-    dst = tmp_path / "one_tile.npz"
+    dst = tmp_path / "persistent.npz"
     code = ("import sys, numpy as np; sys.path.insert(0, %r); "
             "import tests.test_gpu_zpersist as T; np.savez(%r, **T._solve_all())" % (ROOT, str(dst)))
-    env = dict(os.environ, CALES_ZPERSIST="0")
+    env = dict(os.environ, CALES_ZPERSIST="1")
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     other = np.load(dst)

@@ -300,18 +300,26 @@ int cales_adam_step(float* theta, const double* grad, float* m, float* v, int n,
                     float eps, int t, float grad_scale, void* stream);
 
 /*
- * Launch schedule of a plan: {x shared-memory budget per CTA in KB, y tile
- * width in columns, z warps per CTA, z rows-per-segment bound}; 0 selects the
- * built-in heuristic.  Infeasible values fall back to the heuristic.
+ * Launch schedule of a plan, CALES_SCHED_LEN entries: {x shared-memory budget
+ * per CTA in KB, y tile width in columns, z warps per CTA, z rows-per-segment
+ * bound, FFT radix order of x and y (0: radix-16 passes first, the order of
+ * the compile-time-size kernels; 1: radices 5 and 3 first; 2: radix-8 passes
+ * in place of radix 16), z kernel variant (0: one 32-mode tile per CTA; 1:
+ * persistent CTAs with two tile buffers)}; 0 selects the built-in heuristic
+ * and infeasible sizes fall back to it.  A new radix order rebuilds the
+ * plan's transform tables (synchronises the device).  CALES_EINVAL for
+ * negative entries, an order > 2 or a variant > 1.
  */
-int cales_set_schedule(cales_plan_t plan, const int sched[4]);
-int cales_get_schedule(cales_plan_t plan, int sched[4]);
+#define CALES_SCHED_LEN 6
+int cales_set_schedule(cales_plan_t plan, const int sched[CALES_SCHED_LEN]);
+int cales_get_schedule(cales_plan_t plan, int sched[CALES_SCHED_LEN]);
 
 /*
  * Autotuner (the analogue of the paper's runtime-tuned decomposition and
  * communication backends, Sec. 3.1): times candidate schedules of the plan's
- * Poisson solve at its current precision on the device (each stage tuned in
- * turn: x budget 32/64/96 KB, y tiles 8/16/32, z segments 16/32/64 rows),
+ * Poisson solve at its current precision on the device (each knob tuned in
+ * turn: FFT radix order 0/1/2 on the x + y stages, x budget 32/64/96 KB, y
+ * tiles 8/16/32, z segments of 16/32/64 rows, then the z kernel variant),
  * keeps the fastest and sets it on the plan.  With cache_path non-NULL the
  * result is looked up first and stored after tuning in a JSON object keyed by
  * "nx,ny,nz,bcx,bcy,zlo,zhi,precision,device".  Allocates two temporary fields
@@ -323,18 +331,30 @@ int cales_autotune(cales_plan_t plan, const char* cache_path, void* stream);
  * Batched solves (a Runge-Kutta substep of Algorithm 1: per domain the three
  * Helmholtz solves of Eq. 18 and the Poisson solve of Eq. 12, over many
  * independent domains).  kinds[i]: 0 = Poisson, 1 = Helmholtz with alphas[i].
- * Solves are forked over up to 8 streams balanced by grid size (solves that
- * share a plan stay on one stream) and joined back on the caller's stream.
+ * Grouped execution (default): when every plan is CALES_FP32_REFINE with the
+ * same sweep count, a non-periodic z and no plan serves two solves, each
+ * stage of the solver (x, y, z transforms and sweeps, residual) runs once for
+ * all solves of the batch -- one launch per stage and kernel variant, whose
+ * CTAs walk a (solve, block) work list; 17 launches and 4 memsets for two
+ * sweeps, whatever the batch size.  The argument blocks are built and copied
+ * to the device (synchronously) on the first solve or capture with a set of
+ * buffers, and again when the buffers change.  Otherwise the solves are
+ * forked over up to 8 streams balanced by grid size (solves that share a plan
+ * stay on one stream) and joined back on the caller's stream.
  * cales_batch_solve enqueues directly; cales_batch_capture records the same
- * fork/join for fixed f[i], u[i] into one CUDA graph, replayed by
+ * work for fixed f[i], u[i] into one CUDA graph, replayed by
  * cales_batch_launch with a single launch.  Plans, precisions and the
  * pointers captured must stay valid while the graph is used.
+ * cales_batch_set_grouped(batch, 0) forces the fork/join path;
+ * cales_batch_grouped reports whether the last solve or capture was grouped.
  */
 int cales_batch_create(cales_batch_t* out, int n, const cales_plan_t* plans, const int* kinds, const double* alphas);
 int cales_batch_solve(cales_batch_t batch, const void* const* f, void* const* u, void* stream);
 int cales_batch_capture(cales_batch_t batch, const void* const* f, void* const* u, void* stream);
 int cales_batch_launch(cales_batch_t batch, void* stream);
 int cales_batch_graph_nodes(cales_batch_t batch, unsigned long* nodes);
+int cales_batch_set_grouped(cales_batch_t batch, int on);
+int cales_batch_grouped(cales_batch_t batch, int* used);
 void cales_batch_destroy(cales_batch_t batch);
 
 /* Asynchronous zero fill of `bytes` bytes of device memory (accumulators). */

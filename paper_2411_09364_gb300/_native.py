@@ -49,6 +49,8 @@ SIGNATURES = {
     "cales_batch_capture": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
     "cales_batch_launch": (C.c_int, [vp, vp]),
     "cales_batch_graph_nodes": (C.c_int, [vp, C.POINTER(C.c_ulong)]),
+    "cales_batch_set_grouped": (C.c_int, [vp, C.c_int]),
+    "cales_batch_grouped": (C.c_int, [vp, ip]),
     "cales_batch_destroy": (None, [vp]),
     "cales_gradient_adjoint": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "cales_stencil27": (C.c_int, [vp, vp, C.c_float, C.c_float, C.POINTER(vp), C.POINTER(vp), vp]),

@@ -55,6 +55,17 @@ class Batch:
     def launch(self, stream=None):
         N.check(N.lib().cales_batch_launch(self._h, _stream(stream)), "cales_batch_launch")
 
+    def set_grouped(self, on: bool = True):
+        """Grouped stage launches (default) or the fork/join over streams."""
+        N.check(N.lib().cales_batch_set_grouped(self._h, 1 if on else 0), "cales_batch_set_grouped")
+        return self
+
+    def grouped(self) -> bool:
+        """Whether the last solve or capture used the grouped stage launches."""
+        v = C.c_int(0)
+        N.check(N.lib().cales_batch_grouped(self._h, C.byref(v)), "cales_batch_grouped")
+        return bool(v.value)
+
     def graph_nodes(self) -> int:
         n = C.c_ulong(0)
         N.check(N.lib().cales_batch_graph_nodes(self._h, C.byref(n)), "cales_batch_graph_nodes")
@@ -86,15 +97,21 @@ def channel_domain_plans(nx, ny, nz, beta=1.8, lx=2 * math.pi, ly=math.pi, lz=2.
     return {"u": uv, "v": u2, "w": w, "p": p}
 
 
-def rk3_substep_batch(domains, alphas, precision=FP32_REFINE, sweeps=2, beta=1.8):
+def rk3_substep_batch(domains, alphas, precision=FP32_REFINE, sweeps=2, beta=1.8, autotune=True, cache_path=None):
     """Plans and solve list of one RK3 substep over several channel domains.
 
-    domains: list of (nx, ny, nz); alphas: Helmholtz alpha per domain.
+    domains: list of (nx, ny, nz); alphas: Helmholtz alpha per domain.  With
+    ``autotune`` every plan's launch schedule comes from the device autotuner
+    (cales_autotune; looked up in / stored to the JSON ``cache_path`` when
+    given), before the batch is built.
     Returns (batch, plan list, [(domain index, field name)] in batch order).
     """
     plans, kinds, als, tags = [], [], [], []
     for d, (nx, ny, nz) in enumerate(domains):
         dp = channel_domain_plans(nx, ny, nz, beta=beta, precision=precision, sweeps=sweeps)
+        if autotune:
+            for pl in dp.values():
+                pl.autotune(cache_path)
         for name in ("u", "v", "w", "p"):
             plans.append(dp[name])
             kinds.append(0 if name == "p" else 1)

@@ -20,10 +20,14 @@
 #include <string>
 #include <vector>
 
+#include "batch_group.h"
 #include "cales.h"
 #include "plan.h"
 
 struct cales_batch_s {
+    GroupedBatch* grp = nullptr;       // grouped stage launches for the last buffers (nullptr: fork/join)
+    int grouped = 1;                   // try grouped launches (cales_batch_set_grouped)
+    int used_grouped = 0;              // the last solve / capture used them
     std::vector<cales_plan_t> plans;
     std::vector<int> kinds;
     std::vector<double> alphas;
@@ -86,9 +90,10 @@ std::map<std::string, std::vector<int>> read_cache(const char* path) {
         char* q2 = strchr(q1 + 1, '"');
         if (!q2) continue;
         std::string key(q1 + 1, q2);
-        int v[4];
+        int v[6] = {0, 0, 0, 0, 0, 0};
         char* br = strchr(q2, '[');
-        if (br && sscanf(br, "[%d,%d,%d,%d]", &v[0], &v[1], &v[2], &v[3]) == 4) m[key] = {v[0], v[1], v[2], v[3]};
+        const int got = br ? sscanf(br, "[%d,%d,%d,%d,%d,%d]", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) : 0;
+        if (got == 4 || got == 6) m[key] = {v[0], v[1], v[2], v[3], v[4], v[5]};
     }
     fclose(fp);
     return m;
@@ -100,8 +105,8 @@ bool write_cache(const char* path, const std::map<std::string, std::vector<int>>
     fprintf(fp, "{\n");
     size_t i = 0;
     for (const auto& kv : m) {
-        fprintf(fp, "  \"%s\": [%d,%d,%d,%d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
-                kv.second[3], ++i < m.size() ? "," : "");
+        fprintf(fp, "  \"%s\": [%d,%d,%d,%d,%d,%d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1],
+                kv.second[2], kv.second[3], kv.second[4], kv.second[5], ++i < m.size() ? "," : "");
     }
     fprintf(fp, "}\n");
     fclose(fp);
@@ -133,18 +138,20 @@ int stage_times(cales_plan_t P, const void* f, void* p, cudaStream_t st, int rep
 
 extern "C" {
 
-int cales_set_schedule(cales_plan_t P, const int sched[4]) {
+int cales_set_schedule(cales_plan_t P, const int sched[CALES_SCHED_LEN]) {
     if (!P || !sched) return CALES_EINVAL;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < CALES_SCHED_LEN; ++i)
         if (sched[i] < 0) return CALES_EINVAL;
-        P->sched[i] = sched[i];
-    }
+    if (sched[4] > 2 || sched[5] > 1) return CALES_EINVAL;
+    const int rc = plan_set_radix_order(P, sched[4]);
+    if (rc) return rc;
+    for (int i = 0; i < CALES_SCHED_LEN; ++i) P->sched[i] = sched[i];
     return CALES_OK;
 }
 
-int cales_get_schedule(cales_plan_t P, int sched[4]) {
+int cales_get_schedule(cales_plan_t P, int sched[CALES_SCHED_LEN]) {
     if (!P || !sched) return CALES_EINVAL;
-    for (int i = 0; i < 4; ++i) sched[i] = P->sched[i];
+    for (int i = 0; i < CALES_SCHED_LEN; ++i) sched[i] = P->sched[i];
     return CALES_OK;
 }
 
@@ -162,55 +169,70 @@ int cales_autotune(cales_plan_t P, const char* cache_path, void* stream) {
     if (cudaMalloc(&f, n * esz) != cudaSuccess) return CALES_ENOMEM;
     if (cudaMalloc(&p, n * esz) != cudaSuccess) { cudaFree(f); return CALES_ENOMEM; }
     cudaMemsetAsync(f, 0, n * esz, st);
-    int best[4] = {0, 0, 0, 0};
+    int best[CALES_SCHED_LEN] = {0, 0, 0, 0, 0, 0};
     int rc = cales_set_schedule(P, best);
     double t[3];
     rc = rc ? rc : stage_times(P, f, p, st, 1, t);      // warm-up
+    // time a candidate: knobs k1 (and k2) changed from the best so far; false
+    // when the schedule is refused or a launch fails
+    auto trial = [&](int k1, int v1, int k2, int v2, double out[3]) {
+        int s[CALES_SCHED_LEN];
+        for (int i = 0; i < CALES_SCHED_LEN; ++i) s[i] = best[i];
+        s[k1] = v1;
+        if (k2 >= 0) s[k2] = v2;
+        out[0] = out[1] = out[2] = 1e30;
+        if (rc || cales_set_schedule(P, s) != CALES_OK) return false;
+        rc = stage_times(P, f, p, st, 1, out);            // first run with a new schedule fills caches
+        if (!rc) rc = stage_times(P, f, p, st, 3, out);
+        return rc == CALES_OK;
+    };
+    // FFT radix order (x and y stages together)
+    {
+        double bt = 1e30;
+        for (int c = 0; c <= 2; ++c)
+            if (trial(4, c, -1, 0, t) && t[0] + t[1] < bt) { bt = t[0] + t[1]; best[4] = c; }
+    }
     // x: shared-memory budget per CTA
     {
         double bt = 1e30;
         const int cand[3] = {32, 64, 96};
-        for (int c : cand) {
-            int s[4] = {c, best[1], best[2], best[3]};
-            cales_set_schedule(P, s);
-            if (!rc) rc = stage_times(P, f, p, st, 3, t);
-            if (!rc && t[0] < bt) { bt = t[0]; best[0] = c; }
-        }
+        for (int c : cand)
+            if (trial(0, c, -1, 0, t) && t[0] < bt) { bt = t[0]; best[0] = c; }
     }
     // y: tile width
     if (P->ny > 1) {
         double bt = 1e30;
         const int cand[4] = {8, 16, 32, 0};
-        for (int c : cand) {
-            int s[4] = {best[0], c, best[2], best[3]};
-            cales_set_schedule(P, s);
-            if (!rc) rc = stage_times(P, f, p, st, 3, t);
-            if (!rc && t[1] < bt) { bt = t[1]; best[1] = c; }
-        }
+        for (int c : cand)
+            if (trial(1, c, -1, 0, t) && t[1] < bt) { bt = t[1]; best[1] = c; }
     }
-    // z: warps x segment bound
+    // z: warps x segment bound, then the kernel variant (kept only when it
+    // wins by more than 3 %)
     {
         double bt = 1e30;
+        int bw = 0, bm = 0;
         const int mms[3] = {16, 32, 64};
         for (int mm : mms) {
             const int w = (P->nz + mm - 1) / mm;
             if (w < 1 || w > 16) continue;
-            int s[4] = {best[0], best[1], w, mm};
-            cales_set_schedule(P, s);
-            if (!rc) rc = stage_times(P, f, p, st, 3, t);
-            if (!rc && t[2] < bt) { bt = t[2]; best[2] = w; best[3] = mm; }
+            if (trial(2, w, 3, mm, t) && t[2] < bt) { bt = t[2]; bw = w; bm = mm; }
         }
+        best[2] = bw;
+        best[3] = bm;
+        double tz[3];
+        if (trial(5, 1, -1, 0, tz) && tz[2] < 0.97 * bt) best[5] = 1;
     }
     cudaFree(f);
     cudaFree(p);
     if (rc) {
-        int zero[4] = {0, 0, 0, 0};
+        int zero[CALES_SCHED_LEN] = {0, 0, 0, 0, 0, 0};
         cales_set_schedule(P, zero);
         return rc;
     }
-    cales_set_schedule(P, best);
+    rc = cales_set_schedule(P, best);
+    if (rc) return rc;
     if (cache_path) {
-        cache[key] = {best[0], best[1], best[2], best[3]};
+        cache[key] = std::vector<int>(best, best + CALES_SCHED_LEN);
         write_cache(cache_path, cache);
     }
     return CALES_OK;
@@ -261,17 +283,53 @@ int cales_batch_create(cales_batch_t* out, int n, const cales_plan_t* plans, con
     return CALES_OK;
 }
 
+// The grouped launches for buffers f -> u (built on first use, rebuilt when
+// the buffers change); nullptr when the batch takes the fork/join path.
+static int prepare_grouped(cales_batch_t B, const void* const* f, void* const* u) {
+    B->used_grouped = 0;
+    if (!B->grouped) return CALES_OK;
+    if (!grouped_same_buffers(B->grp, f, u)) {
+        grouped_free(B->grp);
+        int rc = CALES_OK;
+        B->grp = grouped_build(B->plans, B->kinds, B->alphas, f, u, &rc);
+        if (rc) return rc;
+    }
+    B->used_grouped = B->grp ? 1 : 0;
+    return CALES_OK;
+}
+
 int cales_batch_solve(cales_batch_t B, const void* const* f, void* const* u, void* stream) {
     if (!B || !f || !u) return CALES_EINVAL;
-    return enqueue(B, f, u, reinterpret_cast<cudaStream_t>(stream));
+    const int rc = prepare_grouped(B, f, u);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return B->used_grouped ? grouped_enqueue(B->grp, st) : enqueue(B, f, u, st);
+}
+
+int cales_batch_set_grouped(cales_batch_t B, int on) {
+    if (!B) return CALES_EINVAL;
+    B->grouped = on ? 1 : 0;
+    if (!on) {
+        grouped_free(B->grp);
+        B->grp = nullptr;
+    }
+    return CALES_OK;
+}
+
+int cales_batch_grouped(cales_batch_t B, int* used) {
+    if (!B || !used) return CALES_EINVAL;
+    *used = B->used_grouped;
+    return CALES_OK;
 }
 
 int cales_batch_capture(cales_batch_t B, const void* const* f, void* const* u, void* stream) {
     if (!B || !f || !u || !stream) return CALES_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     destroy_graph(B);
+    const int prc = prepare_grouped(B, f, u);       // uploads argument blocks: before the capture
+    if (prc) return prc;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CALES_ECUDA;
-    const int rc = enqueue(B, f, u, st);
+    const int rc = B->used_grouped ? grouped_enqueue(B->grp, st) : enqueue(B, f, u, st);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(st, &g);
     if (rc) {
@@ -303,6 +361,7 @@ int cales_batch_graph_nodes(cales_batch_t B, unsigned long* nodes) {
 void cales_batch_destroy(cales_batch_t B) {
     if (!B) return;
     destroy_graph(B);
+    grouped_free(B->grp);
     for (cudaStream_t s : B->streams)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : B->join)

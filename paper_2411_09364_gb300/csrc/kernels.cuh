@@ -162,6 +162,26 @@ template <typename T> size_t zsolve_w_smem(int nz, int P);
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_eddy_viscosity(const SgsArgs<T>& a, cudaStream_t st);
 cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st);
+int residual_rows_per_cta(int nx, int ny);
+
+// Grouped launches: the same stage of many solves in one launch; CTA b runs
+// block work[b].y of item work[b].x (argument blocks in device memory).
+template <typename T> size_t rows_smem_bytes(const RowArgs<T>& a);
+template <typename T> size_t cols_smem_bytes(const ColArgs<T>& a);
+template <typename T> size_t zsolve_w_smem_pb(int nz, int P, int Pb);
+template <typename T, typename TIn>
+cudaError_t launch_rows_forward_grp(const RowArgs<T>* items, const int2* work, int nblocks, size_t smem, cudaStream_t);
+template <typename T, int MODE>
+cudaError_t launch_rows_inverse_grp(const RowArgs<T>* items, const int2* work, int nblocks, size_t smem, cudaStream_t);
+template <typename T>
+cudaError_t launch_cols_grp(const ColArgs<T>* items, const int2* work, int nblocks, int tx, bool inverse, size_t smem,
+                            cudaStream_t);
+template <typename T>
+cudaError_t launch_zsolve_grp(const ZArgs<T>* items, const int2* work, int nblocks, int maxm, bool adjoint,
+                              int threads, size_t smem, cudaStream_t);
+// variant bits: 1 singular (consistency shift), 2 Helmholtz, 4 gauge sum, 8 lo parts present
+cudaError_t launch_residual_ff_grp(const ResidFFArgs* items, const int2* work, int nblocks, int variant,
+                                   cudaStream_t st);
 
 // ---- projection operators and learned-closure kernels ----
 template <typename T> struct GridArgs {

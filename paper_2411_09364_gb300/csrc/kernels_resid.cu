@@ -257,10 +257,9 @@ __device__ __forceinline__ float4 sc4(float g, float4 v) { return make_float4(g 
 // f come in one vector load each, the x neighbours of the pair in two 8-byte
 // loads.  A CTA covers whole rows of one z-plane.
 template <bool SING, bool HELM, bool GAUGE, bool LO>
-__global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
+__device__ __forceinline__ void residual_df_body(const ResidFFArgs& a, const int bx, const int k) {
     const int nx = a.nx, ny = a.ny;
     const long plane = (long)nx * ny;
-    const int k = blockIdx.y;
     const long kbase = (long)k * plane;
     const float2* __restrict__ u = a.u;
     const ff za = ff_from_double(a.c1 * a.za[k]), zc = ff_from_double(a.c1 * a.zc[k]);
@@ -273,7 +272,7 @@ __global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
     const bool px_ = a.bcx == KIND_P, py_ = a.bcy == KIND_P;
     float ghi = 0.f, glo = 0.f;
     const int npair = nx >> 1;
-    const int j0 = blockIdx.x * a.rows_per_cta, j1 = min(j0 + a.rows_per_cta, ny);
+    const int j0 = bx * a.rows_per_cta, j1 = min(j0 + a.rows_per_cta, ny);
     // neighbour offsets and multipliers: a ghost reads the centre (offset 0)
     // and scales it (Neumann mirror 1, Dirichlet -1, node 0); the tests on
     // the multipliers are uniform per CTA (z) or per row (y)
@@ -328,6 +327,59 @@ __global__ void __launch_bounds__(256) k_residual_df(ResidFFArgs a) {
     }
 }
 
+template <bool SING, bool HELM, bool GAUGE, bool LO>
+__global__ void __launch_bounds__(256) k_residual_df(const __grid_constant__ ResidFFArgs a) {
+    residual_df_body<SING, HELM, GAUGE, LO>(a, blockIdx.x, blockIdx.y);
+}
+
+// Grouped launch over many solves: CTA b takes block work[b].y (row block +
+// plane, row blocks fastest) of item work[b].x.
+template <bool SING, bool HELM, bool GAUGE, bool LO>
+__global__ void __launch_bounds__(256) k_residual_df_grp(const ResidFFArgs* __restrict__ items,
+                                                         const int2* __restrict__ work) {
+    __shared__ __align__(16) ResidFFArgs sa;
+    const int2 w = work[blockIdx.x];
+    {
+        const int* src = reinterpret_cast<const int*>(items + w.x);
+        int* d = reinterpret_cast<int*>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(ResidFFArgs) / 4); i += blockDim.x) d[i] = src[i];
+    }
+    __syncthreads();
+    const int nby = (sa.ny + sa.rows_per_cta - 1) / sa.rows_per_cta;
+    const int k = w.y / nby;
+    residual_df_body<SING, HELM, GAUGE, LO>(sa, w.y - k * nby, k);
+}
+
+// Rows per CTA of the double-float residual: about 4096 points, whole rows.
+int residual_rows_per_cta(int nx, int ny) {
+    int rows = (int)((4096 + nx - 1) / nx);
+    if (rows < 1) rows = 1;
+    if (rows > ny) rows = ny;
+    return rows;
+}
+
+cudaError_t launch_residual_ff_grp(const ResidFFArgs* items, const int2* work, int nblocks, int variant,
+                                   cudaStream_t st) {
+    // variant bits: 1 SING, 2 HELM, 4 GAUGE, 8 LO
+    const dim3 g((unsigned)nblocks), b(256);
+    switch (variant) {
+        case 0: k_residual_df_grp<false, false, false, false><<<g, b, 0, st>>>(items, work); break;
+        case 2: k_residual_df_grp<false, true, false, false><<<g, b, 0, st>>>(items, work); break;
+        case 1: k_residual_df_grp<true, false, false, false><<<g, b, 0, st>>>(items, work); break;
+        case 3: k_residual_df_grp<true, true, false, false><<<g, b, 0, st>>>(items, work); break;
+        case 5: k_residual_df_grp<true, false, true, false><<<g, b, 0, st>>>(items, work); break;
+        case 7: k_residual_df_grp<true, true, true, false><<<g, b, 0, st>>>(items, work); break;
+        case 8: k_residual_df_grp<false, false, false, true><<<g, b, 0, st>>>(items, work); break;
+        case 10: k_residual_df_grp<false, true, false, true><<<g, b, 0, st>>>(items, work); break;
+        case 9: k_residual_df_grp<true, false, false, true><<<g, b, 0, st>>>(items, work); break;
+        case 11: k_residual_df_grp<true, true, false, true><<<g, b, 0, st>>>(items, work); break;
+        case 13: k_residual_df_grp<true, false, true, true><<<g, b, 0, st>>>(items, work); break;
+        case 15: k_residual_df_grp<true, true, true, true><<<g, b, 0, st>>>(items, work); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <bool LO>
 static void launch_df(const ResidFFArgs& a, dim3 grid, bool sing, bool helm, cudaStream_t st) {
     if (a.gacc && !helm) k_residual_df<true, false, true, LO><<<grid, 256, 0, st>>>(a);
@@ -340,10 +392,7 @@ static void launch_df(const ResidFFArgs& a, dim3 grid, bool sing, bool helm, cud
 
 cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     ResidFFArgs a = a0;
-    // about 4096 points per CTA, whole rows
-    int rows = (int)((4096 + a.nx - 1) / a.nx);
-    if (rows < 1) rows = 1;
-    if (rows > a.ny) rows = a.ny;
+    const int rows = residual_rows_per_cta(a.nx, a.ny);
     a.rows_per_cta = rows;
     dim3 grid((unsigned)((a.ny + rows - 1) / rows), (unsigned)a.nz);
     const bool vec = (a.nx % 2 == 0) && ((uintptr_t)a.u % 16 == 0) && ((uintptr_t)a.f % 16 == 0) &&

@@ -45,20 +45,36 @@ void cis_frac(long num, long den, double& c, double& s) {
     }
 }
 
-bool factorize(int L, int* radix, int& nrad) {
+// Radix passes of a length-L FFT.  order 0: radix 16 first (fewest
+// shared-memory passes; the compile-time-size kernels use this order, see
+// sf_radix), then one 8, 4 or 2, then the 5s and 3s; order 1: the 5s and 3s
+// first, then the powers of two as in order 0; order 2: radix 8 passes
+// instead of 16 (more passes, fewer registers per butterfly).
+bool factorize(int L, int* radix, int& nrad, int order = 0) {
     nrad = 0;
     int m = L;
-    int twos = 0;
+    int twos = 0, fives = 0, threes = 0;
     while (m % 2 == 0) { m /= 2; ++twos; }
-    // radix 16 first (fewer shared-memory passes); the compile-time-size
-    // kernels use the same order (sf_radix)
-    while (twos >= 4) { radix[nrad++] = 16; twos -= 4; }
-    while (twos >= 3) { radix[nrad++] = 8; twos -= 3; }
-    if (twos == 2) radix[nrad++] = 4;
-    if (twos == 1) radix[nrad++] = 2;
-    while (m % 5 == 0) { m /= 5; radix[nrad++] = 5; }
-    while (m % 3 == 0) { m /= 3; radix[nrad++] = 3; }
-    return m == 1 && nrad <= MAX_RADICES;
+    while (m % 5 == 0) { m /= 5; ++fives; }
+    while (m % 3 == 0) { m /= 3; ++threes; }
+    if (m != 1) return false;
+    auto odd = [&] {
+        for (int i = 0; i < fives && nrad < MAX_RADICES; ++i) radix[nrad++] = 5;
+        for (int i = 0; i < threes && nrad < MAX_RADICES; ++i) radix[nrad++] = 3;
+    };
+    auto pow2 = [&] {
+        int t = twos;
+        if (order != 2)
+            while (t >= 4 && nrad < MAX_RADICES) { radix[nrad++] = 16; t -= 4; }
+        while (t >= 3 && nrad < MAX_RADICES) { radix[nrad++] = 8; t -= 3; }
+        if (t == 2 && nrad < MAX_RADICES) radix[nrad++] = 4;
+        if (t == 1 && nrad < MAX_RADICES) radix[nrad++] = 2;
+    };
+    if (order == 1) { odd(); pow2(); }
+    else { pow2(); odd(); }
+    int prod = 1;
+    for (int i = 0; i < nrad; ++i) prod *= radix[i];
+    return prod == L;
 }
 
 template <typename T> T* dev_upload(const std::vector<T>& h, std::vector<void*>& owned) {
@@ -72,7 +88,7 @@ template <typename T> T* dev_upload(const std::vector<T>& h, std::vector<void*>&
 // Tables of one uniform direction of n unknowns, transform kind `kind`
 // (KIND_P .. KIND_DN) and spacing h.  FFT length L = n/2, or n + 1 for the
 // DST-I of node-centred unknowns (the real DFT of the odd extension).
-int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) {
+int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned, int order = 0) {
     d.n = n;
     d.kind = kind;
     if (kind == KIND_DF) {
@@ -81,7 +97,7 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
         if (n > 1 && (n % 2)) return CALES_EUNSUPPORTED;
         d.L = n >= 2 ? n / 2 : 1;
     }
-    if (!factorize(d.L, d.radix, d.nrad)) return CALES_EUNSUPPORTED;
+    if (!factorize(d.L, d.radix, d.nrad, order)) return CALES_EUNSUPPORTED;
     const int L = d.L;
     // per-pass twiddles W_L^(r k tstep) at twoff[p] + (r - 1) Ns + k
     std::vector<double2> tw, post(L + 1), mak(L + 1);
@@ -161,6 +177,37 @@ int build_dir(DirHost& d, int n, int kind, double h, std::vector<void*>& owned) 
 }
 
 }  // namespace
+
+// Rebuild the x and y tables with FFT radix order `order` (see factorize);
+// the old tables are released.  CALES_EUNSUPPORTED leaves the plan as it was.
+int plan_set_radix_order(cales_plan_s* P, int order) {
+    if (order == P->radix_order) return CALES_OK;
+    if (order < 0 || order > 2) return CALES_EINVAL;
+    DirHost nx_, ny_;
+    std::vector<void*> fresh;
+    int rc = build_dir(nx_, P->nx, P->X.kind, P->dx, fresh, order);
+    if (rc == CALES_OK) rc = build_dir(ny_, P->ny, P->Y.kind, P->dy, fresh, order);
+    if (rc != CALES_OK) {
+        for (void* q : fresh) cudaFree(q);
+        return rc;
+    }
+    for (DirHost* d : {&P->X, &P->Y}) {
+        const void* old[8] = {d->tw_d, d->post_d, d->mak_d, d->lam_d, d->tw_f, d->post_f, d->mak_f, d->lam_f};
+        for (const void* q : old) {
+            for (size_t i = 0; i < P->owned.size(); ++i)
+                if (P->owned[i] == q) {
+                    cudaFree(P->owned[i]);
+                    P->owned.erase(P->owned.begin() + (long)i);
+                    break;
+                }
+        }
+    }
+    P->X = nx_;
+    P->Y = ny_;
+    P->owned.insert(P->owned.end(), fresh.begin(), fresh.end());
+    P->radix_order = order;
+    return CALES_OK;
+}
 
 template <> DirTab<double> DirHost::tab<double>() const {
     DirTab<double> t;
@@ -303,24 +350,16 @@ static bool zpersist_enabled() {
     return on;
 }
 
-// Per-solve options of one pass of the solver.
-struct PassOpt {
-    double sigma, alpha, scale;
-    bool singular, adjoint;
-    double* cacc;              // consistency-constant accumulator (singular mode 0)
-    const double* shift_acc;   // gauge accumulator subtracted by the inverse-x kernel
-    double shift_scale;
-};
-
-// One pass of the solver: in (TIn) -> work (T, mode space) -> out (MODE).
-template <typename T, typename TIn, int MODE>
-int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st) {
-    const long nrows = (long)P->ny * P->nz;
+// Argument blocks of the stages of one pass: in (TIn) -> work (T, mode
+// space) -> out (MODE).  Shared by the single-solve pipeline and the grouped
+// batch executor.
+template <typename T, typename TIn>
+RowArgs<T> fwd_row_args(cales_plan_s* P, const void* in, T* work) {
     RowArgs<T> ra;
     ra.t = P->X.tab<T>();
     ra.in = in;
     ra.out = work;
-    ra.nrows = nrows;
+    ra.nrows = (long)P->ny * P->nz;
     ra.rpc = rows_per_cta<T>(2 * P->X.L, 0, P->sched[0]);
     ra.in_scale = 1.0;
     ra.shift_acc = nullptr;
@@ -328,10 +367,11 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ra.status = P->status;
     ra.bulk = (aligned16(in) && aligned16(work) && ((size_t)P->nx * sizeof(TIn)) % 16 == 0 &&
                ((size_t)P->nx * sizeof(T)) % 16 == 0) ? 1 : 0;
-    P->prof_begin(st, "x_fwd");
-    if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
-    P->prof_end(st);
+    return ra;
+}
 
+template <typename T>
+ColArgs<T> col_args(cales_plan_s* P, T* work) {
     ColArgs<T> ca;
     ca.t = P->Y.tab<T>();
     ca.data = work;
@@ -340,12 +380,13 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ca.tx = choose_tx<T>(2 * P->Y.L, P->sched[1]);
     ca.bulk = (aligned16(work) && ((size_t)P->nx * sizeof(T)) % 16 == 0 && ca.tx * sizeof(T) >= 16) ? 1 : 0;
     ca.status = P->status;
-    if (P->ny > 1) {
-        P->prof_begin(st, "y_fwd");
-        if (launch_cols<T>(ca, false, st) != cudaSuccess) return CALES_ECUDA;
-        P->prof_end(st);
-    }
+    return ca;
+}
 
+// z stage; the pivot-cache mode is chosen from the plan's cache key, which
+// z_args_done updates once the launch is enqueued.
+template <typename T>
+ZArgs<T> z_args(cales_plan_s* P, T* work, const PassOpt& o) {
     ZArgs<T> za;
     za.data = work;
     za.src = nullptr;
@@ -368,26 +409,62 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     za.ecache_mode = 0;
     const int zi = sizeof(T) == 8 ? 1 : 0;
     cales_plan_s::ZCacheKey& zk = P->zkey[zi];
-    if (za.warp_mode && za.P <= 16 && P->zcache[zi]) {
+    if (za.warp_mode && za.P <= 16 && P->zcache[zi] && P->bc[4] != CALES_BC_P) {
         za.ecache = reinterpret_cast<T*>(P->zcache[zi]);
         za.ecache_mode = (zk.valid && zk.P == za.P && zk.maxm == za.maxm && zk.sigma == o.sigma &&
                           zk.alpha == o.alpha) ? 2 : 1;
     }
     za.ecache_stride = (long)P->nx * P->ny;
-    za.persist = zpersist_enabled() ? 1 : 0;
+    za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
+    return za;
+}
+
+template <typename T>
+void z_args_done(cales_plan_s* P, const ZArgs<T>& za, const PassOpt& o) {
+    if (za.ecache_mode == 1) {
+        cales_plan_s::ZCacheKey& zk = P->zkey[sizeof(T) == 8 ? 1 : 0];
+        zk.valid = 1; zk.P = za.P; zk.maxm = za.maxm; zk.sigma = o.sigma; zk.alpha = o.alpha;
+    }
+}
+
+template <typename T, int MODE>
+RowArgs<T> inv_row_args(cales_plan_s* P, T* work, void* out, const PassOpt& o) {
+    RowArgs<T> ri = fwd_row_args<T, T>(P, work, work);
+    ri.in = work;
+    ri.out = out;
+    ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
+               ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
+    ri.shift_acc = o.shift_acc;
+    ri.shift_scale = o.shift_scale;
+    return ri;
+}
+
+// One pass of the solver: in (TIn) -> work (T, mode space) -> out (MODE).
+template <typename T, typename TIn, int MODE>
+int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st) {
+    const RowArgs<T> ra = fwd_row_args<T, TIn>(P, in, work);
+    P->prof_begin(st, "x_fwd");
+    if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+
+    const ColArgs<T> ca = col_args<T>(P, work);
+    if (P->ny > 1) {
+        P->prof_begin(st, "y_fwd");
+        if (launch_cols<T>(ca, false, st) != cudaSuccess) return CALES_ECUDA;
+        P->prof_end(st);
+    }
+
+    ZArgs<T> za = z_args<T>(P, work, o);
     P->prof_begin(st, "z_solve");
     if (P->bc[4] == CALES_BC_P) {
         if (o.adjoint) return CALES_EUNSUPPORTED;
         T* ework = reinterpret_cast<T*>(P->zcyc);
         if (launch_zsolve_cyclic<T>(za, ework, ework + (size_t)P->nx * P->ny * P->nz, st) != cudaSuccess)
             return CALES_ECUDA;
-        za.ecache_mode = 0;
     } else if (launch_zsolve<T>(za, st) != cudaSuccess) {
         return CALES_ECUDA;
     }
-    if (za.ecache_mode == 1) {
-        zk.valid = 1; zk.P = za.P; zk.maxm = za.maxm; zk.sigma = o.sigma; zk.alpha = o.alpha;
-    }
+    z_args_done<T>(P, za, o);
     P->prof_end(st);
 
     if (P->ny > 1) {
@@ -396,14 +473,7 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
         P->prof_end(st);
     }
 
-    RowArgs<T> ri = ra;
-    ri.in = work;
-    ri.out = out;
-    ri.rpc = rows_per_cta<T>(2 * P->X.L, 0, P->sched[0]);
-    ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
-               ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
-    ri.shift_acc = o.shift_acc;
-    ri.shift_scale = o.shift_scale;
+    const RowArgs<T> ri = inv_row_args<T, MODE>(P, work, out, o);
     P->prof_begin(st, MODE >= OUT_FF_ACC ? "x_inv_acc" : "x_inv");
     if (launch_rows_inverse<T, MODE>(ri, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
@@ -429,6 +499,62 @@ void cales_plan_s::prof_end(cudaStream_t st) {
     ++prof_n;
 }
 
+namespace cales {
+
+PassOpt solve_opts(const cales_plan_s* P, bool helm, double alpha, bool adjoint) {
+    const double nxy = (double)P->nx * (double)P->ny;
+    PassOpt o;
+    o.sigma = helm ? 1.0 : 0.0;
+    o.alpha = helm ? alpha : 1.0;
+    o.scale = (helm ? 1.0 : -1.0) / nxy;
+    o.singular = !helm && P->singular_poisson;
+    o.adjoint = adjoint;
+    o.cacc = nullptr;
+    o.shift_acc = nullptr;
+    o.shift_scale = 0.0;
+    return o;
+}
+
+// Residual of sweep s (of ns) of the refinement: r = f - cacc - M p with p
+// held as pairs; the gauge sum into gacc on the last sweep of a singular
+// problem (the operator annihilates constants, so earlier iterates may
+// carry any mean).
+ResidFFArgs resid_args(const cales_plan_s* P, bool helm, double alpha, const void* f, void* p, float* work,
+                       double* cacc, double* gacc, int s, int ns) {
+    const bool sing = !helm && P->singular_poisson;
+    const double c1 = helm ? -alpha : 1.0;
+    ResidFFArgs ra;
+    ra.f = (const double*)f;
+    ra.u = (const float2*)p;
+    ra.r = work;
+    ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
+    ra.bcx = P->X.kind; ra.bcy = P->Y.kind; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
+    split_double(c1 / (P->dx * P->dx), ra.cxh, ra.cxl);
+    split_double(c1 / (P->dy * P->dy), ra.cyh, ra.cyl);
+    ra.c0h = helm ? 1.0f : 0.0f;
+    ra.za = P->za_d;
+    ra.zc = P->zc_d;
+    ra.c1 = c1;
+    ra.cshift = sing ? cacc : nullptr;
+    ra.gacc = (sing && s == ns - 1) ? gacc : nullptr;
+    ra.dzf = P->dzf_d;
+    ra.lo_zero = s == 0 ? 1 : 0;       // the FP32 solve wrote (v, 0) pairs
+    ra.rows_per_cta = residual_rows_per_cta(P->nx, P->ny);
+    return ra;
+}
+
+template RowArgs<float> fwd_row_args<float, double>(cales_plan_s*, const void*, float*);
+template RowArgs<float> fwd_row_args<float, float>(cales_plan_s*, const void*, float*);
+template ColArgs<float> col_args<float>(cales_plan_s*, float*);
+template ZArgs<float> z_args<float>(cales_plan_s*, float*, const PassOpt&);
+template void z_args_done<float>(cales_plan_s*, const ZArgs<float>&, const PassOpt&);
+template RowArgs<float> inv_row_args<float, OUT_F64>(cales_plan_s*, float*, void*, const PassOpt&);
+template RowArgs<float> inv_row_args<float, OUT_FF_INIT>(cales_plan_s*, float*, void*, const PassOpt&);
+template RowArgs<float> inv_row_args<float, OUT_FF_ACC>(cales_plan_s*, float*, void*, const PassOpt&);
+template RowArgs<float> inv_row_args<float, OUT_FF_FINAL>(cales_plan_s*, float*, void*, const PassOpt&);
+
+}  // namespace cales
+
 // FP32 solves with double-float refinement.  While sweeping, the caller's
 // FP64 output buffer holds the solution as (hi, lo) float pairs; the last
 // sweep writes it back as doubles.  For a singular Poisson problem the
@@ -445,27 +571,9 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
     int rc = ns == 0 ? pipeline<float, double, OUT_F64>(P, f, p, work, o, st)
                      : pipeline<float, double, OUT_FF_INIT>(P, f, p, work, o, st);
     if (rc) return rc;
-    const double c1 = helm ? -alpha : 1.0;
     for (int s = 0; s < ns; ++s) {
         if (sing && cudaMemsetAsync(acc + 1, 0, sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
-        ResidFFArgs ra;
-        ra.f = (const double*)f;
-        ra.u = (const float2*)p;
-        ra.r = work;
-        ra.nx = P->nx; ra.ny = P->ny; ra.nz = P->nz;
-        ra.bcx = P->X.kind; ra.bcy = P->Y.kind; ra.zlo = P->bc[4]; ra.zhi = P->bc[5];
-        split_double(c1 / (P->dx * P->dx), ra.cxh, ra.cxl);
-        split_double(c1 / (P->dy * P->dy), ra.cyh, ra.cyl);
-        ra.c0h = helm ? 1.0f : 0.0f;
-        ra.za = P->za_d;
-        ra.zc = P->zc_d;
-        ra.c1 = c1;
-        ra.cshift = sing ? acc : nullptr;
-        // the gauge of p is measured by the last sweep only: the operator
-        // annihilates constants, so earlier iterates may carry any mean
-        ra.gacc = (sing && s == ns - 1) ? acc + 1 : nullptr;
-        ra.dzf = P->dzf_d;
-        ra.lo_zero = s == 0 ? 1 : 0;       // the FP32 solve wrote (v, 0) pairs
+        const ResidFFArgs ra = resid_args(P, helm, alpha, f, p, work, acc, acc + 1, s, ns);
         P->prof_begin(st, "residual");
         if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
         P->prof_end(st);
@@ -490,16 +598,7 @@ static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, c
     if (helm && !(alpha > 0.0)) return CALES_EINVAL;
     if (P->bc[4] == CALES_BC_P && adjoint) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const double nxy = (double)P->nx * (double)P->ny;
-    PassOpt o;
-    o.sigma = helm ? 1.0 : 0.0;
-    o.alpha = helm ? alpha : 1.0;
-    o.scale = (helm ? 1.0 : -1.0) / nxy;
-    o.singular = !helm && P->singular_poisson;
-    o.adjoint = adjoint;
-    o.cacc = nullptr;
-    o.shift_acc = nullptr;
-    o.shift_scale = 0.0;
+    const PassOpt o = solve_opts(P, helm, alpha, adjoint);
     switch (P->precision) {
         case CALES_FP64:
             return pipeline<double, double, OUT_T>(P, f, p, (double*)p, o, st);
@@ -557,7 +656,7 @@ static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t 
     za.ecache = nullptr;
     za.ecache_mode = 0;
     za.ecache_stride = 0;
-    za.persist = zpersist_enabled() ? 1 : 0;
+    za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
     const int zi = sizeof(T) == 8 ? 1 : 0;
     cales_plan_s::ZCacheKey& lk = P->lkey[zi];
     if (za.warp_mode && za.P <= 16 && P->lcache[zi]) {

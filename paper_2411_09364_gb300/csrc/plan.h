@@ -28,6 +28,33 @@ struct ProfRec {
 };
 
 struct cales_plan_s;
+
+namespace cales {
+// Per-solve options of one pass of the solver.
+struct PassOpt {
+    double sigma, alpha, scale;
+    bool singular, adjoint;
+    double* cacc;              // consistency-constant accumulator (singular mode 0)
+    const double* shift_acc;   // gauge accumulator subtracted by the inverse-x kernel
+    double shift_scale;
+};
+// Argument blocks of the stages of one pass (plan.cu), shared by the
+// single-solve pipeline and the grouped batch executor.
+template <typename T, typename TIn> RowArgs<T> fwd_row_args(cales_plan_s* P, const void* in, T* work);
+template <typename T> ColArgs<T> col_args(cales_plan_s* P, T* work);
+template <typename T> ZArgs<T> z_args(cales_plan_s* P, T* work, const PassOpt& o);
+template <typename T> void z_args_done(cales_plan_s* P, const ZArgs<T>& za, const PassOpt& o);
+template <typename T, int MODE> RowArgs<T> inv_row_args(cales_plan_s* P, T* work, void* out, const PassOpt& o);
+// Options of a Poisson (helm false) or Helmholtz solve on plan P.
+PassOpt solve_opts(const cales_plan_s* P, bool helm, double alpha, bool adjoint);
+// Double-float residual arguments of refinement sweep s of ns.
+ResidFFArgs resid_args(const cales_plan_s* P, bool helm, double alpha, const void* f, void* p, float* work,
+                       double* cacc, double* gacc, int s, int ns);
+}  // namespace cales
+
+// Rebuild the x / y FFT tables with another radix order (plan.cu).
+int plan_set_radix_order(cales_plan_s* P, int order);
+
 // Internal entry shared by the C ABI, the batch executor and the autotuner.
 int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint, const void* f, void* p,
                          void* stream);
@@ -57,8 +84,12 @@ struct cales_plan_s {
     double dzf_sum = 0.0;
     int precision = 0, sweeps = 2;
     // launch schedule (0 = built-in heuristic): x shared-memory budget in KB,
-    // y tile width, z warps per CTA, z rows per segment bound
-    int sched[4] = {0, 0, 0, 0};
+    // y tile width, z warps per CTA, z rows per segment bound, radix order of
+    // the x and y FFTs (0 radix 16 first, 1 radices 5 and 3 first, 2 radix 8
+    // instead of 16), z kernel variant (0 one tile per CTA, 1 persistent)
+    static constexpr int NSCHED = 6;
+    int sched[NSCHED] = {0, 0, 0, 0, 0, 0};
+    int radix_order = 0;         // order the X and Y tables were built with
     float* work = nullptr;
     // Segment-entry pivots of the z sweeps (FP32 and FP64 copies, 16 segment
     // slots per mode) and the (sigma, alpha, P, maxm) they were computed for.

@@ -66,13 +66,13 @@ __device__ __forceinline__ void stage_twiddles(cpx<T>* tw_s, const DirTab<T>& t)
 // x direction
 // ---------------------------------------------------------------------------
 template <typename T, typename TIn, int LS = 0, int KS = -1>
-__global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
+__device__ __forceinline__ void rows_forward_body(const RowArgs<T>& a, const int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DirTab<T>& t = a.t;
     const int n = LS ? 2 * LS : t.n, L = LS ? LS : t.L;
     const int kind = KS >= 0 ? KS : t.kind;
     const int nrad = LS ? sf_nrad(LS) : t.nrad;
-    const long row0 = (long)blockIdx.x * a.rpc;
+    const long row0 = (long)bx * a.rpc;
     const int nr = (int)min((long)a.rpc, a.nrows - row0);
     const TIn* __restrict__ in = reinterpret_cast<const TIn*>(a.in) + row0 * n;
     T* __restrict__ out = reinterpret_cast<T*>(a.out) + row0 * n;
@@ -196,6 +196,11 @@ __global__ void __launch_bounds__(256) k_rows_forward(RowArgs<T> a) {
     }
 }
 
+template <typename T, typename TIn, int LS = 0, int KS = -1>
+__global__ void __launch_bounds__(256) k_rows_forward(const __grid_constant__ RowArgs<T> a) {
+    rows_forward_body<T, TIn, LS, KS>(a, blockIdx.x);
+}
+
 // pair + (v - shift) as a normalised pair; without a shift (every sweep but
 // the last of a singular problem) the single float v joins by one TwoSum.
 __device__ __forceinline__ ff pair_update(float2 pr, float v, ff shift, bool has_shift) {
@@ -254,13 +259,13 @@ __device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, 
 
 // Inverse along x; the output mode decides how the result is stored.
 template <typename T, int MODE, int LS = 0, int KS = -1>
-__global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
+__device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DirTab<T>& t = a.t;
     const int n = LS ? 2 * LS : t.n, L = LS ? LS : t.L;
     const int kind = KS >= 0 ? KS : t.kind;
     const int nrad = LS ? sf_nrad(LS) : t.nrad;
-    const long row0 = (long)blockIdx.x * a.rpc;
+    const long row0 = (long)bx * a.rpc;
     const int nr = (int)min((long)a.rpc, a.nrows - row0);
     const T* __restrict__ in = reinterpret_cast<const T*>(a.in) + row0 * n;
     constexpr int OSZ = MODE == OUT_T ? (int)sizeof(T) : 8;
@@ -381,6 +386,11 @@ __global__ void __launch_bounds__(256) k_rows_inverse(RowArgs<T> a) {
     }
 }
 
+template <typename T, int MODE, int LS = 0, int KS = -1>
+__global__ void __launch_bounds__(256) k_rows_inverse(const __grid_constant__ RowArgs<T> a) {
+    rows_inverse_body<T, MODE, LS, KS>(a, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // y direction: tiles of TX columns of one z-plane, in place.  With `bulk`, the
 // tile moves by 16-byte cp.async copies (all in flight), else by plain loads.
@@ -391,7 +401,7 @@ template <typename T> __host__ __device__ __forceinline__ size_t col_smem(int TX
 }
 
 template <typename T, int TX, bool INV, int LS = 0, int KS = -1>
-__global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
+__device__ __forceinline__ void cols_body(const ColArgs<T>& a, const int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DirTab<T>& t = a.t;
     const int n = LS ? 2 * LS : t.n, L = LS ? LS : t.L;     // n = ny
@@ -399,8 +409,8 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     const int nrad = LS ? sf_nrad(LS) : t.nrad;
     const int nx = a.nx;
     const int tiles_x = (nx + TX - 1) / TX;
-    const int plane = blockIdx.x / tiles_x;
-    const int x0 = (blockIdx.x - plane * tiles_x) * TX;
+    const int plane = bx / tiles_x;
+    const int x0 = (bx - plane * tiles_x) * TX;
     const int wx = min(TX, nx - x0);
     const int tid = threadIdx.x;
     T* __restrict__ base = reinterpret_cast<T*>(a.data) + (long)plane * n * nx + x0;
@@ -503,6 +513,11 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             if (c < wx) base[(long)s * nx + c] = ob[e];
         }
     }
+}
+
+template <typename T, int TX, bool INV, int LS = 0, int KS = -1>
+__global__ void __launch_bounds__(256) k_cols(const __grid_constant__ ColArgs<T> a) {
+    cols_body<T, TX, INV, LS, KS>(a, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -682,6 +697,44 @@ cudaError_t launch_cols_v(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<grid, 256, sm, st>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches: one launch covers the same stage of many solves.  CTA b
+// takes work[b] = (item, block of that item) and runs the item's kernel body
+// on its argument block, copied into shared memory first.  Dynamic shared
+// memory is the largest any item needs.
+// ---------------------------------------------------------------------------
+template <typename A>
+__device__ __forceinline__ int load_item_args(A& dst, const A* __restrict__ items, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    const int* src = reinterpret_cast<const int*>(items + w.x);
+    int* d = reinterpret_cast<int*>(&dst);
+    static_assert(sizeof(A) % 4 == 0, "argument block of whole words");
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) d[i] = src[i];
+    __syncthreads();
+    return w.y;
+}
+
+template <typename T, typename TIn>
+__global__ void __launch_bounds__(256) k_rows_forward_grp(const RowArgs<T>* __restrict__ items, const int2* __restrict__ work) {
+    __shared__ __align__(16) RowArgs<T> sa;
+    const int bx = load_item_args(sa, items, work);
+    rows_forward_body<T, TIn, 0, -1>(sa, bx);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_rows_inverse_grp(const RowArgs<T>* __restrict__ items, const int2* __restrict__ work) {
+    __shared__ __align__(16) RowArgs<T> sa;
+    const int bx = load_item_args(sa, items, work);
+    rows_inverse_body<T, MODE, 0, -1>(sa, bx);
+}
+
+template <typename T, int TX, bool INV>
+__global__ void __launch_bounds__(256) k_cols_grp(const ColArgs<T>* __restrict__ items, const int2* __restrict__ work) {
+    __shared__ __align__(16) ColArgs<T> sa;
+    const int bx = load_item_args(sa, items, work);
+    cols_body<T, TX, INV, 0, -1>(sa, bx);
 }
 
 }  // namespace cales

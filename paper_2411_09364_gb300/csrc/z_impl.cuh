@@ -670,10 +670,12 @@ __device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, lon
 // transposed) instead of the uniform forward scale.
 template <typename T, int MAXM, bool FULL, bool ADJ>
 __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch, const ZwTables<T>& tb, long q0,
-                                              int w) {
+                                              int w, const int P, const int Pb) {
+    // P: segments of this line; Pb = blockDim.x / 32 >= P warps, the chain
+    // arrays hold Pb slots.  Warps s >= P (grouped launches over lines of
+    // different depth) own no rows and only take part in the barriers.
     constexpr int TM = 32;
     const int nz = a.nz;
-    const int P = blockDim.x / 32;
     const int m = (nz + P - 1) / P;
     const int tid = threadIdx.x;
     const T* sA = tb.sA;
@@ -690,8 +692,9 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     const T base = a.sigma - a.alpha * lam;
     const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
     const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
-    const int k0 = s * m;
-    const int mseg = max(0, min(m, nz - k0));
+    const bool act = s < P;
+    const int k0 = act ? s * m : 0;
+    const int mseg = act ? max(0, min(m, nz - k0)) : 0;
     const ZPair<T>* AC = sAC + k0;
     const T* G = tb.sG + k0;
     const T* O = tb.sO + k0;
@@ -700,10 +703,10 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     (void)lastseg; (void)firstseg;
     T* col = tile + k0 * TM + c;
     T* c11 = ch;
-    T* c12 = ch + P * TM;
-    T* c21 = ch + 2 * P * TM;
-    T* c22 = ch + 3 * P * TM;
-    T* cin = ch + 4 * P * TM;
+    T* c12 = ch + Pb * TM;
+    T* c21 = ch + 2 * Pb * TM;
+    T* c22 = ch + 3 * Pb * TM;
+    T* cin = ch + 4 * Pb * TM;
     const int me = s * TM + c;
 #define XT(j) (FULL ? (((j) == MAXM - 1 && lastseg) ? etop : T(0)) : ((k0 + (j) == nz - 1) ? etop : T(0)))
 #define GW(j) (ADJ ? G[j] : gsc)
@@ -754,7 +757,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
         __syncthreads();
         e_in = cin[me];
         // (stride 0: every lane of every CTA stores the same value)
-        if (a.ecache_mode == 1 && s > 0 && c < w)
+        if (a.ecache_mode == 1 && act && s > 0 && c < w)
             a.ecache[a.ecache_stride ? (long)s * a.ecache_stride + q : (long)s] = e_in;
     }
     // C: pivots (registers) and the affine composite of the forward sweep
@@ -847,19 +850,18 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
 }
 
 // One tile of 32 consecutive modes per CTA: load (16-byte cp.async, all in
-// flight), solve, store.
+// flight), solve, store.  P segments (warps) of the line, Pb = blockDim / 32.
 template <typename T, int MAXM, bool FULL, bool ADJ>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<T> a) {
+__device__ __forceinline__ void zw_kernel_body(const ZArgs<T>& a, const int bx, const int P, const int Pb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TM = 32;
     const int nz = a.nz;
-    const int P = blockDim.x / 32;
     const int m = (nz + P - 1) / P;
     const long nmodes = (long)a.nx * a.ny;
     T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
-    T* ch = tile + (long)P * m * TM;                   // 6 x [P][32] chain states
-    ZwTables<T> tb(ch + 6 * P * TM, nz);
-    const long q0 = (long)blockIdx.x * TM;
+    T* ch = tile + (long)P * m * TM;                   // 6 x [Pb][32] chain states
+    ZwTables<T> tb(ch + 6 * Pb * TM, nz);
+    const long q0 = (long)bx * TM;
     const int w = (int)min((long)TM, nmodes - q0);
     const T* __restrict__ in = a.src ? a.src : a.data;
     tb.fill(a);
@@ -873,7 +875,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
         }
     }
     __syncthreads();
-    zw_solve_tile<T, MAXM, FULL, ADJ>(a, tile, ch, tb, q0, w);
+    zw_solve_tile<T, MAXM, FULL, ADJ>(a, tile, ch, tb, q0, w, P, Pb);
     if (a.bulk) {
         zw_store<T>(a.data, tile, nmodes, q0, w, nz);
     } else {
@@ -882,6 +884,35 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(ZArgs<
             if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[e];
         }
     }
+}
+
+template <typename T, int MAXM, bool FULL, bool ADJ>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(const __grid_constant__ ZArgs<T> a) {
+    zw_kernel_body<T, MAXM, FULL, ADJ>(a, blockIdx.x, blockDim.x / 32, blockDim.x / 32);
+}
+
+// Grouped launch (z stage of many solves): CTA b solves tile work[b].y of
+// item work[b].x with that item's P segments; blockDim = 32 x the largest P.
+template <typename T, int MAXM, bool ADJ>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w_grp(const ZArgs<T>* __restrict__ items,
+                                                                             const int2* __restrict__ work) {
+    __shared__ __align__(16) ZArgs<T> sa;
+    const int2 wk = work[blockIdx.x];
+    {
+        const int* src = reinterpret_cast<const int*>(items + wk.x);
+        int* d = reinterpret_cast<int*>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(ZArgs<T>) / 4); i += blockDim.x) d[i] = src[i];
+    }
+    __syncthreads();
+    zw_kernel_body<T, MAXM, false, ADJ>(sa, wk.y, sa.P, blockDim.x / 32);
+}
+
+// Shared memory of one tile of a line of nz rows in P segments, chain slots
+// for Pb warps.
+template <typename T>
+size_t zsolve_w_smem_pb(int nz, int P, int Pb) {
+    const int m = (nz + P - 1) / P;
+    return ((size_t)P * m * 32 + 6 * (size_t)Pb * 32 + 8 * (size_t)nz) * sizeof(T);
 }
 
 // Persistent variant (16-byte aligned rows only): each CTA walks the tiles
@@ -916,7 +947,7 @@ __global__ void __launch_bounds__(512, 1) k_zsolve_wp(ZArgs<T> a) {
         __syncthreads();
         const long q0 = t * TM;
         const int w = (int)min((long)TM, nmodes - q0);
-        zw_solve_tile<T, MAXM, FULL, ADJ>(a, cur, ch, tb, q0, w);
+        zw_solve_tile<T, MAXM, FULL, ADJ>(a, cur, ch, tb, q0, w, P, P);
         zw_store<T>(a.data, cur, nmodes, q0, w, nz);
         __syncthreads();                               // the buffer is free for the load after next
     }

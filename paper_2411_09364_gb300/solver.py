@@ -16,6 +16,7 @@ from . import _native as N
 
 BC_P, BC_N, BC_D, BC_DF = 0, 1, 2, 3
 FP64, FP32, FP32_REFINE = 0, 1, 2
+SCHED_LEN = 6          # CALES_SCHED_LEN: launch schedule entries
 _DTYPE = {FP64: torch.float64, FP32: torch.float32, FP32_REFINE: torch.float64}
 
 
@@ -201,11 +202,14 @@ class Plan:
         return out
 
     def set_schedule(self, sched):
-        arr = (C.c_int * 4)(*[int(v) for v in sched])
+        """{x budget KB, y tile, z warps, z segment rows, FFT radix order, z variant};
+        shorter lists are padded with 0 (the heuristic)."""
+        vals = [int(v) for v in sched] + [0] * (SCHED_LEN - len(sched))
+        arr = (C.c_int * SCHED_LEN)(*vals[:SCHED_LEN])
         N.check(N.lib().cales_set_schedule(self._h, arr), "cales_set_schedule")
 
     def schedule(self):
-        arr = (C.c_int * 4)()
+        arr = (C.c_int * SCHED_LEN)()
         N.check(N.lib().cales_get_schedule(self._h, arr), "cales_get_schedule")
         return tuple(arr)
 

@@ -41,6 +41,7 @@ def test_batch_matches_single_solves_and_oracle(cuda_device):
     us2 = [torch.empty_like(f) for f in fs]
     batch.solve(fs, us2)
     torch.cuda.synchronize()
+    assert batch.grouped()                 # FP32 + refinement plans: grouped stage launches
     report = []
     for (d, name), plan, f, u, u2 in zip(tags, plans, fs, us, us2):
         ref = plan.poisson(f) if name == "p" else plan.helmholtz(alphas[d], f)
@@ -66,7 +67,7 @@ def test_batch_graph_replay(cuda_device):
     batch.solve(fs, direct)
     us = [torch.full_like(f, float("nan")) for f in fs]
     st = batch.capture(fs, us)
-    assert batch.graph_nodes() > 4 * len(plans)
+    assert batch.grouped() and batch.graph_nodes() <= 30     # one launch per stage and variant
     for _ in range(2):
         batch.launch(st)
         st.synchronize()
@@ -75,6 +76,36 @@ def test_batch_graph_replay(cuda_device):
                 assert float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) <= 1e-13
             else:
                 assert torch.equal(a, b)
+
+
+def test_grouped_and_fork_join_batches_agree(cuda_device):
+    """The grouped stage launches against the fork/join of per-solve launches
+    over streams: the same kernels' arithmetic per solve, so bit for bit
+    except singular Poisson solves (order of the FP64 gauge-sum atomics)."""
+    domains = [(48, 32, 24), (96, 64, 40), (64, 48, 33)]
+    alphas = [1e-4, 1e-3, 1e-4]
+    batch, plans, tags = B.rk3_substep_batch(domains, alphas)
+    fs = _inputs(plans, 4200)
+    ug = [torch.empty_like(f) for f in fs]
+    batch.solve(fs, ug)
+    assert batch.grouped()
+    batch.set_grouped(False)
+    uf = [torch.empty_like(f) for f in fs]
+    batch.solve(fs, uf)
+    torch.cuda.synchronize()
+    assert not batch.grouped()
+    st = batch.capture(fs, [torch.empty_like(f) for f in fs])
+    nodes_fork = batch.graph_nodes()
+    batch.set_grouped(True)
+    batch.capture(fs, [torch.empty_like(f) for f in fs], st)
+    nodes_grouped = batch.graph_nodes()
+    print(f"graph nodes: fork/join {nodes_fork}, grouped {nodes_grouped}")
+    assert nodes_grouped <= 30 < nodes_fork
+    for (d, name), a, b in zip(tags, ug, uf):
+        if name == "p":
+            assert float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) <= 1e-13, (d, name)
+        else:
+            assert torch.equal(a, b), (d, name)
 
 
 def test_autotune_sets_and_caches_a_schedule(cuda_device, tmp_path):
@@ -102,6 +133,7 @@ def test_rk3_substep_16_domains_graph(cuda_device):
           for (d, _), i, p in zip(tags, range(len(plans)), plans)]
     us = [torch.empty_like(f) for f in fs]
     st = batch.capture(fs, us)
+    assert batch.grouped() and batch.graph_nodes() <= 30
     batch.launch(st)
     st.synchronize()
     worst = {}

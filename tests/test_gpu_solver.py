@@ -175,3 +175,24 @@ def test_config2_channel_divergence_fp64_fp32(cuda_device):
     print(f"config2 rel err FP64 {err64:.3e} FP32 {err32:.3e}")
     assert err64 <= TOL[cs.FP64]
     assert err32 <= TOL[cs.FP32]
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("zvariant", [0, 1])
+def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant):
+    """Every FFT radix order (radix 16 first, 5 and 3 first, radix 8 only) and
+    both z kernel variants of the launch schedule solve the same system:
+    lengths with factors 2, 3 and 5 (x 480 = 2 x 240, y 120 = 2 x 60), a
+    Neumann y, in FP64, FP32 and FP32 + refinement."""
+    nx, ny, nz = 480, 120, 48
+    bc = (0, 0, 1, 1, 1, 2)
+    g, plan = pair(nx, ny, nz, bc, beta=1.7)
+    plan.set_schedule([0, 0, 0, 0, order, zvariant])
+    assert plan.schedule()[4:] == (order, zvariant)
+    f = S.gaussian(71 + order, (nz, ny, nx))
+    for alpha in (None, 1e-3):
+        ref = O.solve(f, g, alpha)
+        for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE):
+            plan.set_precision(prec, 2)
+            assert O.rel_l2(solve_gpu(plan, f, alpha), ref) <= TOL[prec], (prec, alpha)
+    assert plan.status() == 0

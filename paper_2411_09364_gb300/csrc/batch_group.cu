@@ -119,22 +119,22 @@ void add_pass(GroupedBatch* G, std::vector<unsigned char>& hb, std::vector<Item>
         }
     };
     add_cols(false);
-    {   // z, one launch per segment bound
+    {   // z, one launch per (segment bound, segment count): every warp of a
+        // CTA owns rows of its line
         std::map<int, std::vector<ZArgs<float>>> by_m;
         std::map<int, std::vector<long>> nb_m;
-        std::map<int, int> pmax;
         for (size_t i = 0; i < n; ++i) {
             ZArgs<float> za = z_args<float>(it[i].P, it[i].P->work, it[i].o);
             z_args_done<float>(it[i].P, za, it[i].o);
-            by_m[za.maxm].push_back(za);
-            nb_m[za.maxm].push_back(cdiv((long)za.nx * za.ny, 32));
-            pmax[za.maxm] = std::max(pmax[za.maxm], za.P);
+            const int key = za.maxm * 64 + za.P;
+            by_m[key].push_back(za);
+            nb_m[key].push_back(cdiv((long)za.nx * za.ny, 32));
         }
         for (auto& kv : by_m) {
-            const int pb = pmax[kv.first];
+            const int pb = kv.first % 64;
             size_t sm = 0;
             for (const auto& za : kv.second) sm = std::max(sm, zsolve_w_smem_pb<float>(za.nz, za.P, pb));
-            add_launch(G, hb, SK_Z, kv.first, kv.second, nb_m[kv.first], sm, 32 * pb);
+            add_launch(G, hb, SK_Z, kv.first / 64, kv.second, nb_m[kv.first], sm, 32 * pb);
         }
     }
     add_cols(true);

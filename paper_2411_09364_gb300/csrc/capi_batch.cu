@@ -202,7 +202,7 @@ int cales_autotune(cales_plan_t P, const char* cache_path, void* stream) {
     // y: tile width
     if (P->ny > 1) {
         double bt = 1e30;
-        const int cand[4] = {8, 16, 32, 0};
+        const int cand[6] = {8, 16, 32, 64, 128, 0};
         for (int c : cand)
             if (trial(1, c, -1, 0, t) && t[1] < bt) { bt = t[1]; best[1] = c; }
     }

@@ -48,6 +48,8 @@ template <typename T>
 cudaError_t launch_cols_grp(const ColArgs<T>* items, const int2* work, int nblocks, int tx, bool inverse, size_t smem,
                             cudaStream_t st) {
     switch (tx) {
+        case 128: return cols_grp_tx<T, 128>(items, work, nblocks, inverse, smem, st);
+        case 64: return cols_grp_tx<T, 64>(items, work, nblocks, inverse, smem, st);
         case 32: return cols_grp_tx<T, 32>(items, work, nblocks, inverse, smem, st);
         case 16: return cols_grp_tx<T, 16>(items, work, nblocks, inverse, smem, st);
         case 8: return cols_grp_tx<T, 8>(items, work, nblocks, inverse, smem, st);

@@ -256,7 +256,7 @@ __device__ __forceinline__ float4 sc4(float g, float4 v) { return make_float4(g 
 // aligned u and f): the centre pair, both y and both z neighbour pairs and
 // f come in one vector load each, the x neighbours of the pair in two 8-byte
 // loads.  A CTA covers whole rows of one z-plane.
-template <bool SING, bool HELM, bool GAUGE, bool LO>
+template <bool SING, bool HELM, bool GAUGE, bool LO, bool FLAT>
 __device__ __forceinline__ void residual_df_body(const ResidFFArgs& a, const int bx, const int k) {
     const int nx = a.nx, ny = a.ny;
     const long plane = (long)nx * ny;
@@ -281,34 +281,44 @@ __device__ __forceinline__ void residual_df_body(const ResidFFArgs& a, const int
     const long offD = kd ? -plane : (pz_ ? (long)(a.nz - 1) * plane : 0);
     const long offU = ku ? plane : (pz_ ? -(long)(a.nz - 1) * plane : 0);
     const float mD = (kd || pz_) ? 1.f : gd, mU = (ku || pz_) ? 1.f : gu;
-    for (int j = j0; j < j1; ++j) {
+    auto pair_at = [&](const int j, const int pi) {
         const long offS = j > 0 ? -(long)nx : (py_ ? (long)(ny - 1) * nx : 0);
         const long offN = j < ny - 1 ? (long)nx : (py_ ? -(long)(ny - 1) * nx : 0);
         const float mS = (j > 0 || py_) ? 1.f : gyl, mN = (j < ny - 1 || py_) ? 1.f : gyh;
         const long rb = kbase + (long)j * nx;
-        const float2* __restrict__ ur = u + rb;
-        for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
-            const int i = 2 * pi;
-            const float2* q = ur + i;
-            const float4 c = ld4(q);
-            float4 s = ld4(q + offS), n = ld4(q + offN), d = ld4(q + offD), up = ld4(q + offU);
-            const int ow = i > 0 ? -1 : (px_ ? nx - 1 : 0);
-            const int oe = i + 2 < nx ? 2 : (px_ ? -i : 1);
-            float2 w = q[ow], e = q[oe];
-            const double2 fv = *reinterpret_cast<const double2*>(a.f + rb + i);
-            if (mS != 1.f) s = sc4(mS, s);
-            if (mN != 1.f) n = sc4(mN, n);
-            if (mD != 1.f) d = sc4(mD, d);
-            if (mU != 1.f) up = sc4(mU, up);
-            if (!px_) {
-                if (i == 0) w = make_float2(gxl * w.x, gxl * w.y);
-                if (i + 2 == nx) e = make_float2(gxh * e.x, gxh * e.y);
-            }
-            const float r0 = resid_point<SING, HELM, GAUGE, LO>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up),
-                                                                fv.x, cx, cy, zc, za, csh, ghi, glo);
-            const float r1 = resid_point<SING, HELM, GAUGE, LO>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up),
-                                                                fv.y, cx, cy, zc, za, csh, ghi, glo);
-            *reinterpret_cast<float2*>(a.r + rb + i) = make_float2(r0, r1);
+        const int i = 2 * pi;
+        const float2* q = u + rb + i;
+        const float4 c = ld4(q);
+        float4 s = ld4(q + offS), n = ld4(q + offN), d = ld4(q + offD), up = ld4(q + offU);
+        const int ow = i > 0 ? -1 : (px_ ? nx - 1 : 0);
+        const int oe = i + 2 < nx ? 2 : (px_ ? -i : 1);
+        float2 w = q[ow], e = q[oe];
+        const double2 fv = *reinterpret_cast<const double2*>(a.f + rb + i);
+        if (mS != 1.f) s = sc4(mS, s);
+        if (mN != 1.f) n = sc4(mN, n);
+        if (mD != 1.f) d = sc4(mD, d);
+        if (mU != 1.f) up = sc4(mU, up);
+        if (!px_) {
+            if (i == 0) w = make_float2(gxl * w.x, gxl * w.y);
+            if (i + 2 == nx) e = make_float2(gxh * e.x, gxh * e.y);
+        }
+        const float r0 = resid_point<SING, HELM, GAUGE, LO>(lo2(c), w, hi2(c), lo2(s), lo2(n), lo2(d), lo2(up),
+                                                            fv.x, cx, cy, zc, za, csh, ghi, glo);
+        const float r1 = resid_point<SING, HELM, GAUGE, LO>(hi2(c), lo2(c), e, hi2(s), hi2(n), hi2(d), hi2(up),
+                                                            fv.y, cx, cy, zc, za, csh, ghi, glo);
+        *reinterpret_cast<float2*>(a.r + rb + i) = make_float2(r0, r1);
+    };
+    if (!FLAT) {
+        for (int j = j0; j < j1; ++j)
+            for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) pair_at(j, pi);
+    } else {
+        // short rows (FLAT): the threads run over (row, pair) together, so
+        // none idles when a row has fewer pairs than the CTA has threads
+        const int tot = (j1 - j0) * npair;
+        const unsigned mag = div_magic((unsigned)npair);
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int jj = (int)fdivu((unsigned)e, mag);
+            pair_at(j0 + jj, e - jj * npair);
         }
     }
     if (GAUGE && a.gacc) {
@@ -327,15 +337,15 @@ __device__ __forceinline__ void residual_df_body(const ResidFFArgs& a, const int
     }
 }
 
-template <bool SING, bool HELM, bool GAUGE, bool LO>
+template <bool SING, bool HELM, bool GAUGE, bool LO, bool FLAT>
 __global__ void __launch_bounds__(256) k_residual_df(const __grid_constant__ ResidFFArgs a) {
-    residual_df_body<SING, HELM, GAUGE, LO>(a, blockIdx.x, blockIdx.y);
+    residual_df_body<SING, HELM, GAUGE, LO, FLAT>(a, blockIdx.x, blockIdx.y);
 }
 
 // Grouped launch over many solves: CTA b takes block work[b].y (row block +
 // plane, row blocks fastest) of item work[b].x.
 template <bool SING, bool HELM, bool GAUGE, bool LO>
-__global__ void __launch_bounds__(256) k_residual_df_grp(const ResidFFArgs* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_residual_df_grp(const ResidFFArgs* __restrict__ items,
                                                          const int2* __restrict__ work) {
     __shared__ __align__(16) ResidFFArgs sa;
     const int2 w = work[blockIdx.x];
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(256) k_residual_df_grp(const ResidFFArgs* __re
     __syncthreads();
     const int nby = (sa.ny + sa.rows_per_cta - 1) / sa.rows_per_cta;
     const int k = w.y / nby;
-    residual_df_body<SING, HELM, GAUGE, LO>(sa, w.y - k * nby, k);
+    residual_df_body<SING, HELM, GAUGE, LO, true>(sa, w.y - k * nby, k);
 }
 
 // Rows per CTA of the double-float residual: about 4096 points, whole rows.
@@ -380,14 +390,14 @@ cudaError_t launch_residual_ff_grp(const ResidFFArgs* items, const int2* work, i
     return cudaGetLastError();
 }
 
-template <bool LO>
+template <bool LO, bool FLAT>
 static void launch_df(const ResidFFArgs& a, dim3 grid, bool sing, bool helm, cudaStream_t st) {
-    if (a.gacc && !helm) k_residual_df<true, false, true, LO><<<grid, 256, 0, st>>>(a);
-    else if (a.gacc) k_residual_df<true, true, true, LO><<<grid, 256, 0, st>>>(a);
-    else if (sing && !helm) k_residual_df<true, false, false, LO><<<grid, 256, 0, st>>>(a);
-    else if (sing) k_residual_df<true, true, false, LO><<<grid, 256, 0, st>>>(a);
-    else if (helm) k_residual_df<false, true, false, LO><<<grid, 256, 0, st>>>(a);
-    else k_residual_df<false, false, false, LO><<<grid, 256, 0, st>>>(a);
+    if (a.gacc && !helm) k_residual_df<true, false, true, LO, FLAT><<<grid, 256, 0, st>>>(a);
+    else if (a.gacc) k_residual_df<true, true, true, LO, FLAT><<<grid, 256, 0, st>>>(a);
+    else if (sing && !helm) k_residual_df<true, false, false, LO, FLAT><<<grid, 256, 0, st>>>(a);
+    else if (sing) k_residual_df<true, true, false, LO, FLAT><<<grid, 256, 0, st>>>(a);
+    else if (helm) k_residual_df<false, true, false, LO, FLAT><<<grid, 256, 0, st>>>(a);
+    else k_residual_df<false, false, false, LO, FLAT><<<grid, 256, 0, st>>>(a);
 }
 
 cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
@@ -400,8 +410,13 @@ cudaError_t launch_residual_ff(const ResidFFArgs& a0, cudaStream_t st) {
     const bool sing = a.gacc != nullptr || a.cshift != nullptr;
     const bool helm = a.c0h != 0.f;
     if (!vec) k_residual_ff<<<grid, 256, 0, st>>>(a);
-    else if (a.lo_zero) launch_df<false>(a, grid, sing, helm, st);
-    else launch_df<true>(a, grid, sing, helm, st);
+    else if (a.nx / 2 >= 256) {
+        if (a.lo_zero) launch_df<false, false>(a, grid, sing, helm, st);
+        else launch_df<true, false>(a, grid, sing, helm, st);
+    } else {
+        if (a.lo_zero) launch_df<false, true>(a, grid, sing, helm, st);
+        else launch_df<true, true>(a, grid, sing, helm, st);
+    }
     return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
         if (launch_cols_static(a, inverse, st, &err)) return err;
     }
     switch (a.tx) {
+        case 128: return launch_cols_v<T, 128, 0, -1>(a, inverse, st);
+        case 64: return launch_cols_v<T, 64, 0, -1>(a, inverse, st);
         case 32: return launch_cols_v<T, 32, 0, -1>(a, inverse, st);
         case 16: return launch_cols_v<T, 16, 0, -1>(a, inverse, st);
         case 8: return launch_cols_v<T, 8, 0, -1>(a, inverse, st);

@@ -322,15 +322,26 @@ template <typename T> bool choose_zt(int nz, int& tm, int& P, int& maxm, int& wa
     return smem(tm) <= 200 * 1024;
 }
 
-// y tiles: the widest tile (<= 32 columns) whose two buffers fit in ~72 KB.
-template <typename T> int choose_tx(int ny, int forced = 0) {
-    const int cands[4] = {32, 16, 8, 4};
-    if (forced == 4 || forced == 8 || forced == 16 || forced == 32)
-        if ((size_t)2 * forced * (ny >= 2 ? ny : 2) * sizeof(T) <= 200 * 1024 && forced * sizeof(T) >= 16) return forced;
+// y tiles: the widest tile (<= 32 columns, 128-byte rows) whose two buffers
+// fit in ~72 KB.  Short FP32 columns (L x 32 < 2048 complex elements, i.e.
+// ny < 128) take up to 128 columns so that the first radix pass keeps most
+// of the 256 threads busy, but no more columns than the row (rounded up to
+// 32); ny = 128 and longer keep 32 (the compile-time-size kernels).
+// ny: real elements of one FFT line (2L); nx: row length (0: unknown).
+template <typename T> int choose_tx(int ny, int forced = 0, int nx = 0) {
+    const int cands[6] = {128, 64, 32, 16, 8, 4};
     const size_t per_col = 2 * (size_t)(ny >= 2 ? ny : 2) * sizeof(T);
-    for (int i = 0; i < 4; ++i)
-        if (per_col * cands[i] <= 72 * 1024 && cands[i] * sizeof(T) <= 128) return cands[i];
-    for (int i = 0; i < 4; ++i)
+    for (int c : cands)
+        if (forced == c && per_col * c <= 200 * 1024 && c * sizeof(T) >= 16) return forced;
+    int widest = 32;
+    if (sizeof(T) == 4) {
+        const long L = ny / 2 > 0 ? ny / 2 : 1;
+        const int rowcap = nx > 0 ? ((nx + 31) / 32) * 32 : 128;
+        while (widest < 128 && L * widest < 2048 && widest * 2 <= rowcap) widest *= 2;
+    }
+    for (int c : cands)
+        if (c <= widest && per_col * c <= 72 * 1024 && (c * sizeof(T) <= 128 || sizeof(T) == 4)) return c;
+    for (int i = 2; i < 6; ++i)
         if (per_col * cands[i] <= 200 * 1024) return cands[i];
     return 0;
 }
@@ -377,7 +388,7 @@ ColArgs<T> col_args(cales_plan_s* P, T* work) {
     ca.data = work;
     ca.nx = P->nx;
     ca.nplanes = P->nz;
-    ca.tx = choose_tx<T>(2 * P->Y.L, P->sched[1]);
+    ca.tx = choose_tx<T>(2 * P->Y.L, P->sched[1], P->nx);
     ca.bulk = (aligned16(work) && ((size_t)P->nx * sizeof(T)) % 16 == 0 && ca.tx * sizeof(T) >= 16) ? 1 : 0;
     ca.status = P->status;
     return ca;

@@ -50,7 +50,13 @@ enum cales_bc {
 enum cales_precision {
     CALES_FP64 = 0,        /* FP64 transforms and tridiagonal sweeps              */
     CALES_FP32 = 1,        /* FP32 throughout (float fields)                     */
-    CALES_FP32_REFINE = 2  /* FP32 solves + FP64 residual and FP64 accumulation   */
+    CALES_FP32_REFINE = 2, /* FP32 solves + FP64 residual and FP64 accumulation   */
+    CALES_FP32_REFINE_FAST = 3 /* as CALES_FP32_REFINE, but only the first sweep
+                                forms the residual in double-float; later sweeps
+                                update it in FP32 from the previous correction
+                                (r <- r - M d): one residual pass per solve fewer
+                                per extra sweep, about ten times the final
+                                error (double fields, 2 FP32 work fields)     */
 };
 
 enum cales_status {
@@ -107,8 +113,10 @@ enum cales_device_status_bits {
 int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6],
                double dx, double dy, const double* dzc, const double* dzf);
 
-/* Select precision and refinement sweeps (0..8; used by CALES_FP32_REFINE).
- * Allocates the FP32 workspace (4 bytes per grid point) when needed. */
+/* Select precision and refinement sweeps (0..8; used by CALES_FP32_REFINE and
+ * CALES_FP32_REFINE_FAST, which with fewer than 2 sweeps runs as
+ * CALES_FP32_REFINE).  Allocates the FP32 workspace (4 bytes per grid point,
+ * 8 for the fast mode) when needed. */
 int cales_set_precision(cales_plan_t plan, int mode, int refine_sweeps);
 
 /*

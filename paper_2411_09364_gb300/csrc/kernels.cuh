@@ -15,6 +15,14 @@ template <typename T> struct RowArgs {
     double shift_scale;
     int bulk;            // rows move with TMA bulk copies (alignment checked on the host)
     int* status;
+    // OUT_FF_ACC_D only: the FP32 correction is also stored to dout (same
+    // rows as the input), and with gacc non-null the dzf-weighted sum of the
+    // updated pairs is added to gacc[0] (plane k = row / ny, weight gw[k])
+    void* dout;
+    double* gacc;
+    const double* gw;
+    int ny;
+    unsigned nymag;
 };
 
 // Output modes of the inverse x kernel.
@@ -23,7 +31,8 @@ enum OutMode {
     OUT_F64 = 1,        // write double
     OUT_FF_INIT = 2,    // write a double-float pair (v, 0) into the 8-byte slot
     OUT_FF_ACC = 3,     // pair += v - shift
-    OUT_FF_FINAL = 4    // double = pair + v - shift
+    OUT_FF_FINAL = 4,   // double = pair + v - shift
+    OUT_FF_ACC_D = 5    // pair += v, v also stored as FP32 (the correction), optional gauge sum
 };
 
 template <typename T> struct ColArgs {
@@ -104,6 +113,19 @@ struct ResidFFArgs {
     int rows_per_cta;    // set by the launcher
 };
 
+// FP32 update of a refinement residual from the last correction d (the fast
+// refinement mode): r <- r - (c0 d + c1 L d) - (acc[0] - acc[2]).
+struct ResidUpdArgs {
+    float* r;            // in/out [nz][ny][nx]
+    const float* d;      // correction [nz][ny][nx]
+    int nx, ny, nz;
+    int bcx, bcy, zlo, zhi;   // KIND_* for x/y, ZBC_* (0 periodic) for z
+    float cx, cy, c0, c1;     // c1/dx^2, c1/dy^2, c0 (0 or 1), c1 (1 or -alpha)
+    const float* za;     // [nz] couplings 1/(dzc dzf), unscaled
+    const float* zc;
+    const double* acc;   // singular problems: acc[0] (current) and acc[2] (in r), else null
+};
+
 // Smagorinsky / van Driest eddy viscosity at the cell centres of a channel.
 template <typename T> struct SgsArgs {
     const T* u;          // x-faces [nz][ny][nx]
@@ -163,6 +185,7 @@ cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_eddy_viscosity(const SgsArgs<T>& a, cudaStream_t st);
 cudaError_t launch_residual_ff(const ResidFFArgs& a, cudaStream_t st);
 int residual_rows_per_cta(int nx, int ny);
+cudaError_t launch_residual_update(const ResidUpdArgs& a, cudaStream_t st);
 
 // Grouped launches: the same stage of many solves in one launch; CTA b runs
 // block work[b].y of item work[b].x (argument blocks in device memory).

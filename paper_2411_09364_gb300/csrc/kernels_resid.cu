@@ -44,6 +44,44 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
     }
 }
 
+// FP32 residual update of the fast refinement mode: r <- r - M d - dshift,
+// M = c0 I + c1 L with the R2 ghosts (per side) and a periodic z wrap.  One
+// plane per blockIdx.y, threads along x over whole rows.
+__global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__ ResidUpdArgs a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int k = blockIdx.y;
+    const long plane = (long)nx * ny;
+    const float zc = a.c1 * a.zc[k], za = a.c1 * a.za[k];
+    const float dshift = a.acc ? (float)(a.acc[0] - a.acc[2]) : 0.f;
+    const float gxl = ghost_lo(a.bcx), gxh = ghost_hi(a.bcx), gyl = ghost_lo(a.bcy), gyh = ghost_hi(a.bcy);
+    const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
+    const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
+    const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P, pz = a.zlo == 0;
+    const long tot = plane;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long)j * nx);
+        const long idx = (long)k * plane + e;
+        const float* d = a.d;
+        const float c = d[idx];
+        const float w = i > 0 ? d[idx - 1] : (px ? d[idx + nx - 1] : gxl * c);
+        const float ea = i < nx - 1 ? d[idx + 1] : (px ? d[idx - (nx - 1)] : gxh * c);
+        const float s = j > 0 ? d[idx - nx] : (py ? d[idx + (long)(ny - 1) * nx] : gyl * c);
+        const float n = j < ny - 1 ? d[idx + nx] : (py ? d[idx - (long)(ny - 1) * nx] : gyh * c);
+        const float dn = k > 0 ? d[idx - plane] : (pz ? d[idx + (long)(nz - 1) * plane] : gd * c);
+        const float up = k < nz - 1 ? d[idx + plane] : (pz ? d[idx - (long)(nz - 1) * plane] : gu * c);
+        const float ld = a.cx * ((ea - c) + (w - c)) + a.cy * ((n - c) + (s - c)) + zc * (up - c) + za * (dn - c);
+        a.r[idx] = a.r[idx] - (a.c0 * c + ld) - dshift;
+    }
+}
+
+cudaError_t launch_residual_update(const ResidUpdArgs& a, cudaStream_t st) {
+    const long plane = (long)a.nx * a.ny;
+    long bx = (plane + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    k_residual_update<<<dim3((unsigned)bx, (unsigned)a.nz), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
     const long N = (long)a.nx * a.ny * a.nz;
     long blocks = (N + 255) / 256;

@@ -18,6 +18,7 @@ static cudaError_t rows_inv_l(const RowArgs<float>& a, int mode, cudaStream_t st
         case OUT_F64: return launch_rows_inverse_v<float, OUT_F64, LS, KIND_P>(a, st);
         case OUT_FF_INIT: return launch_rows_inverse_v<float, OUT_FF_INIT, LS, KIND_P>(a, st);
         case OUT_FF_ACC: return launch_rows_inverse_v<float, OUT_FF_ACC, LS, KIND_P>(a, st);
+        case OUT_FF_ACC_D: return launch_rows_inverse_v<float, OUT_FF_ACC_D, LS, KIND_P>(a, st);
         default: return launch_rows_inverse_v<float, OUT_FF_FINAL, LS, KIND_P>(a, st);
     }
 }
@@ -33,7 +34,7 @@ bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream
 }
 
 bool launch_rows_inverse_static(const RowArgs<float>& a, int mode, cudaStream_t st, cudaError_t* err) {
-    if (!static_fft_enabled() || a.t.kind != KIND_P || mode < OUT_T || mode > OUT_FF_FINAL || !radices_match(a.t, a.t.L))
+    if (!static_fft_enabled() || a.t.kind != KIND_P || mode < OUT_T || mode > OUT_FF_ACC_D || !radices_match(a.t, a.t.L))
         return false;
     switch (a.t.L) {
         case 128: *err = rows_inv_l<128>(a, mode, st); return true;

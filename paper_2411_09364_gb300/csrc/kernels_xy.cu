@@ -58,6 +58,7 @@ template cudaError_t launch_rows_inverse<float, OUT_F64>(const RowArgs<float>&, 
 template cudaError_t launch_rows_inverse<float, OUT_FF_INIT>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_inverse<float, OUT_FF_ACC>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_inverse<float, OUT_FF_FINAL>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_inverse<float, OUT_FF_ACC_D>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_cols<double>(const ColArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_cols<float>(const ColArgs<float>&, bool, cudaStream_t);
 

@@ -378,6 +378,11 @@ RowArgs<T> fwd_row_args(cales_plan_s* P, const void* in, T* work) {
     ra.status = P->status;
     ra.bulk = (aligned16(in) && aligned16(work) && ((size_t)P->nx * sizeof(TIn)) % 16 == 0 &&
                ((size_t)P->nx * sizeof(T)) % 16 == 0) ? 1 : 0;
+    ra.dout = nullptr;
+    ra.gacc = nullptr;
+    ra.gw = P->dzf_d;
+    ra.ny = P->ny;
+    ra.nymag = div_magic((unsigned)P->ny);
     return ra;
 }
 
@@ -451,8 +456,11 @@ RowArgs<T> inv_row_args(cales_plan_s* P, T* work, void* out, const PassOpt& o) {
 }
 
 // One pass of the solver: in (TIn) -> work (T, mode space) -> out (MODE).
+// OUT_FF_ACC_D: the inverse x pass also stores the correction into work
+// (its own input rows) and adds the gauge sum of the updated pairs to gacc.
 template <typename T, typename TIn, int MODE>
-int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st) {
+int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st,
+             double* gacc = nullptr) {
     const RowArgs<T> ra = fwd_row_args<T, TIn>(P, in, work);
     P->prof_begin(st, "x_fwd");
     if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
@@ -484,7 +492,11 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
         P->prof_end(st);
     }
 
-    const RowArgs<T> ri = inv_row_args<T, MODE>(P, work, out, o);
+    RowArgs<T> ri = inv_row_args<T, MODE>(P, work, out, o);
+    if (MODE == OUT_FF_ACC_D) {
+        ri.dout = work;
+        ri.gacc = gacc;
+    }
     P->prof_begin(st, MODE >= OUT_FF_ACC ? "x_inv_acc" : "x_inv");
     if (launch_rows_inverse<T, MODE>(ri, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
@@ -597,6 +609,68 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
     return CALES_OK;
 }
 
+// Fast refinement: the residual is formed in double-float once, after the
+// first FP32 solve; every later sweep updates it in FP32 from the correction
+// of the sweep before, r_{s+1} = r_s - M d_s (the inverse x pass stores d_s
+// beside the pair update), and subtracts the change of the consistency
+// constant (acc[0] - acc[2]) for a singular problem.  The gauge of the
+// solution is measured by the pair update of the last-but-one sweep (acc[1])
+// and removed by the last one.  work: mode space and corrections; res: the
+// residual field.
+static int refine_solve_fast(cales_plan_t P, bool helm, double alpha, const void* f, void* p, PassOpt o,
+                             float* work, float* res, double* acc, cudaStream_t st) {
+    const int ns = P->sweeps;
+    const bool sing = o.singular;
+    if (ns <= 1) return CALES_EINVAL;
+    if (cudaMemsetAsync(acc, 0, 4 * sizeof(double), st) != cudaSuccess) return CALES_ECUDA;
+    o.cacc = sing ? acc : nullptr;
+    int rc = pipeline<float, double, OUT_FF_INIT>(P, f, p, work, o, st);
+    if (rc) return rc;
+    if (sing && cudaMemcpyAsync(acc + 2, acc, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return CALES_ECUDA;
+    const ResidFFArgs ra = resid_args(P, helm, alpha, f, p, res, acc, nullptr, 0, ns);
+    P->prof_begin(st, "residual");
+    if (launch_residual_ff(ra, st) != cudaSuccess) return CALES_ECUDA;
+    P->prof_end(st);
+    ResidUpdArgs ua;
+    ua.r = res;
+    ua.d = work;
+    ua.nx = P->nx; ua.ny = P->ny; ua.nz = P->nz;
+    ua.bcx = P->X.kind; ua.bcy = P->Y.kind; ua.zlo = P->bc[4]; ua.zhi = P->bc[5];
+    const double c1 = helm ? -alpha : 1.0;
+    ua.cx = (float)(c1 / (P->dx * P->dx));
+    ua.cy = (float)(c1 / (P->dy * P->dy));
+    ua.c0 = helm ? 1.f : 0.f;
+    ua.c1 = (float)c1;
+    ua.za = P->za_f;
+    ua.zc = P->zc_f;
+    ua.acc = sing ? acc : nullptr;
+    for (int s = 0; s < ns; ++s) {
+        const bool last = s == ns - 1;
+        if (s > 0) {
+            P->prof_begin(st, "residual_update");
+            if (launch_residual_update(ua, st) != cudaSuccess) return CALES_ECUDA;
+            P->prof_end(st);
+            if (sing && cudaMemcpyAsync(acc + 2, acc, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return CALES_ECUDA;
+        }
+        if (last) {
+            o.shift_acc = sing ? acc + 1 : nullptr;
+            o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
+            rc = pipeline<float, float, OUT_FF_FINAL>(P, res, p, work, o, st);
+        } else {
+            // the gauge of the solution that the last correction updates
+            if (sing && s == ns - 2 && cudaMemsetAsync(acc + 1, 0, sizeof(double), st) != cudaSuccess)
+                return CALES_ECUDA;
+            PassOpt od = o;
+            od.shift_acc = nullptr;
+            rc = pipeline<float, float, OUT_FF_ACC_D>(P, res, p, work, od, st, (sing && s == ns - 2) ? acc + 1 : nullptr);
+        }
+        if (rc) return rc;
+    }
+    return CALES_OK;
+}
+
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream);
 
 int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint, const void* f, void* p,
@@ -619,6 +693,11 @@ static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, c
             if (adjoint) return CALES_EUNSUPPORTED;
             if (f == p || !P->work) return CALES_EINVAL;
             return refine_solve(P, helm, alpha, f, p, o, P->work, P->acc, st);
+        case CALES_FP32_REFINE_FAST:
+            if (adjoint) return CALES_EUNSUPPORTED;
+            if (f == p || !P->work || !P->work2) return CALES_EINVAL;
+            if (P->sweeps <= 1) return refine_solve(P, helm, alpha, f, p, o, P->work, P->acc, st);
+            return refine_solve_fast(P, helm, alpha, f, p, o, P->work, P->work2, P->acc, st);
         default:
             return CALES_EINVAL;
     }
@@ -817,12 +896,17 @@ int cales_plan(cales_plan_t* out, int nx, int ny, int nz, const int bc[6], doubl
 }
 
 int cales_set_precision(cales_plan_t P, int mode, int sweeps) {
-    if (!P || mode < 0 || mode > 2 || sweeps < 0 || sweeps > 8) return CALES_EINVAL;
-    if (mode == CALES_FP32_REFINE && !P->work) {
+    if (!P || mode < 0 || mode > 3 || sweeps < 0 || sweeps > 8) return CALES_EINVAL;
+    const size_t bytes = (size_t)P->nx * P->ny * P->nz * sizeof(float);
+    if ((mode == CALES_FP32_REFINE || mode == CALES_FP32_REFINE_FAST) && !P->work) {
         void* w = nullptr;
-        const size_t bytes = (size_t)P->nx * P->ny * P->nz * sizeof(float);
         if (cudaMalloc(&w, bytes) != cudaSuccess) return CALES_ENOMEM;
         P->work = reinterpret_cast<float*>(w);
+    }
+    if (mode == CALES_FP32_REFINE_FAST && !P->work2) {
+        void* w = nullptr;
+        if (cudaMalloc(&w, bytes) != cudaSuccess) return CALES_ENOMEM;
+        P->work2 = reinterpret_cast<float*>(w);
     }
     P->precision = mode;
     P->sweeps = sweeps;
@@ -891,6 +975,7 @@ void cales_destroy(cales_plan_t P) {
     for (void* z : P->zcache)
         if (z) cudaFree(z);
     if (P->work) cudaFree(P->work);
+    if (P->work2) cudaFree(P->work2);
     for (int i = 0; i < cales_plan_s::PROF_MAX; ++i) {
         if (P->prof[i].a) { cudaEventDestroy(P->prof[i].a); cudaEventDestroy(P->prof[i].b); }
     }

@@ -91,6 +91,7 @@ struct cales_plan_s {
     int sched[NSCHED] = {0, 0, 0, 0, 0, 0};
     int radix_order = 0;         // order the X and Y tables were built with
     float* work = nullptr;
+    float* work2 = nullptr;      // fast refinement: the residual field kept between sweeps
     // Segment-entry pivots of the z sweeps (FP32 and FP64 copies, 16 segment
     // slots per mode) and the (sigma, alpha, P, maxm) they were computed for.
     struct ZCacheKey { int valid = 0, P = 0, maxm = 0; double sigma = 0.0, alpha = 0.0; };

@@ -226,11 +226,71 @@ __device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
     }
 }
 
-// The 8-byte results of a CTA's rows: pair updates load U pairs per thread
-// before computing any (more loads in flight per thread).
+// The 8-byte results of a CTA's rows (row0 .. of row length n): pair updates
+// load U pairs per thread before computing any (more loads in flight per
+// thread).  OUT_FF_ACC_D also stores each correction as FP32 to a.dout and,
+// with a.gacc, adds the dzf-weighted sum of the updated pairs to a.gacc[0]
+// (each thread's elements run in increasing order, so its running sum is
+// weighted and flushed whenever the plane changes).
 template <typename T, int MODE>
-__device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, int tot, ff shift) {
-    if (MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL) {
+__device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, int tot, ff shift, const RowArgs<T>& a,
+                                            long row0, int n) {
+    if (MODE == OUT_FF_ACC_D) {
+        constexpr int U = 4;
+        const int bd = blockDim.x;
+        float2* po = reinterpret_cast<float2*>(outp);
+        float* dout = reinterpret_cast<float*>(a.dout) + row0 * n;
+        const bool gauge = a.gacc != nullptr;
+        const unsigned nm = div_magic((unsigned)n);
+        int kcur = -1;
+        float ghi = 0.f, glo = 0.f;
+        double dacc = 0.0;
+        for (int e0 = threadIdx.x; e0 < tot; e0 += U * bd) {
+            float2 pr[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * bd;
+                if (e < tot) pr[u] = po[e];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * bd;
+                if (e < tot) {
+                    const float v = float(vals[e]);
+                    const ff x = pair_update(pr[u], v, shift, false);
+                    po[e] = make_float2(x.hi, x.lo);
+                    dout[e] = v;
+                    if (gauge) {
+                        const int k = (int)fdivu((unsigned)(row0 + (long)fdivu((unsigned)e, nm)), a.nymag);
+                        if (k != kcur) {
+                            if (kcur >= 0) dacc += ((double)ghi + (double)glo) * a.gw[kcur];
+                            kcur = k;
+                            ghi = 0.f;
+                            glo = 0.f;
+                        }
+                        const ff g = two_sum(ghi, x.hi);
+                        ghi = g.hi;
+                        glo += g.lo + x.lo;
+                    }
+                }
+            }
+        }
+        if (gauge) {
+            if (kcur >= 0) dacc += ((double)ghi + (double)glo) * a.gw[kcur];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
+            __shared__ double red[32];
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            __syncthreads();
+            if (lane == 0) red[wid] = dacc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[w2];
+                atomicAdd(a.gacc, t);
+            }
+        }
+    } else if (MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL) {
         constexpr int U = 4;
         const int bd = blockDim.x;
         const bool has_shift = shift.hi != 0.f || shift.lo != 0.f;     // uniform per CTA
@@ -257,6 +317,7 @@ __device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, 
     }
 }
 
+
 // Inverse along x; the output mode decides how the result is stored.
 template <typename T, int MODE, int LS = 0, int KS = -1>
 __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int bx) {
@@ -275,9 +336,10 @@ __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int
     const int tot = nr * n;
     const int tid = threadIdx.x;
     if (n == 1) {
-        for (int e = tid; e < tot; e += blockDim.x) {
-            if (MODE == OUT_T) reinterpret_cast<T*>(outp)[e] = in[e];
-            else store8<T, MODE>(outp + (long)e * 8, in[e], shift);
+        if (MODE == OUT_T) {
+            for (int e = tid; e < tot; e += blockDim.x) reinterpret_cast<T*>(outp)[e] = in[e];
+        } else {
+            store8_rows<T, MODE>(outp, in, tot, shift, a, row0, n);
         }
         return;
     }
@@ -291,7 +353,7 @@ __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int
     cpx<T>* b1 = reinterpret_cast<cpx<T>*>(smem_raw + lay.b1);
     cpx<T>* tw_s = reinterpret_cast<cpx<T>*>(smem_raw + lay.tw);
     T* x0 = reinterpret_cast<T*>(b0);
-    constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL;
+    constexpr bool LOAD_OUT = MODE == OUT_FF_ACC || MODE == OUT_FF_FINAL || MODE == OUT_FF_ACC_D;
     if (a.bulk) {
         if (tid == 0) {
             if (LOAD_OUT) bulk_prefetch_l2(outp, (uint32_t)(tot * 8));
@@ -336,7 +398,7 @@ __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int
         }
         __syncthreads();
         if (MODE != OUT_T) {
-            store8_rows<T, MODE>(outp, natout, tot, shift);
+            store8_rows<T, MODE>(outp, natout, tot, shift, a, row0, n);
             return;
         }
         ob = natout;
@@ -356,7 +418,7 @@ __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int
         if (kind == KIND_P) fft_lines<T, true, 0, false, false, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
         else fft_lines<T, true, 0, false, true, LS, KS>(b1, b0, t, nr, L, 1, tw_s, nat);
         if (MODE != OUT_T) {
-            store8_rows<T, MODE>(outp, natout, tot, shift);
+            store8_rows<T, MODE>(outp, natout, tot, shift, a, row0, n);
             return;
         }
         ob = natout;
@@ -365,11 +427,13 @@ __device__ __forceinline__ void rows_inverse_body(const RowArgs<T>& a, const int
         ob = reinterpret_cast<T*>(b0);
         for (int e = tid; e < tot; e += blockDim.x) {
             const int r = sdiv<LS ? 2 * LS : 0>(e, t.nmag), s2 = e - r * n;
-            const T v = zr[r * n + pack_index(kind, n, s2)] * pack_sign<T>(kind, s2);
-            if (MODE == OUT_T) ob[e] = v;
-            else store8<T, MODE>(outp + (long)e * 8, v, shift);
+            ob[e] = zr[r * n + pack_index(kind, n, s2)] * pack_sign<T>(kind, s2);
         }
-        if (MODE != OUT_T) return;
+        if (MODE != OUT_T) {
+            __syncthreads();
+            store8_rows<T, MODE>(outp, ob, tot, shift, a, row0, n);
+            return;
+        }
     }
     }
     if (a.bulk) {

@@ -15,9 +15,9 @@ import torch
 from . import _native as N
 
 BC_P, BC_N, BC_D, BC_DF = 0, 1, 2, 3
-FP64, FP32, FP32_REFINE = 0, 1, 2
+FP64, FP32, FP32_REFINE, FP32_REFINE_FAST = 0, 1, 2, 3
 SCHED_LEN = 6          # CALES_SCHED_LEN: launch schedule entries
-_DTYPE = {FP64: torch.float64, FP32: torch.float32, FP32_REFINE: torch.float64}
+_DTYPE = {FP64: torch.float64, FP32: torch.float32, FP32_REFINE: torch.float64, FP32_REFINE_FAST: torch.float64}
 
 
 def cell_spacings(zf):

@@ -18,7 +18,7 @@ same plan constructor on:
   over all 402,653,184 points.
 
 Tolerances (relative L2 over all points): 1e-12 FP64, 1e-5 FP32, 1e-10
-FP32 + refinement; the largest point error is bounded by 10x the same
+FP32 + refinement (both refinement modes); the largest point error is bounded by 10x the same
 fraction of the largest |p|.  The full-size manufactured case has an FP64
 floor of its own: f = L p* is rounded in FP64 with |L p*| up to
 4 |p*| (1/dx^2 + 1/dy^2 + 1/dz_min^2) ~ 3e6 |p*|, and the solve returns
@@ -38,8 +38,8 @@ from paper_2411_09364_gb300 import solver as cs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {cs.FP64: 1e-12, cs.FP32: 1e-5, cs.FP32_REFINE: 1e-10}
-NAMES = {cs.FP64: "FP64", cs.FP32: "FP32", cs.FP32_REFINE: "FP32+refine"}
+TOL = {cs.FP64: 1e-12, cs.FP32: 1e-5, cs.FP32_REFINE: 1e-10, cs.FP32_REFINE_FAST: 1e-10}
+NAMES = {cs.FP64: "FP64", cs.FP32: "FP32", cs.FP32_REFINE: "FP32+refine", cs.FP32_REFINE_FAST: "FP32+fast refine"}
 BC = (0, 0, 1, 1, 1, 1)          # P x, N y (DCT-II), N z
 LX, LY, LZ, BETA = 6.0, 2.0, 2.0, 1.5
 
@@ -80,7 +80,7 @@ def test_bench_xy_kernels_vs_oracle(cuda_device, nz):
     g, plan, zf = duct_pair(nx, ny, nz)
     f = S.remove_mean(S.gaussian(3000, (nz, ny, nx)), np.diff(zf))
     ref = O.solve(f, g)
-    for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE):
+    for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE, cs.FP32_REFINE_FAST):
         plan.set_precision(prec, 2)
         check(gpu_solve(plan, f), ref, prec, f"duct {nx}x{ny}x{nz}")
     assert plan.status() == 0
@@ -97,7 +97,7 @@ def test_bench_z_depth_vs_oracle(cuda_device):
     g, plan, zf = duct_pair(nx, ny, nz)
     f = S.remove_mean(S.gaussian(3001, (nz, ny, nx)), np.diff(zf))
     ref = O.solve_refined(f, g)
-    for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE):
+    for prec in (cs.FP64, cs.FP32, cs.FP32_REFINE, cs.FP32_REFINE_FAST):
         plan.set_precision(prec, 2)
         for rep in range(2):                 # first solve fills the pivot cache, second reads it
             check(gpu_solve(plan, f), ref, prec, f"duct {nx}x{ny}x{nz} (solve {rep})")
@@ -120,7 +120,7 @@ def test_bench_workload_full_size_manufactured(cuda_device):
     f_dev = torch.from_numpy(f).cuda()
     del f
     p_dev = torch.empty_like(f_dev)
-    for prec in (cs.FP32_REFINE, cs.FP64, cs.FP32):
+    for prec in (cs.FP32_REFINE, cs.FP32_REFINE_FAST, cs.FP64, cs.FP32):
         plan.set_precision(prec, 2)
         if prec == cs.FP32:
             f32 = f_dev.float()

@@ -196,3 +196,33 @@ def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant):
             plan.set_precision(prec, 2)
             assert O.rel_l2(solve_gpu(plan, f, alpha), ref) <= TOL[prec], (prec, alpha)
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0, 1, 1), (0, 0, 1, 1, 1, 1), (1, 1, 2, 2, 3, 3), (1, 2, 0, 0, 2, 1),
+                                (3, 3, 2, 1, 1, 3), (0, 0, 0, 0, 0, 0)])
+@pytest.mark.parametrize("alpha", [None, 1e-3])
+@pytest.mark.parametrize("sweeps", [2, 3])
+def test_fast_refinement_against_oracle(cuda_device, bc, alpha, sweeps):
+    """FP32 solves with one double-float residual and FP32 residual updates
+    for the later sweeps: every z kind (periodic included, with its wrap
+    distance), mixed and node-centred x/y kinds, Poisson and Helmholtz, two
+    and three sweeps, within the refinement tolerance of the oracle."""
+    nx = 95 if bc[0] == 3 else 96
+    ny, nz = 48, 40
+    if bc[4] == 0:
+        zf = S.tanh_faces(nz, 1.6, 2.0)
+        odzc, odzf = O.cell_spacings(zf)
+        gdzc, gdzf = cs.cell_spacings(zf)
+        odzc = np.array(odzc)
+        gdzc = np.array(gdzc)
+        odzc[0] = odzc[-1] = gdzc[0] = gdzc[-1] = 0.5 * (gdzf[0] + gdzf[-1])
+        g = O.Grid(nx, ny, nz, 2 * math.pi / nx, math.pi / ny, odzc, odzf, bc)
+        plan = cs.Plan(nx, ny, nz, bc, 2 * math.pi / nx, math.pi / ny, gdzc, gdzf)
+    else:
+        g, plan = pair(nx, ny, nz, bc, beta=1.8)
+    plan.set_precision(cs.FP32_REFINE_FAST, sweeps)
+    f = S.gaussian(81 + sweeps, (nz, ny, nx))
+    rel = O.rel_l2(solve_gpu(plan, f, alpha), O.solve(f, g, alpha))
+    print(f"fast refinement bc {bc} alpha {alpha} sweeps {sweeps}: rel {rel:.3e}")
+    assert rel <= TOL[cs.FP32_REFINE], rel
+    assert plan.status() == 0

@@ -45,9 +45,12 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
 }
 
 // FP32 residual update of the fast refinement mode: r <- r - M d - dshift,
-// M = c0 I + c1 L with the R2 ghosts (per side) and a periodic z wrap.  One
-// plane per blockIdx.y, threads along x over whole rows.
-__global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__ ResidUpdArgs a) {
+// M = c0 I + c1 L with the R2 ghosts (per side) and a periodic z wrap.  A CTA
+// covers whole rows of one plane (blockIdx.y); each thread takes VW
+// consecutive points of a row (VW = 4 with 16-byte vector loads when the
+// rows allow it, else 1), the threads running over (row, group) together.
+template <int VW>
+__global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__ ResidUpdArgs a, const int rows) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int k = blockIdx.y;
     const long plane = (long)nx * ny;
@@ -57,28 +60,57 @@ __global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__
     const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
     const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
     const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P, pz = a.zlo == 0;
-    const long tot = plane;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nx), i = (int)(e - (long)j * nx);
-        const long idx = (long)k * plane + e;
-        const float* d = a.d;
-        const float c = d[idx];
-        const float w = i > 0 ? d[idx - 1] : (px ? d[idx + nx - 1] : gxl * c);
-        const float ea = i < nx - 1 ? d[idx + 1] : (px ? d[idx - (nx - 1)] : gxh * c);
-        const float s = j > 0 ? d[idx - nx] : (py ? d[idx + (long)(ny - 1) * nx] : gyl * c);
-        const float n = j < ny - 1 ? d[idx + nx] : (py ? d[idx - (long)(ny - 1) * nx] : gyh * c);
-        const float dn = k > 0 ? d[idx - plane] : (pz ? d[idx + (long)(nz - 1) * plane] : gd * c);
-        const float up = k < nz - 1 ? d[idx + plane] : (pz ? d[idx - (long)(nz - 1) * plane] : gu * c);
-        const float ld = a.cx * ((ea - c) + (w - c)) + a.cy * ((n - c) + (s - c)) + zc * (up - c) + za * (dn - c);
-        a.r[idx] = a.r[idx] - (a.c0 * c + ld) - dshift;
+    const long offD = k > 0 ? -plane : (pz ? (long)(nz - 1) * plane : 0);
+    const long offU = k < nz - 1 ? plane : (pz ? -(long)(nz - 1) * plane : 0);
+    const float mD = (k > 0 || pz) ? 1.f : gd, mU = (k < nz - 1 || pz) ? 1.f : gu;
+    const int j0 = blockIdx.x * rows, j1 = min(j0 + rows, ny);
+    const int ng = nx / VW;
+    const unsigned gmag = div_magic((unsigned)ng);
+    const int tot = (j1 - j0) * ng;
+    const float* __restrict__ d = a.d;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int jj = (int)fdivu((unsigned)t, gmag);
+        const int j = j0 + jj, i = (t - jj * ng) * VW;
+        const long rb = (long)k * plane + (long)j * nx;
+        const long offS = j > 0 ? -(long)nx : (py ? (long)(ny - 1) * nx : 0);
+        const long offN = j < ny - 1 ? (long)nx : (py ? -(long)(ny - 1) * nx : 0);
+        const float mS = (j > 0 || py) ? 1.f : gyl, mN = (j < ny - 1 || py) ? 1.f : gyh;
+        const float* q = d + rb + i;
+        float c[VW], s[VW], n[VW], dn[VW], up[VW], r[VW];
+        if (VW == 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(q), s4 = *reinterpret_cast<const float4*>(q + offS);
+            const float4 n4 = *reinterpret_cast<const float4*>(q + offN), d4 = *reinterpret_cast<const float4*>(q + offD);
+            const float4 u4 = *reinterpret_cast<const float4*>(q + offU);
+            const float4 r4 = *reinterpret_cast<const float4*>(a.r + rb + i);
+            c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+            s[0] = s4.x; s[1] = s4.y; s[2] = s4.z; s[3] = s4.w;
+            n[0] = n4.x; n[1] = n4.y; n[2] = n4.z; n[3] = n4.w;
+            dn[0] = d4.x; dn[1] = d4.y; dn[2] = d4.z; dn[3] = d4.w;
+            up[0] = u4.x; up[1] = u4.y; up[2] = u4.z; up[3] = u4.w;
+            r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+        } else {
+            c[0] = q[0]; s[0] = q[offS]; n[0] = q[offN]; dn[0] = q[offD]; up[0] = q[offU]; r[0] = a.r[rb + i];
+        }
+        const float w = i > 0 ? q[-1] : (px ? q[nx - 1] : gxl * c[0]);
+        const float e = i + VW < nx ? q[VW] : (px ? q[VW - nx] : gxh * c[VW - 1]);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const float xl = v > 0 ? c[v - 1] : w, xr = v < VW - 1 ? c[v + 1] : e;
+            const float ld = a.cx * ((xr - c[v]) + (xl - c[v])) + a.cy * ((mN * n[v] - c[v]) + (mS * s[v] - c[v])) +
+                             zc * (mU * up[v] - c[v]) + za * (mD * dn[v] - c[v]);
+            r[v] = r[v] - (a.c0 * c[v] + ld) - dshift;
+        }
+        if (VW == 4) *reinterpret_cast<float4*>(a.r + rb + i) = make_float4(r[0], r[1], r[2], r[3]);
+        else a.r[rb + i] = r[0];
     }
 }
 
 cudaError_t launch_residual_update(const ResidUpdArgs& a, cudaStream_t st) {
-    const long plane = (long)a.nx * a.ny;
-    long bx = (plane + 255) / 256;
-    if (bx > 4096) bx = 4096;
-    k_residual_update<<<dim3((unsigned)bx, (unsigned)a.nz), 256, 0, st>>>(a);
+    const int rows = residual_rows_per_cta(a.nx, a.ny);
+    const dim3 grid((unsigned)((a.ny + rows - 1) / rows), (unsigned)a.nz);
+    const bool vec = a.nx % 4 == 0 && ((uintptr_t)a.r % 16) == 0 && ((uintptr_t)a.d % 16) == 0;
+    if (vec) k_residual_update<4><<<grid, 256, 0, st>>>(a, rows);
+    else k_residual_update<1><<<grid, 256, 0, st>>>(a, rows);
     return cudaGetLastError();
 }
 

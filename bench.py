@@ -4,8 +4,11 @@ Workload: duct Poisson problem 1536 x 512 x 512 (periodic x with Lx = 6,
 Neumann y walls with Ly = 2 -> DCT-II, Neumann z walls with Lz = 2 stretched
 by tanh(beta = 1.5)); seeded Gaussian right-hand side with its dzf-weighted
 mean removed.  One step = one Poisson solve in FP32 with double-float
-refinement (the default 2 sweeps) of a resident 3.2 GB FP64 right-hand side
-into a resident FP64 solution; the plain FP64 GPU solve is timed beside it.
+refinement (the default 2 sweeps; by default the fast mode, whose second
+residual is updated in FP32 from the first correction, ``--mode exact`` for
+double-float residuals in every sweep) of a resident 3.2 GB FP64 right-hand
+side into a resident FP64 solution; the other refinement mode and the plain
+FP64 GPU solve are timed beside it, each with its error against the FP64 solve.
 
 Prints one JSON line (rank 0).  Besides the headline it carries the FP64 CPU
 oracle timed on a bounded sample of the workload (the 1536 x 512 cross-section
@@ -40,16 +43,41 @@ WORKLOAD = dict(name="duct_poisson_1536x512x512", nx=1536, ny=512, nz=512, bc=(0
 # kernels) on a thin stretched z; its oracle solution also pins the GPU error
 SAMPLE = dict(nx=1536, ny=512, nz=16)
 METRIC = "Gpoints/s per Poisson solve (FP32 + double-float refinement, rel err <= 1e-10 vs FP64)"
+MODE_TEXT = {
+    "fast": "FP32 solves + {s} refinement sweeps: first residual in double-float, later ones updated in FP32 "
+            "from the correction (CALES_FP32_REFINE_FAST)",
+    "exact": "FP32 solves + {s} refinement sweeps, every residual in double-float (CALES_FP32_REFINE)",
+}
 UNIT = "Gpoints/s"
 # algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
+# algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
 KERNEL_BYTES_PER_POINT = {
-    "x_fwd": 12.0,       # read f (FP64 8 B) or r (FP32 4 B, sweeps: see below), write 4 B
-    "x_fwd_sweep": 8.0,
+    "x_fwd": 12.0,            # read f (FP64 8 B), write 4 B
+    "x_fwd_sweep": 8.0,       # read r 4 B, write 4 B
     "y_fwd": 8.0, "y_inv": 8.0, "z_solve": 8.0,
-    "x_inv": 12.0,       # read 4 B, write the (hi, lo) pair 8 B
-    "x_inv_acc": 20.0,   # read 4 B + pair 8 B, write 8 B
-    "residual": 20.0,    # read f 8 B + pair 8 B, write r 4 B
+    "x_inv": 12.0,            # read 4 B, write the (hi, lo) pair 8 B
+    "x_inv_acc": 20.0,        # read 4 B + pair 8 B, write 8 B (pair update / final FP64)
+    "x_inv_acc_d": 24.0,      # the same, and the FP32 correction written (4 B): fast mode
+    "residual": 20.0,         # read f 8 B + pair 8 B, write r 4 B
+    "residual_update": 12.0,  # read r 4 B + correction 4 B, write r 4 B: fast mode
 }
+
+
+def kernel_keys(prof):
+    """Launch names of one profile, told apart by position: a forward x pass
+    after a residual reads the FP32 residual; a pair update followed by a
+    residual update also writes the correction."""
+    keys = []
+    for i, (name, _) in enumerate(prof):
+        prev = prof[i - 1][0] if i > 0 else None
+        nxt = prof[i + 1][0] if i + 1 < len(prof) else None
+        if name == "x_fwd" and prev in ("residual", "residual_update"):
+            keys.append("x_fwd_sweep")
+        elif name == "x_inv_acc" and nxt == "residual_update":
+            keys.append("x_inv_acc_d")
+        else:
+            keys.append(name)
+    return keys
 
 
 def peaks():
@@ -506,6 +534,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cales", choices=["cales", "reference"])
     ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--mode", default="fast", choices=["fast", "exact"],
+                    help="refinement mode of the headline: fast = first residual double-float, later ones "
+                         "updated in FP32; exact = every residual double-float")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the timings of the other workloads")
@@ -544,7 +575,9 @@ def main():
     npts = nx * ny * nz
     zf = S.tanh_faces(nz, w["beta"], w["lz"])
     dzc, dzf = cs.cell_spacings(zf)
-    plan = cs.Plan(nx, ny, nz, w["bc"], w["lx"] / nx, w["ly"] / ny, dzc, dzf, cs.FP32_REFINE, args.sweeps)
+    head_mode = cs.FP32_REFINE_FAST if args.mode == "fast" else cs.FP32_REFINE
+    other_mode = cs.FP32_REFINE if args.mode == "fast" else cs.FP32_REFINE_FAST
+    plan = cs.Plan(nx, ny, nz, w["bc"], w["lx"] / nx, w["ly"] / ny, dzc, dzf, head_mode, args.sweeps)
     f_host = torch.from_numpy(make_rhs(nx, ny, nz, zf, w["seed"] + rank))
     f = f_host.to(dev)
     p = torch.empty_like(f)
@@ -582,10 +615,7 @@ def main():
 
     # --- per-kernel breakdown and roofline of the dominant kernel ------------
     tot, cnt = {}, {}
-    prev = None
-    for name, t in prof:
-        key = "x_fwd_sweep" if (name == "x_fwd" and prev == "residual") else name
-        prev = name
+    for key, (name, t) in zip(kernel_keys(prof), prof):
         tot[key] = tot.get(key, 0.0) + t
         cnt[key] = cnt.get(key, 0) + 1
     launches_per_step = len(prof) / args.steps if prof else 0
@@ -622,8 +652,8 @@ def main():
     ms64 = max_over_ranks(ev0.elapsed_time(ev1) / args.fp64_steps)
     rel = float(torch.linalg.vector_norm(p_ref - p64) / torch.linalg.vector_norm(p64))
 
-    # --- the fast refinement mode (later residuals updated in FP32) ----------
-    plan.set_precision(cs.FP32_REFINE_FAST, args.sweeps)
+    # --- the other refinement mode beside it ---------------------------------
+    plan.set_precision(other_mode, args.sweeps)
     pf = torch.empty_like(f)
     for _ in range(args.warmup):
         plan.poisson(f, pf)
@@ -642,7 +672,7 @@ def main():
         per_kernel_fast[name] = per_kernel_fast.get(name, 0.0) + t / args.steps
     rel_fast = float(torch.linalg.vector_norm(pf - p64) / torch.linalg.vector_norm(p64))
     del pf
-    plan.set_precision(cs.FP32_REFINE, args.sweeps)
+    plan.set_precision(head_mode, args.sweeps)
 
     # --- end to end through the C ABI with host buffers ----------------------
     # Every step copies its right-hand side from pinned host memory, solves and
@@ -701,14 +731,14 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "nx": nx, "ny": ny, "nz": nz, "bc": "P x, N y (DCT-II), N z tanh",
-                   "precision": f"FP32 solves + {args.sweeps} double-float refinement sweeps",
+                   "precision": MODE_TEXT[args.mode].format(s=args.sweeps),
                    "l2": f"inputs larger than L2 (f and p {npts * 8 / 1e9:.1f} GB each), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "fp64": {"value": npts * world / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64, "unit": UNIT},
-        "fp32_refine_fast": {"value": npts * world / (ms_fast * 1e-3) / 1e9, "ms_per_step": ms_fast, "unit": UNIT,
-                             "rel_err_vs_fp64_gpu": rel_fast, "per_kernel_ms_per_step": per_kernel_fast,
-                             "mode": f"FP32 solves, first residual double-float, {args.sweeps - 1} later residual(s) "
-                                     f"updated in FP32 from the correction"},
+        ("fp32_refine_exact_residuals" if args.mode == "fast" else "fp32_refine_fast"): {
+            "value": npts * world / (ms_fast * 1e-3) / 1e9, "ms_per_step": ms_fast, "unit": UNIT,
+            "rel_err_vs_fp64_gpu": rel_fast, "per_kernel_ms_per_step": per_kernel_fast,
+            "mode": MODE_TEXT["exact" if args.mode == "fast" else "fast"].format(s=args.sweeps)},
         "rel_err_refine_vs_fp64_gpu": rel,
         "device_status": status,
         "e2e": {"value": npts * world / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,

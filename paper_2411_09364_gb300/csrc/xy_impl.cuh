@@ -229,54 +229,48 @@ __device__ __forceinline__ void store8(unsigned char* slot, T v, ff shift) {
 // The 8-byte results of a CTA's rows (row0 .. of row length n): pair updates
 // load U pairs per thread before computing any (more loads in flight per
 // thread).  OUT_FF_ACC_D also stores each correction as FP32 to a.dout and,
-// with a.gacc, adds the dzf-weighted sum of the updated pairs to a.gacc[0]
-// (each thread's elements run in increasing order, so its running sum is
-// weighted and flushed whenever the plane changes).
+// with a.gacc, adds the dzf-weighted sum of the updated pairs to a.gacc[0].
 template <typename T, int MODE>
 __device__ __forceinline__ void store8_rows(unsigned char* outp, const T* vals, int tot, ff shift, const RowArgs<T>& a,
                                             long row0, int n) {
     if (MODE == OUT_FF_ACC_D) {
+        // row by row, so the gauge sum of a row takes its plane's weight once
         constexpr int U = 4;
         const int bd = blockDim.x;
         float2* po = reinterpret_cast<float2*>(outp);
         float* dout = reinterpret_cast<float*>(a.dout) + row0 * n;
         const bool gauge = a.gacc != nullptr;
-        const unsigned nm = div_magic((unsigned)n);
-        int kcur = -1;
-        float ghi = 0.f, glo = 0.f;
+        const int nrow = tot / n;
         double dacc = 0.0;
-        for (int e0 = threadIdx.x; e0 < tot; e0 += U * bd) {
-            float2 pr[U];
+        for (int r = 0; r < nrow; ++r) {
+            float ghi = 0.f, glo = 0.f;
+            const int rb = r * n;
+            for (int s0 = threadIdx.x; s0 < n; s0 += U * bd) {
+                float2 pr[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * bd;
-                if (e < tot) pr[u] = po[e];
-            }
+                for (int u = 0; u < U; ++u) {
+                    const int sx = s0 + u * bd;
+                    if (sx < n) pr[u] = po[rb + sx];
+                }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * bd;
-                if (e < tot) {
-                    const float v = float(vals[e]);
-                    const ff x = pair_update(pr[u], v, shift, false);
-                    po[e] = make_float2(x.hi, x.lo);
-                    dout[e] = v;
-                    if (gauge) {
-                        const int k = (int)fdivu((unsigned)(row0 + (long)fdivu((unsigned)e, nm)), a.nymag);
-                        if (k != kcur) {
-                            if (kcur >= 0) dacc += ((double)ghi + (double)glo) * a.gw[kcur];
-                            kcur = k;
-                            ghi = 0.f;
-                            glo = 0.f;
+                for (int u = 0; u < U; ++u) {
+                    const int sx = s0 + u * bd;
+                    if (sx < n) {
+                        const float v = float(vals[rb + sx]);
+                        const ff x = pair_update(pr[u], v, shift, false);
+                        po[rb + sx] = make_float2(x.hi, x.lo);
+                        dout[rb + sx] = v;
+                        if (gauge) {
+                            const ff g = two_sum(ghi, x.hi);
+                            ghi = g.hi;
+                            glo += g.lo + x.lo;
                         }
-                        const ff g = two_sum(ghi, x.hi);
-                        ghi = g.hi;
-                        glo += g.lo + x.lo;
                     }
                 }
             }
+            if (gauge) dacc += ((double)ghi + (double)glo) * a.gw[(int)fdivu((unsigned)(row0 + r), a.nymag)];
         }
         if (gauge) {
-            if (kcur >= 0) dacc += ((double)ghi + (double)glo) * a.gw[kcur];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
             __shared__ double red[32];

@@ -77,6 +77,11 @@ template <typename T> struct ZArgs {
     long ecache_stride;  // nmodes; 0 when every line has the same pivots (line solves)
     int persist;         // warp-per-segment kernel: 0 = one tile per CTA; else the persistent
                          // double-buffered variant where it applies
+    // singular mode 0: shift_acc[0] * shift_scale subtracted from the whole
+    // line after the gauge (a constant of the solution in physical space; the
+    // last refinement sweep removes the measured mean of its iterate this way)
+    const double* shift_acc;
+    double shift_scale;
 };
 
 // FP64 residual r = f - (c0 u + c1 L u) of the 7-point staggered Laplacian.

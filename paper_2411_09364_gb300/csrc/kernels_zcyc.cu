@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
         }
         sum = 0.0;
         for (int k = 0; k < nz; ++k) sum += a.dzf[k] * double(x[k * nm]);
-        const T mean = T(sum / sw);
+        // gauge, and the caller's constant shift of the solution
+        const T mean = T(sum / sw + (a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0));
         for (int k = 0; k < nz; ++k) x[k * nm] -= mean;
         return;
     }

@@ -432,6 +432,11 @@ ZArgs<T> z_args(cales_plan_s* P, T* work, const PassOpt& o) {
     }
     za.ecache_stride = (long)P->nx * P->ny;
     za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
+    // the gauge shift of the last refinement sweep is applied to the mode
+    // (0, 0) line here: a constant in mode space (0, 0) is the same constant
+    // at every point after the unnormalised inverse transforms
+    za.shift_acc = o.shift_acc;
+    za.shift_scale = o.shift_scale;
     return za;
 }
 
@@ -450,8 +455,8 @@ RowArgs<T> inv_row_args(cales_plan_s* P, T* work, void* out, const PassOpt& o) {
     ri.out = out;
     ri.bulk = (aligned16(work) && aligned16(out) && ((size_t)P->nx * sizeof(T)) % 16 == 0 &&
                ((size_t)P->nx * 8) % 16 == 0) ? 1 : 0;
-    ri.shift_acc = o.shift_acc;
-    ri.shift_scale = o.shift_scale;
+    ri.shift_acc = nullptr;          // applied by the z solve (z_args)
+    ri.shift_scale = 0.0;
     return ri;
 }
 
@@ -747,6 +752,8 @@ static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t 
     za.ecache_mode = 0;
     za.ecache_stride = 0;
     za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
+    za.shift_acc = nullptr;
+    za.shift_scale = 0.0;
     const int zi = sizeof(T) == 8 ? 1 : 0;
     cales_plan_s::ZCacheKey& lk = P->lkey[zi];
     if (za.warp_mode && za.P <= 16 && P->lcache[zi]) {

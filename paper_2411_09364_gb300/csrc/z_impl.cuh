@@ -80,7 +80,7 @@ template <typename T> struct Piv {
 template <typename T>
 __device__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T* r0, const T* sA, const T* sC, const T* sG,
                             const T* sO, const double* dzf, int nz, T base, bool singular, double* cacc,
-                            double cacc_scale, int sk) {
+                            double cacc_scale, int sk, double shift = 0.0) {
     // coefficient tables may be skewed by one slot per segment of sk rows
 #define SKI(k) ((sk) > 0 ? (k) + (k) / (sk) : (k))
     double gmean = 0.0;
@@ -112,7 +112,7 @@ __device__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T
     if (singular) {
         double s = 0.0, sw = 0.0;
         for (int k = 0; k < nz; ++k) { s += dzf[k] * double(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride]); sw += dzf[k]; }
-        const double mm = s / sw;
+        const double mm = s / sw + shift;      // gauge, and the caller's constant shift
         for (int k = 0; k < nz; ++k) tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] = T(double(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride]) - mm);
     }
     for (int k = 0; k < nz; ++k) tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] *= sO[SKI(k)];
@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(256) k_zsolve(ZArgs<T> a) {
     __syncthreads();
     if (sing_tile && tid == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0);
+        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0,
+                       a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
             if (!isfinite(tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * TM])) {
                 if (a.status) atomicOr(a.status, ST_NONFINITE);
@@ -551,7 +552,8 @@ __global__ void __launch_bounds__(256) k_zsolve_reg(ZArgs<T> a) {
     __syncthreads();
     if (sing_tile && tid == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, m);
+        serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, m,
+                       a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
             if (!isfinite(tile[(k / m) * segs + (k - (k / m) * m) * TM])) {
                 if (a.status) atomicOr(a.status, ST_NONFINITE);
@@ -783,11 +785,17 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     c12[me] = be;
     __syncthreads();
     if (s == 0) {
+        // chain of the segments' affine maps; the coefficients of four
+        // segments are loaded together ahead of their dependent steps
         T y = T(0);
-        for (int t = 0; t < P; ++t) {
-            const int i = t * TM + c;
-            cin[i] = y;
-            y = c11[i] * y + c12[i];
+        for (int t0 = 0; t0 < P; t0 += 4) {
+            T ka[4], kb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (t0 + u < P) { ka[u] = c11[(t0 + u) * TM + c]; kb[u] = c12[(t0 + u) * TM + c]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (t0 + u < P) { cin[(t0 + u) * TM + c] = y; y = ka[u] * y + kb[u]; }
         }
     }
     __syncthreads();
@@ -810,10 +818,14 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     __syncthreads();
     if (s == 0) {
         T x = T(0);
-        for (int t = P - 1; t >= 0; --t) {
-            const int i = t * TM + c;
-            cin[i] = x;
-            x = c21[i] + c22[i] * x;
+        for (int t0 = P - 1; t0 >= 0; t0 -= 4) {
+            T kq[4], kr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (t0 - u >= 0) { kq[u] = c21[(t0 - u) * TM + c]; kr[u] = c22[(t0 - u) * TM + c]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (t0 - u >= 0) { cin[(t0 - u) * TM + c] = x; x = kq[u] + kr[u] * x; }
         }
     }
     __syncthreads();
@@ -839,7 +851,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     if (sing_tile && tid == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
         serial_line<T>(tile, TM, nz, 0, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf, nz, base0, true, a.cacc,
-                       a.cacc_scale, 0);
+                       a.cacc_scale, 0, a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
             if (!isfinite(tile[k * TM])) {
                 if (a.status) atomicOr(a.status, ST_NONFINITE);

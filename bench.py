@@ -392,24 +392,26 @@ def run_configs(args):
                   "min_traffic_roofline_frac": (fi.numel() * 2 * fi.element_size() / (ms * 1e-3) / 1e9) / peaks()[0]})
     if want("rk3_substep"):
         # 16 channel domains x {u, v, w Helmholtz, p Poisson}, FP32 + refinement, one CUDA graph
+        # (--no-autotune keeps the default schedules; --warmup / --steps graph replays)
         alphas = [1e-4 if d % 2 == 0 else 1e-3 for d in range(len(S.BATCH_DOMAINS))]
-        batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas)
+        batch, plans, tags = B.rk3_substep_batch(S.BATCH_DOMAINS, alphas, autotune=not args.no_autotune)
         fs = [torch.from_numpy(S.gaussian(4000 + i, pl.shape)).to(dev) for i, pl in enumerate(plans)]
         us = [torch.empty_like(x) for x in fs]
         st = batch.capture(fs, us)
-        for _ in range(3):
+        for _ in range(args.warmup):
             batch.launch(st)
         st.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
-        for _ in range(10):
+        for _ in range(args.steps):
             batch.launch(st)
         b.record(st)
         st.synchronize()
-        ms = a.elapsed_time(b) / 10
+        ms = a.elapsed_time(b) / args.steps
         pts = sum(pl.numel for pl in plans)
         emit({"workload": "rk3_substep_16_channel_domains", "mode": "fp32_refine", "ms": ms,
-              "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes()})
+              "gpoint_solves_per_s": pts / ms / 1e6, "solves": len(plans), "graph_nodes": batch.graph_nodes(),
+              "grouped": batch.grouped(), "autotuned": not args.no_autotune})
     if want("z_line_helmholtz"):
         # wall-normal implicit line solves (Eq. 21) on the bench grid, Dirichlet walls
         w = wl
@@ -544,6 +546,7 @@ def main():
     ap.add_argument("--shape", default=None, help="NX,NY,NZ: the duct at another size (profiling case)")
     ap.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each)")
     ap.add_argument("--only", default=None, help="with --configs: only the workloads whose name contains this")
+    ap.add_argument("--no-autotune", action="store_true", help="with --configs: default schedules for the batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

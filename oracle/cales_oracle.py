@@ -436,7 +436,8 @@ def solve_z_lines(f: np.ndarray, g: Grid, alpha: float) -> np.ndarray:
     boundary kinds play no part."""
     sub, diag, sup = z_operator(g)
     rhs = np.asarray(f, dtype=np.float64).reshape(g.nz, -1)
-    u = thomas(-alpha * sub, 1.0 - alpha * diag, -alpha * sup, rhs)
+    line = cyclic_solve if g.bc[4] == BC_P else thomas          # periodic z: cyclic line systems
+    u = line(-alpha * sub, 1.0 - alpha * diag, -alpha * sup, rhs)
     return np.ascontiguousarray(u.reshape(g.nz, g.ny, g.nx))
 
 
@@ -445,8 +446,7 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     transposed and applied in reverse order (an independent route to S^T w).
     """
     _check_supported(g)
-    if g.bc[4] == BC_P:
-        raise ValueError("the transposed solve takes non-periodic z")
+    per = g.bc[4] == BC_P
     w = np.asarray(w, dtype=np.float64)
     nx, ny, nz = g.nx, g.ny, g.nz
     sing = is_singular(g, alpha)
@@ -457,14 +457,18 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
     a = _apply_along(inv_matrix(dir_kind(g.bc[2], g.bc[3]), ny).T, a, 1)
     sub, diag, sup = _mode_tridiag(g, alpha)
     rhs = a.reshape(nz, -1)
-    # transposed tridiagonal: sub'[k] = sup[k-1], sup'[k] = sub[k+1]
+    # transposed tridiagonal: sub'[k] = sup[k-1], sup'[k] = sub[k+1]; a
+    # periodic z also swaps the corners: sub'[0] = sup[nz-1], sup'[nz-1] = sub[0]
     subT = np.zeros(nz)
     supT = np.zeros(nz)
     subT[1:] = sup[:-1]
     supT[:-1] = sub[1:]
+    if per:
+        subT[0] = sup[nz - 1]
+        supT[nz - 1] = sub[0]
     if sing:
         out = np.empty_like(rhs)
-        out[:, 1:] = thomas(subT, diag[:, 1:], supT, rhs[:, 1:])
+        out[:, 1:] = (cyclic_solve if per else thomas)(subT, diag[:, 1:], supT, rhs[:, 1:])
         # zero mode: map g -> T_pin^{-1} diag(1,..,1,0) g; its transpose is
         # diag(1,..,1,0) T_pin^{-T} g with T_pin = rows 0..nz-2 of T plus e_last.
         tp = np.zeros((nz, nz))
@@ -478,7 +482,7 @@ def solve_T(w: np.ndarray, g: Grid, alpha=None) -> np.ndarray:
         z0[nz - 1] = 0.0
         out[:, 0] = z0
     else:
-        out = thomas(subT, diag, supT, rhs)
+        out = (cyclic_solve if per else thomas)(subT, diag, supT, rhs)
     out = out.reshape(nz, ny, nx)
     out = _apply_along(fwd_matrix(dir_kind(g.bc[2], g.bc[3]), ny).T, out, 1)
     out = _apply_along(fwd_matrix(dir_kind(g.bc[0], g.bc[1]), nx).T, out, 2)

@@ -56,3 +56,34 @@ def test_mutation_dropped_corners_fail_the_dense_pin(monkeypatch):
     monkeypatch.setattr(C, "cyclic_solve", C.thomas)
     with pytest.raises(AssertionError):
         test_periodic_z_matches_dense_lu(O.BC_P, O.BC_N, 0.03)
+
+
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_P, O.BC_P), (O.BC_N, O.BC_D)])
+@pytest.mark.parametrize("alpha", [None, 0.03])
+def test_periodic_z_transpose_matches_dense(bcx, bcy, alpha):
+    """The transposed solve over a periodic z (corners swapped) is the dense
+    transpose of the solve map, assembled column by column."""
+    g = periodic_grid(4, 3, 6, bcx, bcy, 1.5)
+    n = g.nx * g.ny * g.nz
+    smat = np.empty((n, n))
+    e = np.zeros(n)
+    for q in range(n):
+        e[q] = 1.0
+        smat[:, q] = O.solve(e.reshape(g.nz, g.ny, g.nx), g, alpha).reshape(-1)
+        e[q] = 0.0
+    w = S.gaussian(530 + bcx, (g.nz, g.ny, g.nx))
+    assert O.rel_l2(O.solve_T(w, g, alpha), (smat.T @ w.reshape(-1)).reshape(w.shape)) < 1e-11
+
+
+@pytest.mark.parametrize("alpha", [1e-3, 0.2])
+def test_periodic_z_line_solves_against_the_stencil(alpha):
+    """(I - alpha L_z) u = f on each (i, j) line with the wrap coupling: the
+    z part of the stencil applied to the result returns f."""
+    g = periodic_grid(5, 3, 8, O.BC_P, O.BC_P, 1.5)
+    f = S.gaussian(540, (g.nz, g.ny, g.nx))
+    u = O.solve_z_lines(f, g, alpha)
+    zm, zp = np.roll(u, 1, axis=0), np.roll(u, -1, axis=0)
+    dzc = g.dzc.reshape(-1, 1, 1)
+    dzf = g.dzf.reshape(-1, 1, 1)
+    lz = ((zp - u) / dzc[1:] - (u - zm) / dzc[:-1]) / dzf
+    assert np.max(np.abs(u - alpha * lz - f)) < 1e-12 * np.max(np.abs(f))

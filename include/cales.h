@@ -65,8 +65,7 @@ enum cales_status {
     CALES_EUNSUPPORTED = -2, /* x/y: a length the transforms do not take (see
                                 cales_plan) or a side pairing other than P-P,
                                 N-N, D-D, DF-DF, N-D, D-N; periodic z with
-                                nz < 3 or on a path that needs z walls
-                                (adjoint, line solves, allocation-free solve) */
+                                nz < 3 or in the allocation-free solve      */
     CALES_ENOMEM = -3,       /* device allocation failed                        */
     CALES_ECUDA = -4,        /* a CUDA runtime call failed                      */
     CALES_ETOOBIG = -5       /* grid larger than the static scratch of
@@ -99,8 +98,9 @@ enum cales_device_status_bits {
  * u[0] follows from row 0 through a denominator that is a sum of positive
  * terms.  One thread per mode, 16 bytes per grid point of plan-owned
  * scratch.  It serves the Poisson and Helmholtz solves in every precision
- * mode and the residual; all-periodic/Neumann Poisson problems are made
- * consistent, their zero mode pinned and the result gauged as below.
+ * mode, their adjoints, the wall-normal line solves and the residual;
+ * all-periodic/Neumann Poisson problems are made consistent, their zero mode
+ * pinned and the result gauged as below.
  * dx, dy: uniform spacings.  dzc[0..nz]: distance between unknowns k-1 and k
  * (dzc[0], dzc[nz]: to the ghost/boundary node; mirror value dzf[0] resp.
  * dzf[nz-1] for cell-centred unknowns).  dzf[0..nz-1]: control-volume width

@@ -41,10 +41,17 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
     const T* __restrict__ za = a.za;
     const T* __restrict__ zc = a.zc;
 
+    // right-hand side of row k: scale * data, divided by dzf[k] for the
+    // adjoint (S^T = D S D^-1, D = diag(dzf)); the result is then times dzf[k]
+    const bool adj = a.adjoint != 0;
+    auto rhs = [&](int k) -> T {
+        const T v = sc * x[(long)k * nm];
+        return adj ? T(double(v) / a.dzf[k]) : v;
+    };
     if (a.singular && q == 0) {
         double sum = 0.0, sw = 0.0;
         for (int k = 0; k < nz; ++k) {
-            sum += a.dzf[k] * double(sc * x[k * nm]);
+            sum += a.dzf[k] * double(rhs(k));
             sw += a.dzf[k];
         }
         const T gmean = T(sum / sw);
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
             const T e = base + (k == 0 ? A : A * einv) + (last ? C : T(0));
             const T inv = rcp_<T>((last ? T(0) : C) + e);
             ev[k * nm] = last ? T(0) : C * inv;
-            d = (sc * x[k * nm] - gmean + (k > 0 ? A * d : T(0))) * inv;
+            d = (rhs(k) - gmean + (k > 0 ? A * d : T(0))) * inv;
             x[k * nm] = d;
             einv = e * inv;
         }
@@ -72,10 +79,12 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
         // gauge, and the caller's constant shift of the solution
         const T mean = T(sum / sw + (a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0));
         for (int k = 0; k < nz; ++k) x[k * nm] -= mean;
+        if (adj)
+            for (int k = 0; k < nz; ++k) x[k * nm] = T(double(x[k * nm]) * a.dzf[k]);
         return;
     }
 
-    const T g0 = sc * x[0];
+    const T g0 = rhs(0);
     T einv = T(0), dp = T(0), dq = T(0);
     for (int k = 1; k < nz; ++k) {
         const T A = al * za[k], C = al * zc[k];
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
         const T e = base + (k == 1 ? A : A * einv) + (last ? C : T(0));
         const T inv = rcp_<T>((last ? T(0) : C) + e);
         ev[k * nm] = last ? T(0) : C * inv;
-        dp = (sc * x[k * nm] + (k > 1 ? A * dp : T(0))) * inv;
+        dp = (rhs(k) + (k > 1 ? A * dp : T(0))) * inv;
         dq = (base + (k > 1 ? A * dq : T(0))) * inv;
         x[k * nm] = dp;
         zv[k * nm] = dq;
@@ -100,8 +109,11 @@ __global__ void __launch_bounds__(256) k_zsolve_cyclic(ZArgs<T> a, T* __restrict
     }
     const T A0 = al * za[0], C0 = al * zc[0];
     const T u0 = (g0 + A0 * plast + C0 * pk) / (base + A0 * qlast + C0 * qk);
-    x[0] = u0;
-    for (int k = 1; k < nz; ++k) x[k * nm] += u0 * (T(1) - zv[k * nm]);
+    x[0] = adj ? T(double(u0) * a.dzf[0]) : u0;
+    for (int k = 1; k < nz; ++k) {
+        const T v = x[k * nm] + u0 * (T(1) - zv[k * nm]);
+        x[k * nm] = adj ? T(double(v) * a.dzf[k]) : v;
+    }
 }
 
 template <typename T>

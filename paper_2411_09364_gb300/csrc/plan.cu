@@ -481,7 +481,6 @@ int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt&
     ZArgs<T> za = z_args<T>(P, work, o);
     P->prof_begin(st, "z_solve");
     if (P->bc[4] == CALES_BC_P) {
-        if (o.adjoint) return CALES_EUNSUPPORTED;
         T* ework = reinterpret_cast<T*>(P->zcyc);
         if (launch_zsolve_cyclic<T>(za, ework, ework + (size_t)P->nx * P->ny * P->nz, st) != cudaSuccess)
             return CALES_ECUDA;
@@ -686,7 +685,6 @@ int cales_internal_solve(cales_plan_s* P, bool helm, double alpha, bool adjoint,
 static int solve_common(cales_plan_t P, bool helm, double alpha, bool adjoint, const void* f, void* p, void* stream) {
     if (!P || !f || !p) return CALES_EINVAL;
     if (helm && !(alpha > 0.0)) return CALES_EINVAL;
-    if (P->bc[4] == CALES_BC_P && adjoint) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const PassOpt o = solve_opts(P, helm, alpha, adjoint);
     switch (P->precision) {
@@ -759,6 +757,20 @@ static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t 
     if (za.warp_mode && za.P <= 16 && P->lcache[zi]) {
         za.ecache = reinterpret_cast<T*>(P->lcache[zi]);
         za.ecache_mode = (lk.valid && lk.P == za.P && lk.maxm == za.maxm && lk.alpha == alpha) ? 2 : 1;
+    }
+    if (P->bc[4] == CALES_BC_P) {
+        // periodic z: one cyclic system per line (no eigenvalues, sigma 1),
+        // in place on u
+        if (f != u && cudaMemcpyAsync(u, f, (size_t)P->nx * P->ny * P->nz * sizeof(T), cudaMemcpyDeviceToDevice,
+                                      st) != cudaSuccess)
+            return CALES_ECUDA;
+        za.src = nullptr;
+        T* ework = reinterpret_cast<T*>(P->zcyc);
+        P->prof_begin(st, "z_lines");
+        if (launch_zsolve_cyclic<T>(za, ework, ework + (size_t)P->nx * P->ny * P->nz, st) != cudaSuccess)
+            return CALES_ECUDA;
+        P->prof_end(st);
+        return CALES_OK;
     }
     if (!za.warp_mode) {
         // the other z kernels work in place
@@ -931,7 +943,6 @@ int cales_helmholtz_solve(cales_plan_t P, double alpha, const void* f, void* u, 
 
 int cales_helmholtz_z_solve(cales_plan_t P, double alpha, const void* f, void* u, void* stream) {
     if (!P || !f || !u || !(alpha >= 0.0) || !std::isfinite(alpha)) return CALES_EINVAL;
-    if (P->bc[4] == CALES_BC_P) return CALES_EUNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (P->precision == CALES_FP32) return z_lines<float>(P, alpha, (const float*)f, (float*)u, st);
     return z_lines<double>(P, alpha, (const double*)f, (double*)u, st);

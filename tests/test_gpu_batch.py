@@ -155,3 +155,19 @@ def test_rk3_substep_16_domains_graph(cuda_device):
     pts = sum(p.numel for p in plans)
     print(f"RK3 substep, 16 domains, {len(plans)} solves, {batch.graph_nodes()} graph nodes: "
           f"{dt * 1e3:.2f} ms, {pts / dt / 1e9:.2f} Gpoint-solves/s")
+
+
+def test_fast_refinement_batch_takes_the_fork_join(cuda_device):
+    """Plans in the fast refinement mode are batched by the fork/join over
+    streams (the grouped stages are built for the exact-residual mode); the
+    results stay within the refinement tolerance of the oracle."""
+    domains = [(48, 32, 24), (64, 32, 40)]
+    batch, plans, tags = B.rk3_substep_batch(domains, [1e-3, 1e-4], precision=cs.FP32_REFINE_FAST, autotune=False)
+    fs = _inputs(plans, 4300)
+    us = [torch.empty_like(f) for f in fs]
+    batch.solve(fs, us)
+    torch.cuda.synchronize()
+    assert not batch.grouped()
+    for (d, name), plan, f, u in zip(tags, plans, fs, us):
+        o = O.solve(f.cpu().numpy(), _oracle_grid(plan), None if name == "p" else [1e-3, 1e-4][d])
+        assert O.rel_l2(u.cpu().numpy(), o) <= 1e-10, (d, name)

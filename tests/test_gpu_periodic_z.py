@@ -1,7 +1,8 @@
 """Periodic z (cyclic tridiagonal per mode) through the C ABI against the
-oracle: FP64 and FP32 Poisson and Helmholtz solves on stretched periodic
-grids, every x/y kind, ragged sizes, the singular all-periodic case, and the
-paths that refuse a periodic z."""
+oracle: FP64, FP32 and FP32 + refinement Poisson and Helmholtz solves on
+stretched periodic grids, every x/y kind, ragged sizes, the singular
+all-periodic case, the FP64 residual, the adjoint and the wall-normal line
+solves, and the one path that refuses a periodic z."""
 import math
 
 import numpy as np
@@ -95,10 +96,45 @@ def test_periodic_z_fp64_residual(cuda_device):
         assert np.abs(r.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_periodic_z_refuses_wall_only_paths(cuda_device):
+@pytest.mark.parametrize("precision", [cs.FP64, cs.FP32])
+@pytest.mark.parametrize("alpha", [1e-3, 0.05])
+def test_periodic_z_line_solves(cuda_device, precision, alpha):
+    """Wall-normal implicit line solves (Eq. 21) over a periodic z: one cyclic
+    system per (i, j) line, out of place and in place."""
+    g, plan = pair(24, 10, 33, O.BC_P, O.BC_N, precision=precision)
+    f = S.gaussian(750, (33, 10, 24))
+    x = torch.from_numpy(f).to("cuda", plan.dtype)
+    u = plan.helmholtz_z(alpha, x)
+    y = x.clone()
+    plan.helmholtz_z(alpha, y, y)
+    torch.cuda.synchronize()
+    ref = O.solve_z_lines(f, g, alpha)
+    assert torch.equal(u, y)
+    assert O.rel_l2(u.double().cpu().numpy(), ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("bcx,bcy", [(O.BC_P, O.BC_P), (O.BC_N, O.BC_D)])
+@pytest.mark.parametrize("alpha", [None, 2e-3])
+@pytest.mark.parametrize("precision", [cs.FP64, cs.FP32])
+def test_periodic_z_adjoint_matches_oracle_transpose(cuda_device, bcx, bcy, alpha, precision):
+    g, plan = pair(48, 20, 33, bcx, bcy, precision=precision)
+    w = S.gaussian(760 + bcx, (33, 20, 48))
+    x = torch.from_numpy(w).to("cuda", plan.dtype)
+    out = plan.poisson_adjoint(x) if alpha is None else plan.helmholtz_adjoint(alpha, x)
+    torch.cuda.synchronize()
+    rel = O.rel_l2(out.double().cpu().numpy(), O.solve_T(w, g, alpha))
+    print(f"periodic z adjoint bc {bcx},{bcy} alpha {alpha} prec {precision}: rel {rel:.3e}")
+    assert rel <= TOL[precision]
+
+
+def test_periodic_z_allocation_free_solve_refuses(cuda_device):
+    """The allocation-free entry point keeps to wall-bounded z (its static
+    scratch has no room for the cyclic solve's two fields)."""
+    import ctypes as C
+    from paper_2411_09364_gb300 import _native as N
     g, plan = pair(16, 8, 8, O.BC_P, O.BC_P)
     f = torch.zeros((8, 8, 16), dtype=torch.float64, device="cuda")
-    with pytest.raises(Exception):
-        plan.helmholtz_z(1e-3, f)
-    with pytest.raises(Exception):
-        plan.poisson_adjoint(f)
+    p = torch.zeros_like(f)
+    rc = N.lib().cales_poisson_solve_noalloc(plan.handle, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr()),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -2

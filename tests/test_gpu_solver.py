@@ -179,13 +179,14 @@ def test_config2_channel_divergence_fp64_fp32(cuda_device):
 
 @pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("zvariant", [0, 1])
-def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant):
+@pytest.mark.parametrize("bc,nx,ny", [((0, 0, 1, 1, 1, 2), 480, 120), ((1, 2, 3, 3, 1, 1), 480, 119)])
+def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant, bc, nx, ny):
     """Every FFT radix order (radix 16 first, 5 and 3 first, radix 8 only) and
     both z kernel variants of the launch schedule solve the same system:
-    lengths with factors 2, 3 and 5 (x 480 = 2 x 240, y 120 = 2 x 60), a
-    Neumann y, in FP64, FP32 and FP32 + refinement."""
-    nx, ny, nz = 480, 120, 48
-    bc = (0, 0, 1, 1, 1, 2)
+    lengths with factors 2, 3 and 5 (x 480 = 2 x 240; y 120 = 2 x 60, or 119
+    node unknowns: FFT length 120), Neumann, mixed and node kinds, in FP64,
+    FP32 and FP32 + refinement."""
+    nz = 48
     g, plan = pair(nx, ny, nz, bc, beta=1.7)
     plan.set_schedule([0, 0, 0, 0, order, zvariant])
     assert plan.schedule()[4:] == (order, zvariant)
@@ -201,7 +202,7 @@ def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant):
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0, 1, 1), (0, 0, 1, 1, 1, 1), (1, 1, 2, 2, 3, 3), (1, 2, 0, 0, 2, 1),
                                 (3, 3, 2, 1, 1, 3), (0, 0, 0, 0, 0, 0)])
 @pytest.mark.parametrize("alpha", [None, 1e-3])
-@pytest.mark.parametrize("sweeps", [2, 3])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
 def test_fast_refinement_against_oracle(cuda_device, bc, alpha, sweeps):
     """FP32 solves with one double-float residual and FP32 residual updates
     for the later sweeps: every z kind (periodic included, with its wrap
@@ -224,5 +225,6 @@ def test_fast_refinement_against_oracle(cuda_device, bc, alpha, sweeps):
     f = S.gaussian(81 + sweeps, (nz, ny, nx))
     rel = O.rel_l2(solve_gpu(plan, f, alpha), O.solve(f, g, alpha))
     print(f"fast refinement bc {bc} alpha {alpha} sweeps {sweeps}: rel {rel:.3e}")
-    assert rel <= TOL[cs.FP32_REFINE], rel
+    # one sweep is the plain refinement (nothing to update): about 1e-10
+    assert rel <= (TOL[cs.FP32_REFINE] if sweeps > 1 else 1e-9), rel
     assert plan.status() == 0

@@ -640,57 +640,107 @@ template <typename T> struct ZwTables {
     }
 };
 
-// Rows [0, nz) of the 32 modes q0 .. q0+31 of `in` into the tile [nz][32] with
+// Tile layout: TM modes per row, the rows of segment t (rows [t m, t m + m))
+// at t * sst; for 16 FP32 modes a row is half the banks, so a segment of an
+// even number of rows is padded by 16 words to put the two segments that one
+// warp reads in different bank halves.
+template <typename T, int TM>
+__host__ __device__ __forceinline__ int zw_seg_stride(int m) {
+    return m * TM + ((TM * (int)sizeof(T) == 64 && (m & 1) == 0) ? 16 : 0);
+}
+
+// Rows [0, nz) of the TM modes q0 .. q0+TM-1 of `in` into the tile with
 // 16-byte cp.async copies (zero-filled past the w live modes); completion by
-// the caller's commit / wait.
-template <typename T>
-__device__ __forceinline__ void zw_load_async(T* tile, const T* __restrict__ in, long nmodes, long q0, int w, int nz) {
-    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
-    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
-        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-        cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
+// the caller's commit / wait.  Thread e copies chunk e % CPR of rows
+// e / CPR, e / CPR + RS, ... (RS = blockDim / CPR), tracking the row's
+// segment without a division per copy.
+template <typename T, int TM = 32>
+__device__ __forceinline__ void zw_load_async(T* tile, const T* __restrict__ in, long nmodes, long q0, int w, int nz,
+                                              int m = 0) {
+    constexpr int EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    if constexpr (TM == 32) {
+        for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+            cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
+        }
+    } else {
+        const int sst = zw_seg_stride<T, TM>(m), rs = blockDim.x / CPR;
+        const int c0 = (threadIdx.x % CPR) * EPC;
+        int k = threadIdx.x / CPR, sg = k / m, j = k - sg * m;
+        for (; k < nz; k += rs) {
+            cp_async16(tile + sg * sst + j * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
+            j += rs;
+            while (j >= m) { j -= m; ++sg; }
+        }
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, long nmodes, long q0, int w, int nz) {
-    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
-    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
-        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-        if (c0 < w)
-            *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) = *reinterpret_cast<const float4*>(tile + k * TM + c0);
+template <typename T, int TM = 32>
+__device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, long nmodes, long q0, int w, int nz,
+                                         int m = 0) {
+    constexpr int EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    if constexpr (TM == 32) {
+        for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+            if (c0 < w)
+                *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) = *reinterpret_cast<const float4*>(tile + k * TM + c0);
+        }
+    } else {
+        const int sst = zw_seg_stride<T, TM>(m), rs = blockDim.x / CPR;
+        const int c0 = (threadIdx.x % CPR) * EPC;
+        int k = threadIdx.x / CPR, sg = k / m, j = k - sg * m;
+        for (; k < nz; k += rs) {
+            if (c0 < w)
+                *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) =
+                    *reinterpret_cast<const float4*>(tile + sg * sst + j * TM + c0);
+            j += rs;
+            while (j >= m) { j -= m; ++sg; }
+        }
     }
 }
 
-// The solve of one tile of 32 modes (q0 .. q0 + w - 1) already in shared
-// memory, in place; every thread of the CTA takes part (P warps, warp s owns
-// rows [s m, s m + m)).  Phases as in the header of this file; the segment
+// The solve of one tile of TM modes (q0 .. q0 + w - 1) already in shared
+// memory, in place; every thread of the CTA takes part (P groups of TM
+// threads, group s owns rows [s m, s m + m); for TM = 16 a warp holds two
+// groups).  Phases as in the header of this file; the segment
 // states are chained by warp 0 through `ch` (6 x [P][32]).
 // FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
 // predicates and the first/last-row conditions reduce to compile-time tests
 // on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
 // transposed) instead of the uniform forward scale.
-template <typename T, int MAXM, bool FULL, bool ADJ>
+template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
 __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch, const ZwTables<T>& tb, long q0,
-                                              int w, const int P, const int Pb) {
-    // P: segments of this line; Pb = blockDim.x / 32 >= P warps, the chain
-    // arrays hold Pb slots.  Warps s >= P (grouped launches over lines of
+                                              int w, const int P, const int Pb, const bool pending = false) {
+    // pending: the tile's cp.async copies and the table fill may still be in
+    // flight; the per-mode global loads below are issued first, then the CTA
+    // waits for its copies and synchronises.
+    // P: segments of this line; Pb = blockDim.x / TM >= P groups, the chain
+    // arrays hold Pb slots.  Groups s >= P (grouped launches over lines of
     // different depth) own no rows and only take part in the barriers.
-    constexpr int TM = 32;
     const int nz = a.nz;
     const int m = (nz + P - 1) / P;
+    const int sst = zw_seg_stride<T, TM>(m);
+#define ZROW(k) ((TM == 32) ? (k) * TM : ((k) / m) * sst + ((k) - ((k) / m) * m) * TM)
     const int tid = threadIdx.x;
     const T* sA = tb.sA;
     const T* sC = tb.sC;
     const ZPair<T>* sAC = tb.sAC;
     const bool sing_tile = a.singular && q0 == 0;
-    if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) tb.save0[k] = tile[k * TM];
-
-    const int s = tid >> 5, c = tid & 31;
+    const int s = tid / TM, c = tid % TM;
     const long q = q0 + (c < w ? c : 0);
-    const int my = (int)(q / a.nx), mx = (int)(q - (long)my * a.nx);
+    int my, mx;
+    if ((long)a.nx * a.ny < (1L << 31)) { my = (int)q / a.nx; mx = (int)q - my * a.nx; }
+    else { my = (int)(q / a.nx); mx = (int)(q - (long)my * a.nx); }
     const T lam = a.lamx[mx] + a.lamy[my];
+    // cached segment-entry pivot (stride 0: every lane of every CTA reads the same slot)
+    const T e_cached = (a.ecache_mode == 2 && s > 0)
+                           ? a.ecache[a.ecache_stride ? (long)s * a.ecache_stride + q : (long)s] : T(0);
+    if (pending) {
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    if (sing_tile && tid == 0)
+        for (int k = 0; k < nz; ++k) tb.save0[k] = tile[ZROW(k)];
     const T base = a.sigma - a.alpha * lam;
     const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
     const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
@@ -703,7 +753,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     const T gsc = T(a.scale);
     const bool lastseg = s == P - 1, firstseg = s == 0;
     (void)lastseg; (void)firstseg;
-    T* col = tile + k0 * TM + c;
+    T* col = tile + (act ? s : 0) * sst + c;
     T* c11 = ch;
     T* c12 = ch + Pb * TM;
     T* c21 = ch + 2 * Pb * TM;
@@ -717,7 +767,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
 
     T e_in;
     if (a.ecache_mode == 2) {
-        e_in = s > 0 ? a.ecache[a.ecache_stride ? (long)s * a.ecache_stride + q : (long)s] : T(0);
+        e_in = e_cached;
     } else {
         // A: composite pivot map of the segment
         {
@@ -850,57 +900,60 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     __syncthreads();
     if (sing_tile && tid == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, nz, 0, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf, nz, base0, true, a.cacc,
-                       a.cacc_scale, 0, a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
+        serial_line<T>(tile, TM, TM == 32 ? nz : m, TM == 32 ? 0 : sst, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf,
+                       nz, base0, true, a.cacc, a.cacc_scale, 0, a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
-            if (!isfinite(tile[k * TM])) {
+            if (!isfinite(tile[ZROW(k)])) {
                 if (a.status) atomicOr(a.status, ST_NONFINITE);
                 break;
             }
     }
+#undef ZROW
     __syncthreads();
 }
 
-// One tile of 32 consecutive modes per CTA: load (16-byte cp.async, all in
-// flight), solve, store.  P segments (warps) of the line, Pb = blockDim / 32.
-template <typename T, int MAXM, bool FULL, bool ADJ>
+// One tile of TM consecutive modes per CTA: load (16-byte cp.async, all in
+// flight), solve, store.  P segments (groups of TM threads) of the line,
+// Pb = blockDim / TM.
+template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
 __device__ __forceinline__ void zw_kernel_body(const ZArgs<T>& a, const int bx, const int P, const int Pb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TM = 32;
     const int nz = a.nz;
     const int m = (nz + P - 1) / P;
+    const int sst = zw_seg_stride<T, TM>(m);
     const long nmodes = (long)a.nx * a.ny;
-    T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
-    T* ch = tile + (long)P * m * TM;                   // 6 x [Pb][32] chain states
+    T* tile = reinterpret_cast<T*>(smem_raw);          // P segments of sst elements
+    T* ch = tile + (long)P * sst;                      // 6 x [Pb][TM] chain states
     ZwTables<T> tb(ch + 6 * Pb * TM, nz);
     const long q0 = (long)bx * TM;
     const int w = (int)min((long)TM, nmodes - q0);
     const T* __restrict__ in = a.src ? a.src : a.data;
-    tb.fill(a);
+    // the tile copy is issued first; the coefficient tables are filled and
+    // the per-mode values loaded while it is in flight
     if (a.bulk) {
-        zw_load_async<T>(tile, in, nmodes, q0, w, nz);
-        cp_async_wait_all();
+        zw_load_async<T, TM>(tile, in, nmodes, q0, w, nz, m);
     } else {
         for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
-            const int k = e / TM, c = e - k * TM;
-            tile[e] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
+            const int k = e / TM, c = e - k * TM, sg = k / m;
+            tile[sg * sst + (k - sg * m) * TM + c] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
         }
     }
-    __syncthreads();
-    zw_solve_tile<T, MAXM, FULL, ADJ>(a, tile, ch, tb, q0, w, P, Pb);
+    tb.fill(a);
+    zw_solve_tile<T, MAXM, FULL, ADJ, TM>(a, tile, ch, tb, q0, w, P, Pb, true);
     if (a.bulk) {
-        zw_store<T>(a.data, tile, nmodes, q0, w, nz);
+        zw_store<T, TM>(a.data, tile, nmodes, q0, w, nz, m);
     } else {
         for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
-            const int k = e / TM, cc = e - k * TM;
-            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[e];
+            const int k = e / TM, cc = e - k * TM, sg = k / m;
+            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[sg * sst + (k - sg * m) * TM + cc];
         }
     }
 }
 
-template <typename T, int MAXM, bool FULL, bool ADJ>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(const __grid_constant__ ZArgs<T> a) {
-    zw_kernel_body<T, MAXM, FULL, ADJ>(a, blockIdx.x, blockDim.x / 32, blockDim.x / 32);
+template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
+__global__ void __launch_bounds__(16 * TM, sizeof(T) == 4 ? 64 / TM : 32 / TM)
+    k_zsolve_w(const __grid_constant__ ZArgs<T> a) {
+    zw_kernel_body<T, MAXM, FULL, ADJ, TM>(a, blockIdx.x, blockDim.x / TM, blockDim.x / TM);
 }
 
 // Grouped launch (z stage of many solves): CTA b solves tile work[b].y of
@@ -966,10 +1019,15 @@ __global__ void __launch_bounds__(512, 1) k_zsolve_wp(ZArgs<T> a) {
     cp_async_wait_none();
 }
 
+template <typename T, int TM>
+size_t zsolve_w_smem_tm(int nz, int P) {
+    const int m = (nz + P - 1) / P;
+    return ((size_t)P * zw_seg_stride<T, TM>(m) + 6 * (size_t)P * TM + 8 * (size_t)nz) * sizeof(T);
+}
+
 template <typename T>
 size_t zsolve_w_smem(int nz, int P) {
-    const int m = (nz + P - 1) / P;
-    return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 8 * (size_t)nz) * sizeof(T);
+    return zsolve_w_smem_tm<T, 32>(nz, P);
 }
 
 // Shared memory of the persistent variant: two tile buffers.
@@ -1000,7 +1058,7 @@ static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
     // persistent double-buffered kernel when every SM gets several tiles and
     // two tile buffers fit
     const size_t smp = zsolve_wp_smem<T>(a.nz, a.P);
-    if (a.bulk && a.persist != 0 && ntiles >= 8L * nsm && smp <= 227 * 1024) {
+    if (a.bulk && a.persist == 1 && ntiles >= 8L * nsm && smp <= 227 * 1024) {
         auto kern = full ? (a.adjoint ? k_zsolve_wp<T, MAXM, true, true> : k_zsolve_wp<T, MAXM, true, false>)
                          : (a.adjoint ? k_zsolve_wp<T, MAXM, false, true> : k_zsolve_wp<T, MAXM, false, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
@@ -1010,6 +1068,16 @@ static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
         const long slots = (long)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < slots ? ntiles : slots);
         kern<<<grid, 32 * a.P, smp, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (a.persist == 2) {
+        // 16 modes per CTA: 16 P threads, four CTAs per SM (FP32) instead of two
+        constexpr int TM = 16;
+        const size_t sm = zsolve_w_smem_tm<T, TM>(a.nz, a.P);
+        auto kern = full ? (a.adjoint ? k_zsolve_w<T, MAXM, true, true, TM> : k_zsolve_w<T, MAXM, true, false, TM>)
+                         : (a.adjoint ? k_zsolve_w<T, MAXM, false, true, TM> : k_zsolve_w<T, MAXM, false, false, TM>);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<(unsigned)((nmodes + TM - 1) / TM), TM * a.P, sm, st>>>(a);
         return cudaGetLastError();
     }
     const size_t sm = zsolve_w_smem<T>(a.nz, a.P);

@@ -313,11 +313,10 @@ int cales_adam_step(float* theta, const double* grad, float* m, float* v, int n,
  * bound, FFT radix order of x and y (0: radix-16 passes first, the order of
  * the compile-time-size kernels; 1: radices 5 and 3 first; 2: radix-8 passes
  * in place of radix 16), z kernel variant (0: one 32-mode tile per CTA; 1:
- * persistent CTAs with two tile buffers; 2: one 16-mode tile per CTA, half
- * the threads and shared memory)}; 0 selects the built-in heuristic and
- * infeasible sizes fall back to it.  A new radix order rebuilds the plan's
- * transform tables (synchronises the device).  CALES_EINVAL for negative
- * entries, an order > 2 or a variant > 2.
+ * persistent CTAs with two tile buffers)}; 0 selects the built-in heuristic
+ * and infeasible sizes fall back to it.  A new radix order rebuilds the
+ * plan's transform tables (synchronises the device).  CALES_EINVAL for
+ * negative entries, an order > 2 or a variant > 1.
  */
 #define CALES_SCHED_LEN 6
 int cales_set_schedule(cales_plan_t plan, const int sched[CALES_SCHED_LEN]);
@@ -328,8 +327,8 @@ int cales_get_schedule(cales_plan_t plan, int sched[CALES_SCHED_LEN]);
  * communication backends, Sec. 3.1): times candidate schedules of the plan's
  * Poisson solve at its current precision on the device (each knob tuned in
  * turn: FFT radix order 0/1/2 on the x + y stages, x budget 32/64/96 KB, y
- * tiles 8/16/32/64/128, z segments of 16/32/64 rows, then the z kernel
- * variants 1 and 2, each kept only when more than 3 % faster),
+ * tiles 8/16/32/64/128, z segments of 16/32/64 rows, then the persistent z
+ * kernel, kept only when more than 3 % faster),
  * keeps the fastest and sets it on the plan.  With cache_path non-NULL the
  * result is looked up first and stored after tuning in a JSON object keyed by
  * "nx,ny,nz,bcx,bcy,zlo,zhi,precision,device".  Allocates two temporary fields

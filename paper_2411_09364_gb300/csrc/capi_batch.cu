@@ -142,7 +142,7 @@ int cales_set_schedule(cales_plan_t P, const int sched[CALES_SCHED_LEN]) {
     if (!P || !sched) return CALES_EINVAL;
     for (int i = 0; i < CALES_SCHED_LEN; ++i)
         if (sched[i] < 0) return CALES_EINVAL;
-    if (sched[4] > 2 || sched[5] > 2) return CALES_EINVAL;
+    if (sched[4] > 2 || sched[5] > 1) return CALES_EINVAL;
     const int rc = plan_set_radix_order(P, sched[4]);
     if (rc) return rc;
     for (int i = 0; i < CALES_SCHED_LEN; ++i) P->sched[i] = sched[i];
@@ -220,9 +220,7 @@ int cales_autotune(cales_plan_t P, const char* cache_path, void* stream) {
         best[2] = bw;
         best[3] = bm;
         double tz[3];
-        double bv = 0.97 * bt;
-        for (int v = 1; v <= 2; ++v)
-            if (trial(5, v, -1, 0, tz) && tz[2] < bv) { bv = tz[2]; best[5] = v; }
+        if (trial(5, 1, -1, 0, tz) && tz[2] < 0.97 * bt) best[5] = 1;
     }
     cudaFree(f);
     cudaFree(p);

@@ -75,9 +75,8 @@ template <typename T> struct ZArgs {
     T* ecache;
     int ecache_mode;
     long ecache_stride;  // nmodes; 0 when every line has the same pivots (line solves)
-    int persist;         // warp-per-segment kernel: 0 = one tile of 32 modes per CTA; 1 = the
-                         // persistent double-buffered variant where it applies; 2 = one tile
-                         // of 16 modes per CTA (half the threads and shared memory)
+    int persist;         // warp-per-segment kernel: 0 = one tile per CTA; else the persistent
+                         // double-buffered variant where it applies
     // singular mode 0: shift_acc[0] * shift_scale subtracted from the whole
     // line after the gauge (a constant of the solution in physical space; the
     // last refinement sweep removes the measured mean of its iterate this way)

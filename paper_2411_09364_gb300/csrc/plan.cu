@@ -353,20 +353,13 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // (FP32, 16 segments of 32 rows) it took 1.55 ms per launch against 0.87 ms,
 // since one resident CTA per SM leaves the serial segment chains and the
 // tile copies unhidden.
-// CALES_ZVARIANT=1|2 picks the persistent or the 16-mode variant for plans
-// whose schedule leaves the z variant to the default (CALES_ZPERSIST=1 is the
-// older spelling of CALES_ZVARIANT=1).
-static int zvariant_env() {
-    static const int v = [] {
-        const char* e = getenv("CALES_ZVARIANT");
-        if (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) return e[0] - '0';
-        const char* p = getenv("CALES_ZPERSIST");
-        return (p && p[0] == '1') ? 1 : 0;
+static bool zpersist_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("CALES_ZPERSIST");
+        return e && e[0] == '1';
     }();
-    return v;
+    return on;
 }
-
-static int zvariant(const cales_plan_s* P) { return P->sched[5] != 0 ? P->sched[5] : zvariant_env(); }
 
 // Argument blocks of the stages of one pass: in (TIn) -> work (T, mode
 // space) -> out (MODE).  Shared by the single-solve pipeline and the grouped
@@ -438,7 +431,7 @@ ZArgs<T> z_args(cales_plan_s* P, T* work, const PassOpt& o) {
                           zk.alpha == o.alpha) ? 2 : 1;
     }
     za.ecache_stride = (long)P->nx * P->ny;
-    za.persist = zvariant(P);
+    za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
     // the gauge shift of the last refinement sweep is applied to the mode
     // (0, 0) line here: a constant in mode space (0, 0) is the same constant
     // at every point after the unnormalised inverse transforms
@@ -756,7 +749,7 @@ static int z_lines(cales_plan_t P, double alpha, const T* f, T* u, cudaStream_t 
     za.ecache = nullptr;
     za.ecache_mode = 0;
     za.ecache_stride = 0;
-    za.persist = zvariant(P);
+    za.persist = (zpersist_enabled() || P->sched[5] == 1) ? 1 : 0;
     za.shift_acc = nullptr;
     za.shift_scale = 0.0;
     const int zi = sizeof(T) == 8 ? 1 : 0;

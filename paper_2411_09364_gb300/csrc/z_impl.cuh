@@ -78,7 +78,7 @@ template <typename T> struct Piv {
 
 // Serial solve of one line (the singular mode 0): raw g0 -> x into col.
 template <typename T>
-__device__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T* r0, const T* sA, const T* sC, const T* sG,
+__device__ __noinline__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T* r0, const T* sA, const T* sC, const T* sG,
                             const T* sO, const double* dzf, int nz, T base, bool singular, double* cacc,
                             double cacc_scale, int sk, double shift = 0.0) {
     // coefficient tables may be skewed by one slot per segment of sk rows
@@ -117,6 +117,93 @@ __device__ void serial_line(T* tile, int stride, int m, int segs, const T* g0, T
     }
     for (int k = 0; k < nz; ++k) tile[(long)(k / m) * segs + (long)(k - (k / m) * m) * stride] *= sO[SKI(k)];
 #undef SKI
+}
+
+// The same line by one warp, for Neumann sides on both ends of z and a zero
+// diagonal shift (sigma = 0, lambda(0, 0) = 0).  Then every pivot excess is
+// zero: d_k = C_k below the pinned last row, so the forward elimination
+// y_k = (g_k + A_k y_{k-1}) / C_k and the back-substitution
+// x_k = y_k + (C_k / d_k) x_{k+1} are affine recurrences.  Lane l takes rows
+// [l R, l R + R) (R = ceil(nz / 32)); each recurrence is composed per chunk,
+// the chunk maps are combined by a shuffle scan (lane order forward, reverse
+// order backward) and the chunk is swept again from its incoming value.  The
+// per-row arithmetic is that of serial_line; projection and gauge sums are
+// warp reductions of the same FP64 terms.
+template <typename T>
+__device__ __noinline__ void singular_line_warp(T* tile, int stride, const T* g0, const T* sA, const T* sC, const T* sG, const T* sO,
+                                   const double* dzf, int nz, double* cacc, double cacc_scale, double shift,
+                                   int* status) {
+    const unsigned FULLM = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int R = (nz + 31) / 32;
+    const int k0 = min(nz, lane * R), k1 = min(nz, k0 + R);
+    double sg = 0.0, sw = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        sg += dzf[k] * double(g0[k]) * double(sG[k]);
+        sw += dzf[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sg += __shfl_xor_sync(FULLM, sg, o);
+        sw += __shfl_xor_sync(FULLM, sw, o);
+    }
+    const double gmean = sg / sw;
+    if (lane == 0 && cacc) cacc[0] += gmean * cacc_scale;
+    // forward: chunk map y_out = al * y_in + be
+    T al = T(1), be = T(0);
+    for (int k = k0; k < k1; ++k) {
+        if (k == nz - 1) { al = T(0); be = T(0); continue; }
+        const T inv = rcp_<T>(sC[k]);
+        const T ak = k > 0 ? sA[k] : T(0);
+        const T g = T(double(g0[k]) * double(sG[k]) - gmean);
+        al = ak * inv * al;
+        be = (g + ak * be) * inv;
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+        const T pa = __shfl_up_sync(FULLM, al, o), pb = __shfl_up_sync(FULLM, be, o);
+        if (lane >= o) { be = al * pb + be; al = al * pa; }
+    }
+    T y = __shfl_up_sync(FULLM, be, 1);
+    if (lane == 0) y = T(0);
+    for (int k = k0; k < k1; ++k) {
+        if (k == nz - 1) {
+            y = T(0);
+        } else {
+            const T inv = rcp_<T>(sC[k]);
+            const T ak = k > 0 ? sA[k] : T(0);
+            const T g = T(double(g0[k]) * double(sG[k]) - gmean);
+            y = (g + ak * y) * inv;
+        }
+        tile[(long)k * stride] = y;
+    }
+    // backward: chunk map x_top = Q + Rm * x_in (x_in: first row of the next chunk)
+    T Q = T(0), Rm = T(1);
+    for (int k = k1 - 1; k >= k0; --k) {
+        const T r = k < nz - 1 ? sC[k] * rcp_<T>(sC[k]) : T(0);
+        Q = tile[(long)k * stride] + r * Q;
+        Rm = r * Rm;
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+        const T nq = __shfl_down_sync(FULLM, Q, o), nr = __shfl_down_sync(FULLM, Rm, o);
+        if (lane + o < 32) { Q = Q + Rm * nq; Rm = Rm * nr; }
+    }
+    T x = __shfl_down_sync(FULLM, Q, 1);
+    if (lane == 31) x = T(0);
+    double sx = 0.0;
+    for (int k = k1 - 1; k >= k0; --k) {
+        const T r = k < nz - 1 ? sC[k] * rcp_<T>(sC[k]) : T(0);
+        x = tile[(long)k * stride] + r * x;
+        tile[(long)k * stride] = x;
+        sx += dzf[k] * double(x);
+    }
+    for (int o = 16; o > 0; o >>= 1) sx += __shfl_xor_sync(FULLM, sx, o);
+    const double mm = sx / sw + shift;      // gauge, and the caller's constant shift
+    bool bad = false;
+    for (int k = k0; k < k1; ++k) {
+        const T v = T(double(tile[(long)k * stride]) - mm) * sO[k];
+        tile[(long)k * stride] = v;
+        bad |= !isfinite(v);
+    }
+    if (__any_sync(FULLM, bad) && lane == 0 && status) atomicOr(status, ST_NONFINITE);
 }
 
 // Segment stride of the shared tile (elements): m*tm rounded so that the P
@@ -640,93 +727,54 @@ template <typename T> struct ZwTables {
     }
 };
 
-// Tile layout: TM modes per row, the rows of segment t (rows [t m, t m + m))
-// at t * sst; for 16 FP32 modes a row is half the banks, so a segment of an
-// even number of rows is padded by 16 words to put the two segments that one
-// warp reads in different bank halves.
-template <typename T, int TM>
-__host__ __device__ __forceinline__ int zw_seg_stride(int m) {
-    return m * TM + ((TM * (int)sizeof(T) == 64 && (m & 1) == 0) ? 16 : 0);
-}
-
-// Rows [0, nz) of the TM modes q0 .. q0+TM-1 of `in` into the tile with
+// Rows [0, nz) of the 32 modes q0 .. q0+31 of `in` into the tile [nz][32] with
 // 16-byte cp.async copies (zero-filled past the w live modes); completion by
-// the caller's commit / wait.  Thread e copies chunk e % CPR of rows
-// e / CPR, e / CPR + RS, ... (RS = blockDim / CPR), tracking the row's
-// segment without a division per copy.
-template <typename T, int TM = 32>
-__device__ __forceinline__ void zw_load_async(T* tile, const T* __restrict__ in, long nmodes, long q0, int w, int nz,
-                                              int m = 0) {
-    constexpr int EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
-    if constexpr (TM == 32) {
-        for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
-        }
-    } else {
-        const int sst = zw_seg_stride<T, TM>(m), rs = blockDim.x / CPR;
-        const int c0 = (threadIdx.x % CPR) * EPC;
-        int k = threadIdx.x / CPR, sg = k / m, j = k - sg * m;
-        for (; k < nz; k += rs) {
-            cp_async16(tile + sg * sst + j * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
-            j += rs;
-            while (j >= m) { j -= m; ++sg; }
-        }
+// the caller's commit / wait.
+template <typename T>
+__device__ __forceinline__ void zw_load_async(T* tile, const T* __restrict__ in, long nmodes, long q0, int w, int nz) {
+    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+        cp_async16(tile + k * TM + c0, in + (long)k * nmodes + q0 + (c0 < w ? c0 : 0), c0 < w);
     }
 }
 
-template <typename T, int TM = 32>
-__device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, long nmodes, long q0, int w, int nz,
-                                         int m = 0) {
-    constexpr int EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
-    if constexpr (TM == 32) {
-        for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
-            const int k = e / CPR, c0 = (e - k * CPR) * EPC;
-            if (c0 < w)
-                *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) = *reinterpret_cast<const float4*>(tile + k * TM + c0);
-        }
-    } else {
-        const int sst = zw_seg_stride<T, TM>(m), rs = blockDim.x / CPR;
-        const int c0 = (threadIdx.x % CPR) * EPC;
-        int k = threadIdx.x / CPR, sg = k / m, j = k - sg * m;
-        for (; k < nz; k += rs) {
-            if (c0 < w)
-                *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) =
-                    *reinterpret_cast<const float4*>(tile + sg * sst + j * TM + c0);
-            j += rs;
-            while (j >= m) { j -= m; ++sg; }
-        }
+template <typename T>
+__device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, long nmodes, long q0, int w, int nz) {
+    constexpr int TM = 32, EPC = 16 / (int)sizeof(T), CPR = TM / EPC;
+    for (int e = threadIdx.x; e < nz * CPR; e += blockDim.x) {
+        const int k = e / CPR, c0 = (e - k * CPR) * EPC;
+        if (c0 < w)
+            *reinterpret_cast<float4*>(out + (long)k * nmodes + q0 + c0) = *reinterpret_cast<const float4*>(tile + k * TM + c0);
     }
 }
 
-// The solve of one tile of TM modes (q0 .. q0 + w - 1) already in shared
-// memory, in place; every thread of the CTA takes part (P groups of TM
-// threads, group s owns rows [s m, s m + m); for TM = 16 a warp holds two
-// groups).  Phases as in the header of this file; the segment
+// The solve of one tile of 32 modes (q0 .. q0 + w - 1) already in shared
+// memory, in place; every thread of the CTA takes part (P warps, warp s owns
+// rows [s m, s m + m)).  Phases as in the header of this file; the segment
 // states are chained by warp 0 through `ch` (6 x [P][32]).
 // FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
 // predicates and the first/last-row conditions reduce to compile-time tests
 // on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
 // transposed) instead of the uniform forward scale.
-template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
+template <typename T, int MAXM, bool FULL, bool ADJ>
 __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch, const ZwTables<T>& tb, long q0,
                                               int w, const int P, const int Pb, const bool pending = false) {
     // pending: the tile's cp.async copies and the table fill may still be in
     // flight; the per-mode global loads below are issued first, then the CTA
     // waits for its copies and synchronises.
-    // P: segments of this line; Pb = blockDim.x / TM >= P groups, the chain
-    // arrays hold Pb slots.  Groups s >= P (grouped launches over lines of
+    // P: segments of this line; Pb = blockDim.x / 32 >= P warps, the chain
+    // arrays hold Pb slots.  Warps s >= P (grouped launches over lines of
     // different depth) own no rows and only take part in the barriers.
+    constexpr int TM = 32;
     const int nz = a.nz;
     const int m = (nz + P - 1) / P;
-    const int sst = zw_seg_stride<T, TM>(m);
-#define ZROW(k) ((TM == 32) ? (k) * TM : ((k) / m) * sst + ((k) - ((k) / m) * m) * TM)
     const int tid = threadIdx.x;
     const T* sA = tb.sA;
     const T* sC = tb.sC;
     const ZPair<T>* sAC = tb.sAC;
     const bool sing_tile = a.singular && q0 == 0;
-    const int s = tid / TM, c = tid % TM;
+    const int s = tid >> 5, c = tid & 31;
     const long q = q0 + (c < w ? c : 0);
     int my, mx;
     if ((long)a.nx * a.ny < (1L << 31)) { my = (int)q / a.nx; mx = (int)q - my * a.nx; }
@@ -740,7 +788,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
         __syncthreads();
     }
     if (sing_tile && tid == 0)
-        for (int k = 0; k < nz; ++k) tb.save0[k] = tile[ZROW(k)];
+        for (int k = 0; k < nz; ++k) tb.save0[k] = tile[k * TM];
     const T base = a.sigma - a.alpha * lam;
     const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
     const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
@@ -753,7 +801,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     const T gsc = T(a.scale);
     const bool lastseg = s == P - 1, firstseg = s == 0;
     (void)lastseg; (void)firstseg;
-    T* col = tile + (act ? s : 0) * sst + c;
+    T* col = tile + k0 * TM + c;
     T* c11 = ch;
     T* c12 = ch + Pb * TM;
     T* c21 = ch + 2 * Pb * TM;
@@ -898,32 +946,36 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     if ((sing_tile && c == 0) || c >= w) bad = false;
     if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
     __syncthreads();
-    if (sing_tile && tid == 0) {
+    if (sing_tile && s == 0) {
         const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
-        serial_line<T>(tile, TM, TM == 32 ? nz : m, TM == 32 ? 0 : sst, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf,
-                       nz, base0, true, a.cacc, a.cacc_scale, 0, a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
-        for (int k = 0; k < nz; ++k)
-            if (!isfinite(tile[ZROW(k)])) {
-                if (a.status) atomicOr(a.status, ST_NONFINITE);
-                break;
-            }
+        const double shift = a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0;
+        if (base0 == T(0) && a.zlo == ZBC_N && a.zhi == ZBC_N) {
+            singular_line_warp<T>(tile, TM, tb.save0, sA, sC, tb.sG, tb.sO, a.dzf, nz, a.cacc, a.cacc_scale, shift,
+                                  a.status);
+        } else if (c == 0) {
+            serial_line<T>(tile, TM, nz, 0, tb.save0, tb.r0, sA, sC, tb.sG, tb.sO, a.dzf, nz, base0, true, a.cacc,
+                           a.cacc_scale, 0, shift);
+            for (int k = 0; k < nz; ++k)
+                if (!isfinite(tile[k * TM])) {
+                    if (a.status) atomicOr(a.status, ST_NONFINITE);
+                    break;
+                }
+        }
     }
-#undef ZROW
     __syncthreads();
 }
 
-// One tile of TM consecutive modes per CTA: load (16-byte cp.async, all in
-// flight), solve, store.  P segments (groups of TM threads) of the line,
-// Pb = blockDim / TM.
-template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
+// One tile of 32 consecutive modes per CTA: load (16-byte cp.async, all in
+// flight), solve, store.  P segments (warps) of the line, Pb = blockDim / 32.
+template <typename T, int MAXM, bool FULL, bool ADJ>
 __device__ __forceinline__ void zw_kernel_body(const ZArgs<T>& a, const int bx, const int P, const int Pb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TM = 32;
     const int nz = a.nz;
     const int m = (nz + P - 1) / P;
-    const int sst = zw_seg_stride<T, TM>(m);
     const long nmodes = (long)a.nx * a.ny;
-    T* tile = reinterpret_cast<T*>(smem_raw);          // P segments of sst elements
-    T* ch = tile + (long)P * sst;                      // 6 x [Pb][TM] chain states
+    T* tile = reinterpret_cast<T*>(smem_raw);          // [P*m][32]
+    T* ch = tile + (long)P * m * TM;                   // 6 x [Pb][32] chain states
     ZwTables<T> tb(ch + 6 * Pb * TM, nz);
     const long q0 = (long)bx * TM;
     const int w = (int)min((long)TM, nmodes - q0);
@@ -931,29 +983,28 @@ __device__ __forceinline__ void zw_kernel_body(const ZArgs<T>& a, const int bx, 
     // the tile copy is issued first; the coefficient tables are filled and
     // the per-mode values loaded while it is in flight
     if (a.bulk) {
-        zw_load_async<T, TM>(tile, in, nmodes, q0, w, nz, m);
+        zw_load_async<T>(tile, in, nmodes, q0, w, nz);
     } else {
         for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
-            const int k = e / TM, c = e - k * TM, sg = k / m;
-            tile[sg * sst + (k - sg * m) * TM + c] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
+            const int k = e / TM, c = e - k * TM;
+            tile[e] = c < w ? in[(long)k * nmodes + q0 + c] : T(0);
         }
     }
     tb.fill(a);
-    zw_solve_tile<T, MAXM, FULL, ADJ, TM>(a, tile, ch, tb, q0, w, P, Pb, true);
+    zw_solve_tile<T, MAXM, FULL, ADJ>(a, tile, ch, tb, q0, w, P, Pb, true);
     if (a.bulk) {
-        zw_store<T, TM>(a.data, tile, nmodes, q0, w, nz, m);
+        zw_store<T>(a.data, tile, nmodes, q0, w, nz);
     } else {
         for (int e = threadIdx.x; e < nz * TM; e += blockDim.x) {
-            const int k = e / TM, cc = e - k * TM, sg = k / m;
-            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[sg * sst + (k - sg * m) * TM + cc];
+            const int k = e / TM, cc = e - k * TM;
+            if (cc < w) a.data[(long)k * nmodes + q0 + cc] = tile[e];
         }
     }
 }
 
-template <typename T, int MAXM, bool FULL, bool ADJ, int TM = 32>
-__global__ void __launch_bounds__(16 * TM, sizeof(T) == 4 ? 64 / TM : 32 / TM)
-    k_zsolve_w(const __grid_constant__ ZArgs<T> a) {
-    zw_kernel_body<T, MAXM, FULL, ADJ, TM>(a, blockIdx.x, blockDim.x / TM, blockDim.x / TM);
+template <typename T, int MAXM, bool FULL, bool ADJ>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_zsolve_w(const __grid_constant__ ZArgs<T> a) {
+    zw_kernel_body<T, MAXM, FULL, ADJ>(a, blockIdx.x, blockDim.x / 32, blockDim.x / 32);
 }
 
 // Grouped launch (z stage of many solves): CTA b solves tile work[b].y of
@@ -1019,15 +1070,10 @@ __global__ void __launch_bounds__(512, 1) k_zsolve_wp(ZArgs<T> a) {
     cp_async_wait_none();
 }
 
-template <typename T, int TM>
-size_t zsolve_w_smem_tm(int nz, int P) {
-    const int m = (nz + P - 1) / P;
-    return ((size_t)P * zw_seg_stride<T, TM>(m) + 6 * (size_t)P * TM + 8 * (size_t)nz) * sizeof(T);
-}
-
 template <typename T>
 size_t zsolve_w_smem(int nz, int P) {
-    return zsolve_w_smem_tm<T, 32>(nz, P);
+    const int m = (nz + P - 1) / P;
+    return ((size_t)P * m * 32 + 6 * (size_t)P * 32 + 8 * (size_t)nz) * sizeof(T);
 }
 
 // Shared memory of the persistent variant: two tile buffers.
@@ -1058,7 +1104,7 @@ static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
     // persistent double-buffered kernel when every SM gets several tiles and
     // two tile buffers fit
     const size_t smp = zsolve_wp_smem<T>(a.nz, a.P);
-    if (a.bulk && a.persist == 1 && ntiles >= 8L * nsm && smp <= 227 * 1024) {
+    if (a.bulk && a.persist != 0 && ntiles >= 8L * nsm && smp <= 227 * 1024) {
         auto kern = full ? (a.adjoint ? k_zsolve_wp<T, MAXM, true, true> : k_zsolve_wp<T, MAXM, true, false>)
                          : (a.adjoint ? k_zsolve_wp<T, MAXM, false, true> : k_zsolve_wp<T, MAXM, false, false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
@@ -1068,16 +1114,6 @@ static cudaError_t launch_zsolve_w(const ZArgs<T>& a, cudaStream_t st) {
         const long slots = (long)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < slots ? ntiles : slots);
         kern<<<grid, 32 * a.P, smp, st>>>(a);
-        return cudaGetLastError();
-    }
-    if (a.persist == 2) {
-        // 16 modes per CTA: 16 P threads, four CTAs per SM (FP32) instead of two
-        constexpr int TM = 16;
-        const size_t sm = zsolve_w_smem_tm<T, TM>(a.nz, a.P);
-        auto kern = full ? (a.adjoint ? k_zsolve_w<T, MAXM, true, true, TM> : k_zsolve_w<T, MAXM, true, false, TM>)
-                         : (a.adjoint ? k_zsolve_w<T, MAXM, false, true, TM> : k_zsolve_w<T, MAXM, false, false, TM>);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<(unsigned)((nmodes + TM - 1) / TM), TM * a.P, sm, st>>>(a);
         return cudaGetLastError();
     }
     const size_t sm = zsolve_w_smem<T>(a.nz, a.P);

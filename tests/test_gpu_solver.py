@@ -178,11 +178,11 @@ def test_config2_channel_divergence_fp64_fp32(cuda_device):
 
 
 @pytest.mark.parametrize("order", [0, 1, 2])
-@pytest.mark.parametrize("zvariant", [0, 1, 2])
+@pytest.mark.parametrize("zvariant", [0, 1])
 @pytest.mark.parametrize("bc,nx,ny", [((0, 0, 1, 1, 1, 2), 480, 120), ((1, 2, 3, 3, 1, 1), 480, 119)])
 def test_schedule_radix_order_and_z_variant(cuda_device, order, zvariant, bc, nx, ny):
     """Every FFT radix order (radix 16 first, 5 and 3 first, radix 8 only) and
-    every z kernel variant of the launch schedule solves the same system:
+    both z kernel variants of the launch schedule solve the same system:
     lengths with factors 2, 3 and 5 (x 480 = 2 x 240; y 120 = 2 x 60, or 119
     node unknowns: FFT length 120), Neumann, mixed and node kinds, in FP64,
     FP32 and FP32 + refinement."""

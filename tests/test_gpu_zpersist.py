@@ -1,12 +1,10 @@
-"""The other z kernel variants against the one-tile-per-CTA kernel of 32 modes:
-the persistent double-buffered kernel (variant 1) and the kernel with 16 modes
-per CTA (variant 2, segment-padded tile layout).
+"""The persistent double-buffered z kernel against the one-tile-per-CTA kernel.
 
-All run the same per-mode arithmetic (the same device function), so their
-solves agree bit for bit.  The variant runs in a child process started with
-CALES_ZVARIANT set (read once per process).  The grids have enough modes (at
-least eight 32-mode tiles per SM) for the persistent kernel to be chosen: full
-and ragged z segments (odd and even segment lengths), FP32, FP64 and FP32 +
+Both run the same per-tile arithmetic (the same device function), so their
+solves agree bit for bit.  The persistent kernel runs in a child process started
+with CALES_ZPERSIST=1 (read once per process).  The grids have enough modes
+(at least eight 32-mode tiles per SM) for the persistent kernel to be chosen:
+full and ragged z segments, a ragged last mode tile, FP32, FP64 and FP32 +
 refinement, Poisson, Helmholtz and the adjoint solve.
 """
 import os
@@ -29,7 +27,7 @@ CASES = [
     (512, 128, 64, (0, 0, 0, 0, 1, 1), (cs.FP32, cs.FP32_REFINE)),      # 4 full segments of 16 rows
     (256, 256, 300, (0, 0, 1, 1, 2, 1), (cs.FP32, cs.FP32_REFINE)),     # 10 segments of 30 rows (ragged)
     (256, 160, 96, (0, 0, 2, 2, 3, 3), (cs.FP64, cs.FP32)),             # FP64 tiles, wall-node z
-    (200, 99, 170, (0, 0, 3, 3, 1, 1), (cs.FP32, cs.FP64)),             # 11 segments of 16 rows, last 10; ragged mode tile
+    (400, 99, 170, (0, 0, 3, 3, 1, 1), (cs.FP32, cs.FP64)),             # 11 segments of 16 rows, last 10; last mode tile 16 wide
 ]
 
 
@@ -54,13 +52,12 @@ def _solve_all():
     return out
 
 
-@pytest.mark.parametrize("variant", ["1", "2"])
-def test_z_kernel_variants_agree_bitwise(cuda_device, tmp_path, variant):
+def test_persistent_and_one_tile_z_kernels_agree_bitwise(cuda_device, tmp_path):
     mine = _solve_all()
-    dst = tmp_path / f"variant{variant}.npz"
+    dst = tmp_path / "persistent.npz"
     code = ("import sys, numpy as np; sys.path.insert(0, %r); "
             "import tests.test_gpu_zpersist as T; np.savez(%r, **T._solve_all())" % (ROOT, str(dst)))
-    env = dict(os.environ, CALES_ZVARIANT=variant)
+    env = dict(os.environ, CALES_ZPERSIST="1")
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     other = np.load(dst)

@@ -44,8 +44,8 @@ template <> __device__ __forceinline__ double rcp_<double>(double d) {
     const unsigned e = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
     if (e - 898u > 249u) return 1.0 / d;
     double r = (double)__frcp_rn((float)d);
-    r = r * fma(-d, r, 2.0);
-    r = r * fma(-d, r, 2.0);
+    r = __dmul_rn(r, __fma_rn(-d, r, 2.0));
+    r = __dmul_rn(r, __fma_rn(-d, r, 2.0));
     return r;
 }
 
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(256) k_zsolve(ZArgs<T> a) {
     if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
     __syncthreads();
     if (sing_tile && tid == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
+        const T base0 = a.sigma - mul_(a.alpha, a.lamx[0] + a.lamy[0]);
         serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, 0,
                        a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
@@ -438,7 +438,7 @@ template <typename T> __device__ __forceinline__ T frcp(T d);
 template <> __device__ __forceinline__ float frcp<float>(float d) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-    return r * __fmaf_rn(-d, r, 2.0f);
+    return __fmul_rn(r, __fmaf_rn(-d, r, 2.0f));
 }
 template <> __device__ __forceinline__ double frcp<double>(double d) { return rcp_<double>(d); }
 
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(256) k_zsolve_reg(ZArgs<T> a) {
     if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
     __syncthreads();
     if (sing_tile && tid == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
+        const T base0 = a.sigma - mul_(a.alpha, a.lamx[0] + a.lamy[0]);
         serial_line<T>(tile, TM, m, segs, save0, r0, sA, sC, sG, sO, a.dzf, nz, base0, true, a.cacc, a.cacc_scale, m,
                        a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0);
         for (int k = 0; k < nz; ++k)
@@ -695,6 +695,10 @@ static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
 // broadcast.  The tile moves by 16-byte cp.async copies (all in flight at
 // once) and vector stores.  Segment states are chained by warp 0 through
 // shared memory.  Pivot reciprocals of a segment stay in registers.
+// Every product that feeds a sum is rounded explicitly (mul_ / fma_), so the
+// compiler's FMA contraction cannot differ between the instantiations (full
+// or ragged segments, one-tile, grouped, persistent): all of them give
+// bit-identical solves.
 // ---------------------------------------------------------------------------
 template <typename T> struct alignas(2 * sizeof(T)) ZPair { T a, c; };
 
@@ -789,9 +793,9 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     }
     if (sing_tile && tid == 0)
         for (int k = 0; k < nz; ++k) tb.save0[k] = tile[k * TM];
-    const T base = a.sigma - a.alpha * lam;
-    const T ebot = a.zlo == ZBC_D ? T(2) * sA[0] : (a.zlo == ZBC_DF ? sA[0] : T(0));
-    const T etop = a.zhi == ZBC_D ? T(2) * sC[nz - 1] : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
+    const T base = a.sigma - mul_(a.alpha, lam);
+    const T ebot = a.zlo == ZBC_D ? mul_(T(2), sA[0]) : (a.zlo == ZBC_DF ? sA[0] : T(0));
+    const T etop = a.zhi == ZBC_D ? mul_(T(2), sC[nz - 1]) : (a.zhi == ZBC_DF ? sC[nz - 1] : T(0));
     const bool act = s < P;
     const int k0 = act ? s * m : 0;
     const int mseg = act ? max(0, min(m, nz - k0)) : 0;
@@ -824,7 +828,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
                 T e = base + ebot + (nz == 1 ? etop : T(0));
     #pragma unroll
                 for (int j = 1; j < MAXM; ++j)
-                    if (INSEG(j)) e = base + AC[j].a * e * frcp<T>(AC[j - 1].c + e) + XT(j);
+                    if (INSEG(j)) e = fma_(mul_(AC[j].a, e), frcp<T>(AC[j - 1].c + e), base) + XT(j);
                 g11 = T(0); g12 = e; g21 = T(0); g22 = T(1);         // constant map -> e_end
             } else {
     #pragma unroll
@@ -832,13 +836,13 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
                     if (INSEG(j)) {
                         const T x = XT(j);
                         const T cm = AC[j - 1].c;              // k0 + j - 1 >= 0 for s > 0
-                        const T am = base + AC[j].a + x, bm = (base + x) * cm;
-                        const T n11 = am * g11 + bm * g21, n12 = am * g12 + bm * g22;
-                        const T n21 = g11 + cm * g21, n22 = g12 + cm * g22;
+                        const T am = base + AC[j].a + x, bm = mul_(base + x, cm);
+                        const T n11 = fma_(am, g11, mul_(bm, g21)), n12 = fma_(am, g12, mul_(bm, g22));
+                        const T n21 = fma_(cm, g21, g11), n22 = fma_(cm, g22, g12);
                         g11 = n11; g12 = n12; g21 = n21; g22 = n22;
                         if ((j & 3) == 3) {
                             const T nrm = frcp<T>(g11 + g12 + g21 + g22);
-                            g11 *= nrm; g12 *= nrm; g21 *= nrm; g22 *= nrm;
+                            g11 = mul_(g11, nrm); g12 = mul_(g12, nrm); g21 = mul_(g21, nrm); g22 = mul_(g22, nrm);
                         }
                     }
                 }
@@ -851,7 +855,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
             for (int t = 0; t < P; ++t) {
                 const int i = t * TM + c;
                 cin[i] = e;
-                e = (c11[i] * e + c12[i]) * frcp<T>(c21[i] * e + c22[i]);
+                e = mul_(fma_(c11[i], e, c12[i]), frcp<T>(fma_(c21[i], e, c22[i])));
             }
         }
         __syncthreads();
@@ -866,15 +870,15 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     {
         T e;
         if (k0 == 0) e = base + ebot + (nz == 1 ? etop : T(0));
-        else e = base + AC[0].a * e_in * frcp<T>(AC[-1].c + e_in) + XT(0);
+        else e = fma_(mul_(AC[0].a, e_in), frcp<T>(AC[-1].c + e_in), base) + XT(0);
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
             if (INSEG(j)) {
                 const ZPair<T> ac = AC[j];
-                if (j > 0) e = base + ac.a * e * inv[j - 1] + XT(j);
+                if (j > 0) e = fma_(mul_(ac.a, e), inv[j - 1], base) + XT(j);
                 inv[j] = frcp<T>(ac.c + e);
-                al = ac.a * inv[j] * al;
-                be = (col[j * TM] * GW(j) + ac.a * be) * inv[j];
+                al = mul_(mul_(ac.a, inv[j]), al);
+                be = mul_(fma_(ac.a, be, mul_(col[j * TM], GW(j))), inv[j]);
                 bad |= !(inv[j] > T(0));
             }
         }
@@ -904,10 +908,10 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
         for (int j = 0; j < MAXM; ++j) {
             if (INSEG(j)) {
                 const ZPair<T> ac = AC[j];
-                y = (col[j * TM] * GW(j) + ac.a * y) * inv[j];
+                y = mul_(fma_(ac.a, y, mul_(col[j * TM], GW(j))), inv[j]);
                 col[j * TM] = y;
-                Q += R * y;
-                R *= ac.c * inv[j];
+                Q = fma_(R, y, Q);
+                R = mul_(R, mul_(ac.c, inv[j]));
             }
         }
         c21[me] = Q;
@@ -933,8 +937,8 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
 #pragma unroll
         for (int j = MAXM - 1; j >= 0; --j) {
             if (INSEG(j)) {
-                x = col[j * TM] + AC[j].c * inv[j] * x;
-                col[j * TM] = ADJ ? x * O[j] : x;
+                x = fma_(mul_(AC[j].c, inv[j]), x, col[j * TM]);
+                col[j * TM] = ADJ ? mul_(x, O[j]) : x;
                 xs += x;
             }
         }
@@ -947,7 +951,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     if (bad && a.status) atomicOr(a.status, ST_BADPIVOT | ST_NONFINITE);
     __syncthreads();
     if (sing_tile && s == 0) {
-        const T base0 = a.sigma - a.alpha * (a.lamx[0] + a.lamy[0]);
+        const T base0 = a.sigma - mul_(a.alpha, a.lamx[0] + a.lamy[0]);
         const double shift = a.shift_acc ? a.shift_acc[0] * a.shift_scale : 0.0;
         if (base0 == T(0) && a.zlo == ZBC_N && a.zhi == ZBC_N) {
             singular_line_warp<T>(tile, TM, tb.save0, sA, sC, tb.sG, tb.sO, a.dzf, nz, a.cacc, a.cacc_scale, shift,

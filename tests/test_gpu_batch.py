@@ -78,13 +78,17 @@ def test_batch_graph_replay(cuda_device):
                 assert torch.equal(a, b)
 
 
-def test_grouped_and_fork_join_batches_agree(cuda_device):
+@pytest.mark.parametrize("autotune", [True, False])
+def test_grouped_and_fork_join_batches_agree(cuda_device, autotune):
     """The grouped stage launches against the fork/join of per-solve launches
     over streams: the same kernels' arithmetic per solve, so bit for bit
-    except singular Poisson solves (order of the FP64 gauge-sum atomics)."""
+    except singular Poisson solves (order of the FP64 gauge-sum atomics).
+    With the default schedules the w solve of the third domain (32 wall-node
+    rows, two full z segments of 16) runs the full-segment z kernel alone and
+    the ragged-segment kernel in the grouped launch."""
     domains = [(48, 32, 24), (96, 64, 40), (64, 48, 33)]
     alphas = [1e-4, 1e-3, 1e-4]
-    batch, plans, tags = B.rk3_substep_batch(domains, alphas)
+    batch, plans, tags = B.rk3_substep_batch(domains, alphas, autotune=autotune)
     fs = _inputs(plans, 4200)
     ug = [torch.empty_like(f) for f in fs]
     batch.solve(fs, ug)

@@ -4,8 +4,9 @@ Both run the same per-tile arithmetic (the same device function), so their
 solves agree bit for bit.  The persistent kernel runs in a child process started
 with CALES_ZPERSIST=1 (read once per process).  The grids have enough modes
 (at least eight 32-mode tiles per SM) for the persistent kernel to be chosen:
-full and ragged z segments, a ragged last mode tile, FP32, FP64 and FP32 +
-refinement, Poisson, Helmholtz and the adjoint solve.
+full and ragged z segments, a ragged last mode tile, the bench's 512-deep duct
+lines (16 segments of 32 rows, singular mode (0, 0) solved by one warp), FP32,
+FP64 and FP32 + refinement, Poisson, Helmholtz and the adjoint solve.
 """
 import os
 import subprocess
@@ -28,6 +29,7 @@ CASES = [
     (256, 256, 300, (0, 0, 1, 1, 2, 1), (cs.FP32, cs.FP32_REFINE)),     # 10 segments of 30 rows (ragged)
     (256, 160, 96, (0, 0, 2, 2, 3, 3), (cs.FP64, cs.FP32)),             # FP64 tiles, wall-node z
     (400, 99, 170, (0, 0, 3, 3, 1, 1), (cs.FP32, cs.FP64)),             # 11 segments of 16 rows, last 10; last mode tile 16 wide
+    (1536, 40, 512, (0, 0, 1, 1, 1, 1), (cs.FP32, cs.FP32_REFINE)),     # the bench's duct lines: 16 segments of 32 rows
 ]
 
 

@@ -50,7 +50,6 @@ MODE_TEXT = {
 }
 UNIT = "Gpoints/s"
 # algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
-# algorithmic bytes per grid point and launch of each kernel (FP32 mode space)
 KERNEL_BYTES_PER_POINT = {
     "x_fwd": 12.0,            # read f (FP64 8 B), write 4 B
     "x_fwd_sweep": 8.0,       # read r 4 B, write 4 B
@@ -60,6 +59,7 @@ KERNEL_BYTES_PER_POINT = {
     "x_inv_acc_d": 24.0,      # the same, and the FP32 correction written (4 B): fast mode
     "residual": 20.0,         # read f 8 B + pair 8 B, write r 4 B
     "residual_update": 12.0,  # read r 4 B + correction 4 B, write r 4 B: fast mode
+    "x_fwd_ru": 12.0,         # the last update fused into the x transform: read r 4 B + correction 4 B, write 4 B
 }
 
 
@@ -73,7 +73,7 @@ def kernel_keys(prof):
         nxt = prof[i + 1][0] if i + 1 < len(prof) else None
         if name == "x_fwd" and prev in ("residual", "residual_update"):
             keys.append("x_fwd_sweep")
-        elif name == "x_inv_acc" and nxt == "residual_update":
+        elif name == "x_inv_acc" and nxt in ("residual_update", "x_fwd_ru"):
             keys.append("x_inv_acc_d")
         else:
             keys.append(name)

@@ -4,6 +4,72 @@
 
 namespace cales {
 
+// FP32 update of a refinement residual from the last correction d (the fast
+// refinement mode): r <- r - (c0 d + c1 L d) - (acc[0] - acc[2]).
+struct ResidUpdArgs {
+    float* r;            // in/out [nz][ny][nx]
+    const float* d;      // correction [nz][ny][nx]
+    int nx, ny, nz;
+    int bcx, bcy, zlo, zhi;   // KIND_* for x/y, ZBC_* (0 periodic) for z
+    float cx, cy, c0, c1;     // c1/dx^2, c1/dy^2, c0 (0 or 1), c1 (1 or -alpha)
+    const float* za;     // [nz] couplings 1/(dzc dzf), unscaled
+    const float* zc;
+    const double* acc;   // singular problems: acc[0] (current) and acc[2] (in r), else null
+};
+
+// Input tag of the forward x transform whose rows are the residual update
+// above, formed in shared memory (the update fused into the transform).
+struct RUIn {};
+
+// The residual update at VW consecutive points i .. i+VW-1 of row j of plane
+// k: returns r - (c0 d + c1 L d) - dshift there, with the R2 ghosts per side
+// and the periodic wraps.  Every product that feeds a sum is rounded
+// explicitly, so the standalone update and the one fused into the forward x
+// transform give the same bits.  VW = 4 needs 16-byte aligned rows.
+template <int VW>
+__device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, int i, int j, int k, float dshift, float* out) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long plane = (long)nx * ny;
+    const float zc = mul_(a.c1, a.zc[k]), za = mul_(a.c1, a.za[k]);
+    const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
+    const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
+    const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P, pz = a.zlo == 0;
+    const long offD = k > 0 ? -plane : (pz ? (long)(nz - 1) * plane : 0);
+    const long offU = k < nz - 1 ? plane : (pz ? -(long)(nz - 1) * plane : 0);
+    const float mD = (k > 0 || pz) ? 1.f : gd, mU = (k < nz - 1 || pz) ? 1.f : gu;
+    const long rb = (long)k * plane + (long)j * nx;
+    const long offS = j > 0 ? -(long)nx : (py ? (long)(ny - 1) * nx : 0);
+    const long offN = j < ny - 1 ? (long)nx : (py ? -(long)(ny - 1) * nx : 0);
+    const float mS = (j > 0 || py) ? 1.f : ghost_lo(a.bcy), mN = (j < ny - 1 || py) ? 1.f : ghost_hi(a.bcy);
+    const float* q = a.d + rb + i;
+    float c[VW], sv[VW], nv[VW], dn[VW], up[VW], r[VW];
+    if (VW == 4) {
+        const float4 c4 = *reinterpret_cast<const float4*>(q), s4 = *reinterpret_cast<const float4*>(q + offS);
+        const float4 n4 = *reinterpret_cast<const float4*>(q + offN), d4 = *reinterpret_cast<const float4*>(q + offD);
+        const float4 u4 = *reinterpret_cast<const float4*>(q + offU);
+        const float4 r4 = *reinterpret_cast<const float4*>(a.r + rb + i);
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+        nv[0] = n4.x; nv[1] = n4.y; nv[2] = n4.z; nv[3] = n4.w;
+        dn[0] = d4.x; dn[1] = d4.y; dn[2] = d4.z; dn[3] = d4.w;
+        up[0] = u4.x; up[1] = u4.y; up[2] = u4.z; up[3] = u4.w;
+        r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+    } else {
+        c[0] = q[0]; sv[0] = q[offS]; nv[0] = q[offN]; dn[0] = q[offD]; up[0] = q[offU]; r[0] = a.r[rb + i];
+    }
+    const float w = i > 0 ? q[-1] : (px ? q[nx - 1] : mul_(ghost_lo(a.bcx), c[0]));
+    const float e = i + VW < nx ? q[VW] : (px ? q[VW - nx] : mul_(ghost_hi(a.bcx), c[VW - 1]));
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+        const float xl = v > 0 ? c[v - 1] : w, xr = v < VW - 1 ? c[v + 1] : e;
+        const float tx = (xr - c[v]) + (xl - c[v]);
+        const float ty = (mul_(mN, nv[v]) - c[v]) + (mul_(mS, sv[v]) - c[v]);
+        const float tu = mul_(mU, up[v]) - c[v], td = mul_(mD, dn[v]) - c[v];
+        const float ld = fma_(za, td, fma_(zc, tu, fma_(a.cy, ty, mul_(a.cx, tx))));
+        out[v] = (r[v] - fma_(a.c0, c[v], ld)) - dshift;
+    }
+}
+
 template <typename T> struct RowArgs {
     DirTab<T> t;
     const void* in;
@@ -23,6 +89,10 @@ template <typename T> struct RowArgs {
     const double* gw;
     int ny;
     unsigned nymag;
+    // forward transform with input RUIn: the rows are the residual update
+    // (ru.r rows of this CTA, ru.d with its neighbours), computed in shared
+    // memory; `in` is unused
+    ResidUpdArgs ru;
 };
 
 // Output modes of the inverse x kernel.
@@ -118,19 +188,6 @@ struct ResidFFArgs {
     int rows_per_cta;    // set by the launcher
 };
 
-// FP32 update of a refinement residual from the last correction d (the fast
-// refinement mode): r <- r - (c0 d + c1 L d) - (acc[0] - acc[2]).
-struct ResidUpdArgs {
-    float* r;            // in/out [nz][ny][nx]
-    const float* d;      // correction [nz][ny][nx]
-    int nx, ny, nz;
-    int bcx, bcy, zlo, zhi;   // KIND_* for x/y, ZBC_* (0 periodic) for z
-    float cx, cy, c0, c1;     // c1/dx^2, c1/dy^2, c0 (0 or 1), c1 (1 or -alpha)
-    const float* za;     // [nz] couplings 1/(dzc dzf), unscaled
-    const float* zc;
-    const double* acc;   // singular problems: acc[0] (current) and acc[2] (in r), else null
-};
-
 // Smagorinsky / van Driest eddy viscosity at the cell centres of a channel.
 template <typename T> struct SgsArgs {
     const T* u;          // x-faces [nz][ny][nx]
@@ -172,13 +229,16 @@ template <typename T> struct MomArgs {
 enum StatusBits { ST_NONFINITE = 1, ST_BADPIVOT = 2, ST_TIMEOUT = 4 };
 
 template <typename T, typename TIn> cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st);
+// RUIn input: needs nx % 4 == 0 and 16-byte aligned ru.r, ru.d
+bool rows_forward_ru_ok(const RowArgs<float>& a);
 template <typename T, int MODE> cudaError_t launch_rows_inverse(const RowArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st);
 // Compile-time-size FP32 variants of the transforms (periodic rows with
 // L = 128, 256, 768; column tiles (L, TX) = (64, 32), (128, 32), (256, 16)
 // of every kind): launch and return true when the sizes have one.
 // CALES_STATIC_FFT=0 in the environment turns them off.
-bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream_t st, cudaError_t* err);
+// in_kind: 0 FP32 rows, 1 FP64 rows, 2 the fused residual update (RUIn)
+bool launch_rows_forward_static(const RowArgs<float>& a, int in_kind, cudaStream_t st, cudaError_t* err);
 bool launch_rows_inverse_static(const RowArgs<float>& a, int mode, cudaStream_t st, cudaError_t* err);
 bool launch_cols_static(const ColArgs<float>& a, bool inverse, cudaStream_t st, cudaError_t* err);
 bool static_fft_enabled();

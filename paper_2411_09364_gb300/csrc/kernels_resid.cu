@@ -51,57 +51,22 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
 // rows allow it, else 1), the threads running over (row, group) together.
 template <int VW>
 __global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__ ResidUpdArgs a, const int rows) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nx = a.nx, ny = a.ny;
     const int k = blockIdx.y;
     const long plane = (long)nx * ny;
-    const float zc = a.c1 * a.zc[k], za = a.c1 * a.za[k];
     const float dshift = a.acc ? (float)(a.acc[0] - a.acc[2]) : 0.f;
-    const float gxl = ghost_lo(a.bcx), gxh = ghost_hi(a.bcx), gyl = ghost_lo(a.bcy), gyh = ghost_hi(a.bcy);
-    const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
-    const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
-    const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P, pz = a.zlo == 0;
-    const long offD = k > 0 ? -plane : (pz ? (long)(nz - 1) * plane : 0);
-    const long offU = k < nz - 1 ? plane : (pz ? -(long)(nz - 1) * plane : 0);
-    const float mD = (k > 0 || pz) ? 1.f : gd, mU = (k < nz - 1 || pz) ? 1.f : gu;
     const int j0 = blockIdx.x * rows, j1 = min(j0 + rows, ny);
     const int ng = nx / VW;
     const unsigned gmag = div_magic((unsigned)ng);
     const int tot = (j1 - j0) * ng;
-    const float* __restrict__ d = a.d;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
         const int jj = (int)fdivu((unsigned)t, gmag);
         const int j = j0 + jj, i = (t - jj * ng) * VW;
-        const long rb = (long)k * plane + (long)j * nx;
-        const long offS = j > 0 ? -(long)nx : (py ? (long)(ny - 1) * nx : 0);
-        const long offN = j < ny - 1 ? (long)nx : (py ? -(long)(ny - 1) * nx : 0);
-        const float mS = (j > 0 || py) ? 1.f : gyl, mN = (j < ny - 1 || py) ? 1.f : gyh;
-        const float* q = d + rb + i;
-        float c[VW], s[VW], n[VW], dn[VW], up[VW], r[VW];
-        if (VW == 4) {
-            const float4 c4 = *reinterpret_cast<const float4*>(q), s4 = *reinterpret_cast<const float4*>(q + offS);
-            const float4 n4 = *reinterpret_cast<const float4*>(q + offN), d4 = *reinterpret_cast<const float4*>(q + offD);
-            const float4 u4 = *reinterpret_cast<const float4*>(q + offU);
-            const float4 r4 = *reinterpret_cast<const float4*>(a.r + rb + i);
-            c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-            s[0] = s4.x; s[1] = s4.y; s[2] = s4.z; s[3] = s4.w;
-            n[0] = n4.x; n[1] = n4.y; n[2] = n4.z; n[3] = n4.w;
-            dn[0] = d4.x; dn[1] = d4.y; dn[2] = d4.z; dn[3] = d4.w;
-            up[0] = u4.x; up[1] = u4.y; up[2] = u4.z; up[3] = u4.w;
-            r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
-        } else {
-            c[0] = q[0]; s[0] = q[offS]; n[0] = q[offN]; dn[0] = q[offD]; up[0] = q[offU]; r[0] = a.r[rb + i];
-        }
-        const float w = i > 0 ? q[-1] : (px ? q[nx - 1] : gxl * c[0]);
-        const float e = i + VW < nx ? q[VW] : (px ? q[VW - nx] : gxh * c[VW - 1]);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-            const float xl = v > 0 ? c[v - 1] : w, xr = v < VW - 1 ? c[v + 1] : e;
-            const float ld = a.cx * ((xr - c[v]) + (xl - c[v])) + a.cy * ((mN * n[v] - c[v]) + (mS * s[v] - c[v])) +
-                             zc * (mU * up[v] - c[v]) + za * (mD * dn[v] - c[v]);
-            r[v] = r[v] - (a.c0 * c[v] + ld) - dshift;
-        }
-        if (VW == 4) *reinterpret_cast<float4*>(a.r + rb + i) = make_float4(r[0], r[1], r[2], r[3]);
-        else a.r[rb + i] = r[0];
+        float r[VW];
+        resupd_group<VW>(a, i, j, k, dshift, r);
+        float* o = a.r + (long)k * plane + (long)j * nx + i;
+        if (VW == 4) *reinterpret_cast<float4*>(o) = make_float4(r[0], r[1], r[2], r[3]);
+        else o[0] = r[0];
     }
 }
 

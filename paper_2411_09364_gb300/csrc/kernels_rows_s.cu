@@ -6,9 +6,12 @@
 namespace cales {
 
 template <int LS>
-static cudaError_t rows_fwd_l(const RowArgs<float>& a, bool in_f64, cudaStream_t st) {
-    return in_f64 ? launch_rows_forward_v<float, double, LS, KIND_P>(a, st)
-                  : launch_rows_forward_v<float, float, LS, KIND_P>(a, st);
+static cudaError_t rows_fwd_l(const RowArgs<float>& a, int in_kind, cudaStream_t st) {
+    switch (in_kind) {
+        case 1: return launch_rows_forward_v<float, double, LS, KIND_P>(a, st);
+        case 2: return launch_rows_forward_v<float, RUIn, LS, KIND_P>(a, st);
+        default: return launch_rows_forward_v<float, float, LS, KIND_P>(a, st);
+    }
 }
 
 template <int LS>
@@ -23,12 +26,12 @@ static cudaError_t rows_inv_l(const RowArgs<float>& a, int mode, cudaStream_t st
     }
 }
 
-bool launch_rows_forward_static(const RowArgs<float>& a, bool in_f64, cudaStream_t st, cudaError_t* err) {
+bool launch_rows_forward_static(const RowArgs<float>& a, int in_kind, cudaStream_t st, cudaError_t* err) {
     if (!static_fft_enabled() || a.t.kind != KIND_P || !radices_match(a.t, a.t.L)) return false;
     switch (a.t.L) {
-        case 128: *err = rows_fwd_l<128>(a, in_f64, st); return true;
-        case 256: *err = rows_fwd_l<256>(a, in_f64, st); return true;
-        case 768: *err = rows_fwd_l<768>(a, in_f64, st); return true;
+        case 128: *err = rows_fwd_l<128>(a, in_kind, st); return true;
+        case 256: *err = rows_fwd_l<256>(a, in_kind, st); return true;
+        case 768: *err = rows_fwd_l<768>(a, in_kind, st); return true;
         default: return false;
     }
 }

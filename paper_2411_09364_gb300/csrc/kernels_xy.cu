@@ -4,6 +4,7 @@
 #include "xy_impl.cuh"
 
 #include <cstdlib>
+#include <type_traits>
 
 namespace cales {
 
@@ -19,7 +20,8 @@ template <typename T, typename TIn>
 cudaError_t launch_rows_forward(const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         cudaError_t err = cudaSuccess;
-        if (launch_rows_forward_static(a, sizeof(TIn) == 8, st, &err)) return err;
+        const int in_kind = std::is_same<TIn, RUIn>::value ? 2 : (sizeof(TIn) == 8 ? 1 : 0);
+        if (launch_rows_forward_static(a, in_kind, st, &err)) return err;
     }
     return launch_rows_forward_v<T, TIn, 0, -1>(a, st);
 }
@@ -52,6 +54,12 @@ cudaError_t launch_cols(const ColArgs<T>& a, bool inverse, cudaStream_t st) {
 template cudaError_t launch_rows_forward<double, double>(const RowArgs<double>&, cudaStream_t);
 template cudaError_t launch_rows_forward<float, float>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_forward<float, double>(const RowArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_forward<float, RUIn>(const RowArgs<float>&, cudaStream_t);
+
+bool rows_forward_ru_ok(const RowArgs<float>& a) {
+    const auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    return a.t.n >= 4 && a.t.n % 4 == 0 && al16(a.ru.r) && al16(a.ru.d) && a.ru.nx == a.t.n;
+}
 template cudaError_t launch_rows_inverse<double, OUT_T>(const RowArgs<double>&, cudaStream_t);
 template cudaError_t launch_rows_inverse<float, OUT_T>(const RowArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_inverse<float, OUT_F64>(const RowArgs<float>&, cudaStream_t);

@@ -20,6 +20,8 @@
 #include "kernels.cuh"
 #include "plan.h"
 
+#include <type_traits>
+
 using namespace cales;
 
 namespace {
@@ -376,7 +378,8 @@ RowArgs<T> fwd_row_args(cales_plan_s* P, const void* in, T* work) {
     ra.shift_acc = nullptr;
     ra.shift_scale = 0.0;
     ra.status = P->status;
-    ra.bulk = (aligned16(in) && aligned16(work) && ((size_t)P->nx * sizeof(TIn)) % 16 == 0 &&
+    const size_t in_size = std::is_same<TIn, RUIn>::value ? sizeof(T) : sizeof(TIn);
+    ra.bulk = (aligned16(in) && aligned16(work) && ((size_t)P->nx * in_size) % 16 == 0 &&
                ((size_t)P->nx * sizeof(T)) % 16 == 0) ? 1 : 0;
     ra.dout = nullptr;
     ra.gacc = nullptr;
@@ -463,11 +466,14 @@ RowArgs<T> inv_row_args(cales_plan_s* P, T* work, void* out, const PassOpt& o) {
 // One pass of the solver: in (TIn) -> work (T, mode space) -> out (MODE).
 // OUT_FF_ACC_D: the inverse x pass also stores the correction into work
 // (its own input rows) and adds the gauge sum of the updated pairs to gacc.
+// TIn = RUIn: the forward x pass forms its rows as the residual update *ru
+// (the fused fast-mode update; `in` unused).
 template <typename T, typename TIn, int MODE>
 int pipeline(cales_plan_s* P, const void* in, void* out, T* work, const PassOpt& o, cudaStream_t st,
-             double* gacc = nullptr) {
-    const RowArgs<T> ra = fwd_row_args<T, TIn>(P, in, work);
-    P->prof_begin(st, "x_fwd");
+             double* gacc = nullptr, const ResidUpdArgs* ru = nullptr) {
+    RowArgs<T> ra = fwd_row_args<T, TIn>(P, in, work);
+    if constexpr (std::is_same<TIn, RUIn>::value) ra.ru = *ru;
+    P->prof_begin(st, std::is_same<TIn, RUIn>::value ? "x_fwd_ru" : "x_fwd");
     if (launch_rows_forward<T, TIn>(ra, st) != cudaSuccess) return CALES_ECUDA;
     P->prof_end(st);
 
@@ -613,6 +619,26 @@ static int refine_solve(cales_plan_t P, bool helm, double alpha, const void* f, 
     return CALES_OK;
 }
 
+// The last residual update of the fast refinement fused into the forward x
+// transform of the last solve: only with CALES_FUSE_RU=1.  It saves the 8
+// bytes per point of writing and re-reading the updated residual, but on
+// GB300 at 1536 x 512 x 512 the fused pass took 1.66 ms against 1.42 ms for
+// the update (0.73 ms, 96 % of the copy bandwidth at 64 warps per SM) and the
+// transform (0.69 ms) apart: inside the transform's CTAs (73 KB of shared
+// memory, 24 warps per SM) the update's neighbour loads are not hidden, and
+// fewer rows per CTA did not help (1.69 ms with 2 rows, 2.26 ms with 1).
+// Needs rows of a multiple of 4 points and 16-byte aligned fields.
+static bool fuse_residual_update(cales_plan_t P, const ResidUpdArgs& ua) {
+    static const bool on = [] {
+        const char* e = getenv("CALES_FUSE_RU");
+        return e && e[0] == '1';
+    }();
+    if (!on) return false;
+    RowArgs<float> ra = fwd_row_args<float, RUIn>(P, nullptr, ua.r);
+    ra.ru = ua;
+    return rows_forward_ru_ok(ra);
+}
+
 // Fast refinement: the residual is formed in double-float once, after the
 // first FP32 solve; every later sweep updates it in FP32 from the correction
 // of the sweep before, r_{s+1} = r_s - M d_s (the inverse x pass stores d_s
@@ -651,6 +677,17 @@ static int refine_solve_fast(cales_plan_t P, bool helm, double alpha, const void
     ua.acc = sing ? acc : nullptr;
     for (int s = 0; s < ns; ++s) {
         const bool last = s == ns - 1;
+        if (last && fuse_residual_update(P, ua)) {
+            // the last update fused into the forward x pass: the update of
+            // each row is formed in shared memory and transformed there, the
+            // transformed rows overwrite the residual (this pass reads only
+            // its own rows of it), which then serves as the solve's workspace
+            o.shift_acc = sing ? acc + 1 : nullptr;
+            o.shift_scale = 1.0 / ((double)P->nx * (double)P->ny * P->dzf_sum);
+            rc = pipeline<float, RUIn, OUT_FF_FINAL>(P, nullptr, p, res, o, st, nullptr, &ua);
+            if (rc) return rc;
+            continue;
+        }
         if (s > 0) {
             P->prof_begin(st, "residual_update");
             if (launch_residual_update(ua, st) != cudaSuccess) return CALES_ECUDA;

@@ -14,6 +14,8 @@
 #pragma once
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace cales {
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -74,11 +76,13 @@ __device__ __forceinline__ void rows_forward_body(const RowArgs<T>& a, const int
     const int nrad = LS ? sf_nrad(LS) : t.nrad;
     const long row0 = (long)bx * a.rpc;
     const int nr = (int)min((long)a.rpc, a.nrows - row0);
-    const TIn* __restrict__ in = reinterpret_cast<const TIn*>(a.in) + row0 * n;
+    constexpr bool RUP = std::is_same<TIn, RUIn>::value;
+    using TLd = typename std::conditional<RUP, T, TIn>::type;     // element type of `in`
+    const TLd* __restrict__ in = reinterpret_cast<const TLd*>(a.in) + row0 * n;
     T* __restrict__ out = reinterpret_cast<T*>(a.out) + row0 * n;
     const T sc = T(a.in_scale);
     const int tid = threadIdx.x;
-    if (n == 1) {
+    if (!RUP && n == 1) {
         for (int e = tid; e < nr; e += blockDim.x) out[e] = T(in[e]) * sc;
         return;
     }
@@ -94,7 +98,54 @@ __device__ __forceinline__ void rows_forward_body(const RowArgs<T>& a, const int
     const cpx<T>* pst = tw_s + t.twlen;
     const cpx<T>* mkt = tw_s + t.twlen + L + 1;
     const int tot = nr * n;
-    if (IN64) {
+    if constexpr (RUP) {
+        // the fused residual update: the CTA's rows formed in b0 (natural
+        // order), as the bulk copy of the standalone transform would leave them
+        if constexpr (sizeof(T) == 4) {
+            float* xs = reinterpret_cast<float*>(b0);
+            const ResidUpdArgs& u = a.ru;
+            // L2 prefetch of the rows the update reads: r and the correction
+            // at the CTA's rows, the correction one row before and after
+            // (y neighbours) and one plane below and above (z neighbours)
+            if (tid < 4) {
+                const long plane = (long)n * u.ny, N = plane * u.nz;
+                long lo = row0 * n, hi = lo + (long)nr * n;
+                const float* base = tid == 0 ? u.r : u.d;
+                if (tid == 1) { lo -= n; hi += n; }
+                if (tid == 2) { lo -= plane; hi -= plane; }
+                if (tid == 3) { lo += plane; hi += plane; }
+                lo = max(lo, 0L);
+                hi = min(hi, N);
+                if (hi > lo) bulk_prefetch_l2(base + lo, (uint32_t)((hi - lo) * sizeof(float)));
+            }
+            const float dshift = u.acc ? (float)(u.acc[0] - u.acc[2]) : 0.f;
+            const int ng = n / 4, tg = nr * ng;
+            const unsigned gmag = div_magic((unsigned)ng), ymag = div_magic((unsigned)u.ny);
+            // two groups per thread in flight
+            for (int e0 = tid; e0 < tg; e0 += 2 * blockDim.x) {
+                float v[2][4];
+                int off[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = e0 + h * blockDim.x;
+                    off[h] = -1;
+                    if (e < tg) {
+                        const int rr = (int)fdivu((unsigned)e, gmag), g = e - rr * ng;
+                        const unsigned R = (unsigned)(row0 + rr);
+                        const int k = (int)fdivu(R, ymag), j = (int)R - k * u.ny;
+                        resupd_group<4>(u, 4 * g, j, k, dshift, v[h]);
+                        off[h] = rr * n + 4 * g;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (off[h] >= 0)
+                        *reinterpret_cast<float4*>(xs + off[h]) = make_float4(v[h][0], v[h][1], v[h][2], v[h][3]);
+            }
+        }
+        stage_twiddles(tw_s, t);
+        __syncthreads();
+    } else if (IN64) {
         if (tid == 0 && a.bulk) bulk_prefetch_l2(in, (uint32_t)(tot * sizeof(TIn)));
         stage_twiddles(tw_s, t);
         __syncthreads();

@@ -21,23 +21,39 @@ struct ResidUpdArgs {
 // above, formed in shared memory (the update fused into the transform).
 struct RUIn {};
 
-// The residual update at VW consecutive points i .. i+VW-1 of row j of plane
-// k: returns r - (c0 d + c1 L d) - dshift there, with the R2 ghosts per side
-// and the periodic wraps.  Every product that feeds a sum is rounded
-// explicitly, so the standalone update and the one fused into the forward x
-// transform give the same bits.  VW = 4 needs 16-byte aligned rows.
-template <int VW>
-__device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, int i, int j, int k, float dshift, float* out) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long plane = (long)nx * ny;
-    const float zc = mul_(a.c1, a.zc[k]), za = mul_(a.c1, a.za[k]);
+// Plane constants of the residual update (plane k): the scaled z couplings,
+// the offsets of the z neighbours (periodic wrap, or the point itself at a
+// wall) and their ghost multipliers.
+struct RUPlane {
+    float zc, za, mD, mU;
+    long offD, offU;
+};
+__device__ __forceinline__ RUPlane ru_plane(const ResidUpdArgs& a, int k) {
+    const long plane = (long)a.nx * a.ny;
+    const bool pz = a.zlo == 0;
     const float gd = a.zlo == ZBC_N ? 1.f : (a.zlo == ZBC_D ? -1.f : 0.f);
     const float gu = a.zhi == ZBC_N ? 1.f : (a.zhi == ZBC_D ? -1.f : 0.f);
-    const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P, pz = a.zlo == 0;
-    const long offD = k > 0 ? -plane : (pz ? (long)(nz - 1) * plane : 0);
-    const long offU = k < nz - 1 ? plane : (pz ? -(long)(nz - 1) * plane : 0);
-    const float mD = (k > 0 || pz) ? 1.f : gd, mU = (k < nz - 1 || pz) ? 1.f : gu;
-    const long rb = (long)k * plane + (long)j * nx;
+    RUPlane c;
+    c.zc = mul_(a.c1, a.zc[k]);
+    c.za = mul_(a.c1, a.za[k]);
+    c.offD = k > 0 ? -plane : (pz ? (long)(a.nz - 1) * plane : 0);
+    c.offU = k < a.nz - 1 ? plane : (pz ? -(long)(a.nz - 1) * plane : 0);
+    c.mD = (k > 0 || pz) ? 1.f : gd;
+    c.mU = (k < a.nz - 1 || pz) ? 1.f : gu;
+    return c;
+}
+
+// The residual update at VW consecutive points i .. i+VW-1 of row j of plane
+// k (plane constants pk): returns r - (c0 d + c1 L d) - dshift there, with the
+// R2 ghosts per side and the periodic wraps.  Every product that feeds a sum
+// is rounded explicitly, so the standalone update and the one fused into the
+// forward x transform give the same bits.  VW = 4 needs 16-byte aligned rows.
+template <int VW>
+__device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, const RUPlane& pk, int i, int j, int k, float dshift,
+                                             float* out) {
+    const int nx = a.nx, ny = a.ny;
+    const bool px = a.bcx == KIND_P, py = a.bcy == KIND_P;
+    const long rb = (long)k * nx * ny + (long)j * nx;
     const long offS = j > 0 ? -(long)nx : (py ? (long)(ny - 1) * nx : 0);
     const long offN = j < ny - 1 ? (long)nx : (py ? -(long)(ny - 1) * nx : 0);
     const float mS = (j > 0 || py) ? 1.f : ghost_lo(a.bcy), mN = (j < ny - 1 || py) ? 1.f : ghost_hi(a.bcy);
@@ -45,8 +61,8 @@ __device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, int i, int j
     float c[VW], sv[VW], nv[VW], dn[VW], up[VW], r[VW];
     if (VW == 4) {
         const float4 c4 = *reinterpret_cast<const float4*>(q), s4 = *reinterpret_cast<const float4*>(q + offS);
-        const float4 n4 = *reinterpret_cast<const float4*>(q + offN), d4 = *reinterpret_cast<const float4*>(q + offD);
-        const float4 u4 = *reinterpret_cast<const float4*>(q + offU);
+        const float4 n4 = *reinterpret_cast<const float4*>(q + offN), d4 = *reinterpret_cast<const float4*>(q + pk.offD);
+        const float4 u4 = *reinterpret_cast<const float4*>(q + pk.offU);
         const float4 r4 = *reinterpret_cast<const float4*>(a.r + rb + i);
         c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
         sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
@@ -55,7 +71,7 @@ __device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, int i, int j
         up[0] = u4.x; up[1] = u4.y; up[2] = u4.z; up[3] = u4.w;
         r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
     } else {
-        c[0] = q[0]; sv[0] = q[offS]; nv[0] = q[offN]; dn[0] = q[offD]; up[0] = q[offU]; r[0] = a.r[rb + i];
+        c[0] = q[0]; sv[0] = q[offS]; nv[0] = q[offN]; dn[0] = q[pk.offD]; up[0] = q[pk.offU]; r[0] = a.r[rb + i];
     }
     const float w = i > 0 ? q[-1] : (px ? q[nx - 1] : mul_(ghost_lo(a.bcx), c[0]));
     const float e = i + VW < nx ? q[VW] : (px ? q[VW - nx] : mul_(ghost_hi(a.bcx), c[VW - 1]));
@@ -64,8 +80,8 @@ __device__ __forceinline__ void resupd_group(const ResidUpdArgs& a, int i, int j
         const float xl = v > 0 ? c[v - 1] : w, xr = v < VW - 1 ? c[v + 1] : e;
         const float tx = (xr - c[v]) + (xl - c[v]);
         const float ty = (mul_(mN, nv[v]) - c[v]) + (mul_(mS, sv[v]) - c[v]);
-        const float tu = mul_(mU, up[v]) - c[v], td = mul_(mD, dn[v]) - c[v];
-        const float ld = fma_(za, td, fma_(zc, tu, fma_(a.cy, ty, mul_(a.cx, tx))));
+        const float tu = mul_(pk.mU, up[v]) - c[v], td = mul_(pk.mD, dn[v]) - c[v];
+        const float ld = fma_(pk.za, td, fma_(pk.zc, tu, fma_(a.cy, ty, mul_(a.cx, tx))));
         out[v] = (r[v] - fma_(a.c0, c[v], ld)) - dshift;
     }
 }

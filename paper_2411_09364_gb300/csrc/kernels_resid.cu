@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__
     const int k = blockIdx.y;
     const long plane = (long)nx * ny;
     const float dshift = a.acc ? (float)(a.acc[0] - a.acc[2]) : 0.f;
+    const RUPlane pk = ru_plane(a, k);
     const int j0 = blockIdx.x * rows, j1 = min(j0 + rows, ny);
     const int ng = nx / VW;
     const unsigned gmag = div_magic((unsigned)ng);
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) k_residual_update(const __grid_constant__
         const int jj = (int)fdivu((unsigned)t, gmag);
         const int j = j0 + jj, i = (t - jj * ng) * VW;
         float r[VW];
-        resupd_group<VW>(a, i, j, k, dshift, r);
+        resupd_group<VW>(a, pk, i, j, k, dshift, r);
         float* o = a.r + (long)k * plane + (long)j * nx + i;
         if (VW == 4) *reinterpret_cast<float4*>(o) = make_float4(r[0], r[1], r[2], r[3]);
         else o[0] = r[0];

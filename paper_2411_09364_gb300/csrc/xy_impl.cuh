@@ -133,7 +133,7 @@ __device__ __forceinline__ void rows_forward_body(const RowArgs<T>& a, const int
                         const int rr = (int)fdivu((unsigned)e, gmag), g = e - rr * ng;
                         const unsigned R = (unsigned)(row0 + rr);
                         const int k = (int)fdivu(R, ymag), j = (int)R - k * u.ny;
-                        resupd_group<4>(u, 4 * g, j, k, dshift, v[h]);
+                        resupd_group<4>(u, ru_plane(u, k), 4 * g, j, k, dshift, v[h]);
                         off[h] = rr * n + 4 * g;
                     }
                 }

@@ -897,7 +897,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
                 if (t0 + u < P) { ka[u] = c11[(t0 + u) * TM + c]; kb[u] = c12[(t0 + u) * TM + c]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 + u < P) { cin[(t0 + u) * TM + c] = y; y = ka[u] * y + kb[u]; }
+                if (t0 + u < P) { cin[(t0 + u) * TM + c] = y; y = fma_(ka[u], y, kb[u]); }
         }
     }
     __syncthreads();
@@ -927,7 +927,7 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
                 if (t0 - u >= 0) { kq[u] = c21[(t0 - u) * TM + c]; kr[u] = c22[(t0 - u) * TM + c]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 - u >= 0) { cin[(t0 - u) * TM + c] = x; x = kq[u] + kr[u] * x; }
+                if (t0 - u >= 0) { cin[(t0 - u) * TM + c] = x; x = fma_(kr[u], x, kq[u]); }
         }
     }
     __syncthreads();

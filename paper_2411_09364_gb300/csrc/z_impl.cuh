@@ -886,24 +886,22 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
     c11[me] = al;
     c12[me] = be;
     __syncthreads();
-    if (s == 0) {
-        // chain of the segments' affine maps; the coefficients of four
-        // segments are loaded together ahead of their dependent steps
+    // E: forward sweep writing y, back-substitution composite.  Each warp
+    // chains the affine maps of the segments before its own (in segment
+    // order, four segments' coefficients loaded ahead of their dependent
+    // steps), so no warp waits for a serial chain and a second barrier.
+    {
         T y = T(0);
-        for (int t0 = 0; t0 < P; t0 += 4) {
+        for (int t0 = 0; t0 < s && act; t0 += 4) {
             T ka[4], kb[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 + u < P) { ka[u] = c11[(t0 + u) * TM + c]; kb[u] = c12[(t0 + u) * TM + c]; }
+                if (t0 + u < s) { ka[u] = c11[(t0 + u) * TM + c]; kb[u] = c12[(t0 + u) * TM + c]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 + u < P) { cin[(t0 + u) * TM + c] = y; y = fma_(ka[u], y, kb[u]); }
+                if (t0 + u < s) y = fma_(ka[u], y, kb[u]);
         }
-    }
-    __syncthreads();
-    // E: forward sweep writing y, back-substitution composite
-    {
-        T y = cin[me], Q = T(0), R = T(1);
+        T Q = T(0), R = T(1);
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
             if (INSEG(j)) {
@@ -918,22 +916,19 @@ __device__ __forceinline__ void zw_solve_tile(const ZArgs<T>& a, T* tile, T* ch,
         c22[me] = R;
     }
     __syncthreads();
-    if (s == 0) {
-        T x = T(0);
-        for (int t0 = P - 1; t0 >= 0; t0 -= 4) {
+    // G: back-substitution; each warp chains the back-substitution maps of
+    // the segments above its own, from the top segment down
+    {
+        T x = T(0), xs = T(0);
+        for (int t0 = P - 1; t0 > s && act; t0 -= 4) {
             T kq[4], kr[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 - u >= 0) { kq[u] = c21[(t0 - u) * TM + c]; kr[u] = c22[(t0 - u) * TM + c]; }
+                if (t0 - u > s) { kq[u] = c21[(t0 - u) * TM + c]; kr[u] = c22[(t0 - u) * TM + c]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (t0 - u >= 0) { cin[(t0 - u) * TM + c] = x; x = fma_(kr[u], x, kq[u]); }
+                if (t0 - u > s) x = fma_(kr[u], x, kq[u]);
         }
-    }
-    __syncthreads();
-    // G: back-substitution
-    {
-        T x = cin[me], xs = T(0);
 #pragma unroll
         for (int j = MAXM - 1; j >= 0; --j) {
             if (INSEG(j)) {

@@ -693,8 +693,9 @@ static cudaError_t launch_zsolve_reg(const ZArgs<T>& a, cudaStream_t st) {
 // [s*m, s*m + m) of all 32 modes, so every shared-memory row access of a warp
 // is one contiguous 128-byte (FP32) row and every coefficient read is a
 // broadcast.  The tile moves by 16-byte cp.async copies (all in flight at
-// once) and vector stores.  Segment states are chained by warp 0 through
-// shared memory.  Pivot reciprocals of a segment stay in registers.
+// once) and vector stores.  Segment states pass through shared memory: warp 0
+// chains the pivot maps, each warp the elimination maps before and after its
+// own segment.  Pivot reciprocals of a segment stay in registers.
 // Every product that feeds a sum is rounded explicitly (mul_ / fma_), so the
 // compiler's FMA contraction cannot differ between the instantiations (full
 // or ragged segments, one-tile, grouped, persistent): all of them give
@@ -756,7 +757,7 @@ __device__ __forceinline__ void zw_store(T* __restrict__ out, const T* tile, lon
 // The solve of one tile of 32 modes (q0 .. q0 + w - 1) already in shared
 // memory, in place; every thread of the CTA takes part (P warps, warp s owns
 // rows [s m, s m + m)).  Phases as in the header of this file; the segment
-// states are chained by warp 0 through `ch` (6 x [P][32]).
+// states pass through `ch` (6 x [P][32]).
 // FULL: every segment has exactly MAXM rows (nz = P * MAXM), so the row
 // predicates and the first/last-row conditions reduce to compile-time tests
 // on j plus one warp-uniform test on s.  ADJ: the adjoint weights (Eq. 16
